@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ParIS+ hot path on random-walk data (ParIS+ Sec. 4 workload shape).
+
+Workload (one step): build the iSAX index of 20,000,000 z-normalised random-walk series of
+length 256 (fp32, w = 16, 8-bit symbols) that are already resident in HBM, then answer exact
+1-NN for 3,000 queries -- 1,000 noisy copies of dataset rows for each noise level
+sigma in {0.01, 0.1, 1.0}. value = queries answered per second of step time (build included).
+
+Prints one JSON line. ``--impl reference`` times the CPU oracle (FP64 brute force with exact
+re-ranking) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact 1-NN queries/s at 20M×256 fp32; build GB/s; LB-scan % of HBM peak"
+SIGMAS = (0.01, 0.1, 1.0)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=20_000_000)
+    p.add_argument("--len", type=int, default=256)
+    p.add_argument("--per-sigma", type=int, default=1000)
+    p.add_argument("--k", type=int, default=1)
+    p.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(n, length, per_sigma, rank, pinned=True):
+    import numpy as np
+    import torch
+
+    import synth
+    host = torch.empty((n, length), dtype=torch.float32, pin_memory=pinned)
+    synth.random_walk(n, length, seed=1 + 1000 * rank, out=host.numpy())
+    q, sig, src = synth.sigma_queries(host.numpy(), n, length, per_sigma, SIGMAS)
+    qhost = torch.from_numpy(np.ascontiguousarray(q))
+    if pinned:
+        qhost = qhost.pin_memory()
+    return host, qhost, sig, src
+
+
+def cpu_baseline(host_np, queries_np, target_s):
+    """The oracle as it stands (FP64 GEMM screening + exact re-rank) on a bounded sample."""
+    import numpy as np
+
+    from oracle import knn as oknn
+    n = host_np.shape[0]
+    per = len(queries_np) // len(SIGMAS)
+    sample_q = queries_np[[0, per, 2 * per]]          # one query per sigma level
+    probe = min(n, 1 << 20)
+    t0 = time.perf_counter()
+    oknn.knn_chunked(lambda a, b: host_np[a:b], probe, sample_q, 1)
+    t_probe = time.perf_counter() - t0
+    rows = int(min(n, max(probe, probe * target_s / max(t_probe, 1e-3))))
+    t0 = time.perf_counter()
+    oknn.knn_chunked(lambda a, b: host_np[a:b], rows, sample_q, 1)
+    t = time.perf_counter() - t0
+    per_query_full = t / len(sample_q) * (n / rows)
+    return {"value": 1.0 / per_query_full, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(sample_q)} queries (one per sigma) over the first {rows} of {n} rows, "
+                      f"time scaled by {n / rows:.3g} to the full collection; {t:.1f} s of CPU work"}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not d:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2009_00166_gb300", "csrc", d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+        return None
+    return float(d["bytes_per_launch"]) * (d.get("scale", 1.0))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+    from oracle import knn as oknn
+    n, length = args.n, args.len
+    host = synth.random_walk(n, length, seed=1)
+    q, _, _ = synth.sigma_queries(host, n, length, args.per_sigma, SIGMAS)
+    per = args.per_sigma
+    sample_q = q[[0, per, 2 * per]]
+    # each step: the three sample queries over a row prefix sized to a few seconds of CPU work
+    probe = min(n, 1 << 19)
+    t0 = time.perf_counter()
+    oknn.knn_chunked(lambda a, b: host[a:b], probe, sample_q, 1)
+    tp = time.perf_counter() - t0
+    rows = int(min(n, max(probe, probe * 8.0 / max(tp, 1e-3))))
+    for _ in range(args.warmup):
+        oknn.knn_chunked(lambda a, b: host[a:b], rows, sample_q[:1], 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oknn.knn_chunked(lambda a, b: host[a:b], rows, sample_q, 1)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    qps = len(sample_q) * args.steps / (t * n / rows)
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps * n / rows,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"exact 1-NN over {n}x{length} random-walk fp32 series, w=16, 8-bit iSAX, "
+                                   f"queries sigma in {list(SIGMAS)}", "n": n, "len": length},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"3 queries (one per sigma) per step over the first {rows} of {n} rows; "
+                                       f"time scaled by {n / rows:.3g} to the full collection"},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import paper_2009_00166_gb300 as P
+    from paper_2009_00166_gb300 import _build
+    if not os.path.exists(P.binding.LIB_PATH):
+        _build.build()
+    n, length, k = args.n, args.len, args.k
+    mode = P.PARIS_MODE_BATCHED if args.mode == "batched" else P.PARIS_MODE_PLAIN
+    host, qhost, sig, _ = make_workload(n, length, args.per_sigma, rank)
+    X = host.to(dev)
+    Q = qhost.to(dev)
+    groups = [Q[i * args.per_sigma:(i + 1) * args.per_sigma] for i in range(len(SIGMAS))]
+    nq = Q.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def step(collect=None):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        idx = P.paris_build(X, 16, 256)
+        e1.record(stream)
+        per_sigma_stats = []
+        for g in groups:
+            out = P.paris_exact_knn_ex(idx, g, k, mode=mode, want_stats=collect is not None)
+            if collect is not None:
+                per_sigma_stats.append(out[2])
+        e2.record(stream)
+        e2.synchronize()
+        idx.free()
+        if collect is not None:
+            collect.append({"build_ms": e0.elapsed_time(e1), "query_ms": e1.elapsed_time(e2),
+                            "stats": per_sigma_stats})
+        return e0.elapsed_time(e2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    launches0 = P.paris_kernel_launches()
+    recs = []
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    launches = P.paris_kernel_launches() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        out_i = torch.empty((nq, k), dtype=torch.int64, pin_memory=True)
+        out_d = torch.empty((nq, k), dtype=torch.float32, pin_memory=True)
+        hq = qhost.numpy()
+        times = []
+        for it in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            idx = P.paris_build(host, 16, 256)                      # host series: copied in by the library
+            for i in range(len(SIGMAS)):
+                sl = slice(i * args.per_sigma, (i + 1) * args.per_sigma)
+                P.paris_exact_knn_ex(idx, qhost[sl], k, out_idx=out_i[sl], out_dist=out_d[sl], mode=mode)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            idx.free()
+        t = sum(times[1:])                                          # first pass warms the allocator
+        e2e = {"value": nq * args.e2e_steps * world / t, "unit": "queries/s",
+               "h2d_bytes_per_step": int(host.numel() * 4 + hq.size * 4),
+               "d2h_bytes_per_step": int(nq * k * 12)}
+        del hq
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel, from the per-phase device times of the timed steps
+    hbm_peak, peak_kind = measured_peaks()
+    steps = len(recs)
+    ph = {"prep": 0.0, "descent": 0.0, "lbscan": 0.0, "refine": 0.0, "select": 0.0}
+    cands = refined = leaf_rows = 0
+    for r in recs:
+        for s in r["stats"]:
+            for key in ph:
+                ph[key] += s["ms_" + key]
+            cands += s["candidates"]
+            refined += s["refined"]
+            leaf_rows += s["leaf_rows"]
+    build_ms = sum(r["build_ms"] for r in recs) / steps
+    query_ms = sum(r["query_ms"] for r in recs) / steps
+    launches_lb = nq * steps
+    lb_bytes = 16.0 * n + 8.0 * cands / launches_lb
+    lb_launch_ms = ph["lbscan"] / launches_lb
+    lb_gbs = lb_bytes / (lb_launch_ms * 1e-3) / 1e9
+    refine_bytes_total = refined * (length * 4.0) + cands * 12.0
+    refine_gbs = refine_bytes_total / (ph["refine"] * 1e-3) / 1e9 if ph["refine"] > 0 else 0.0
+    per_sigma = []
+    for i, s in enumerate(SIGMAS):
+        tot = sum(r["stats"][i]["ms_prep"] + r["stats"][i]["ms_descent"] + r["stats"][i]["ms_lbscan"] +
+                  r["stats"][i]["ms_refine"] + r["stats"][i]["ms_select"] for r in recs)
+        c = sum(r["stats"][i]["candidates"] for r in recs) / (steps * args.per_sigma)
+        per_sigma.append({"sigma": s, "queries_per_s": args.per_sigma * steps / (tot * 1e-3),
+                          "candidates_per_query": c, "pruning_ratio": 1.0 - c / n})
+    dominant = max(ph, key=ph.get)
+    if dominant == "refine":
+        roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel")}
+    else:
+        roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": lb_gbs / hbm_peak, "traffic": traffic_for("lbscan_kernel")}
+    roof["peak_kind"] = peak_kind
+    value = nq * steps * world / (total_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"build + exact {k}-NN, {n}x{length} random-walk fp32 series (w=16, 8-bit iSAX), "
+                               f"{nq} queries = {args.per_sigma} per sigma in {list(SIGMAS)}",
+                   "n": n, "len": length, "w": 16, "card": 256, "k": k, "queries_per_step": nq, "mode": args.mode,
+                   "l2": "inputs larger than L2 (20.5 GB series; 320 MB summaries read per query)",
+                   "parallelism": f"replicas x{world} (independent collections per GPU)"},
+        "roofline": roof,
+        "lb_scan": {"achieved_gbs": lb_gbs, "frac_of_hbm": lb_gbs / hbm_peak, "peak_kind": peak_kind,
+                    "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes},
+        "build": {"ms": build_ms, "gb_per_s": n * length * 4 / (build_ms * 1e-3) / 1e9,
+                  "series_per_s": n / (build_ms * 1e-3)},
+        "query_ms_per_step": query_ms,
+        "phase_ms_per_step": {kk: v / steps for kk, v in ph.items()},
+        "per_sigma": per_sigma,
+        "refine_gbs": refine_gbs,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(host.numpy(), qhost.numpy(), args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

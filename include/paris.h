@@ -1,0 +1,177 @@
+/*
+ * paris.h -- C ABI of a GB300 (sm_103a) implementation of the ParIS+ exact similarity-search
+ * hot path: iSAX index build and exact k-NN query answering over z-normalised fp32 series.
+ *
+ * Paper: B. Peng, P. Fatourou, T. Palpanas, "ParIS+: Data Series Indexing on Multi-Core
+ * Architectures". Section references below are to that paper.
+ *
+ * Conventions for every entry point
+ *   - Returns a paris_status; nothing is thrown across the ABI. On failure a message is kept
+ *     for the calling thread and returned by paris_last_error().
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are stream-ordered
+ *     and return after the work completes unless stated otherwise.
+ *   - "device or host" pointers are classified with cudaPointerGetAttributes; host buffers are
+ *     staged through device memory by the library (pinned host memory copies fastest).
+ *   - All arrays are dense and row-major. Series and queries must be finite fp32 values
+ *     (PARIS_EINVAL otherwise) and are expected to be z-normalised (Sec. 2.1); the library
+ *     does not normalise.
+ *   - Device memory the library needs is taken from the allocator installed with
+ *     paris_set_allocator (default: cudaMallocAsync / cudaFreeAsync on the call's stream).
+ */
+#ifndef PARIS_H
+#define PARIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paris_index paris_index; /* opaque; owned by the caller after paris_build */
+
+typedef enum paris_status {
+  PARIS_OK = 0,
+  PARIS_EINVAL = 1,    /* bad argument (shape, null pointer, non-finite value, k > n ...) */
+  PARIS_ENOMEM = 2,    /* device or host allocation failed */
+  PARIS_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error string) */
+  PARIS_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  PARIS_EINTERNAL = 5, /* an internal capacity was exceeded (message says which) */
+} paris_status;
+
+/* ------------------------------------------------------------------------------------------
+ * Index build (Sec. 2.2 iSAX; Alg. 2 ConvertToSAX; Sec. 3.1-3.2 index construction).
+ *
+ * For each series r: PAA_i = RN64(exact sum of segment i) / (len/w), i < w; iSAX symbol
+ * sym_i = number of breakpoints beta_j = Phi^-1(j/card) (j = 1..card-1) that are <= PAA_i;
+ * SAX[r] = the w symbols (the summary array of Alg. 2, indexed by position); the key is the
+ * bit-plane interleave of the symbols (first plane = first bit of every segment = the ADS+ root
+ * child) and the index orders rows by (top 64 key bits, row). The ADS+ leaves are the runs of
+ * that order sharing a key prefix with at most leaf_capacity rows.
+ *
+ *   series  device or host, [n][len] fp32. Device series are BORROWED: keep them alive and
+ *           unchanged until paris_free (refinement reads them). Host series are copied.
+ *   n       1 <= n < 2^32;  len >= 1;  1 <= w <= 16 with len % w == 0;
+ *   card    alphabet size, a power of two in [2, 256] (256 = 8-bit symbols).
+ *   out     receives the new index; *out is NULL on failure.
+ * ---------------------------------------------------------------------------------------- */
+paris_status paris_build(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
+                         void* stream, paris_index** out);
+
+typedef struct paris_build_opts {
+  int32_t leaf_capacity; /* L: rows per approximate-search leaf; 0 = 2048; max 4096 */
+  int32_t reserved[7];   /* must be zero */
+} paris_build_opts;
+
+/* paris_build with options (opts may be NULL = defaults). */
+paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
+                            const paris_build_opts* opts, void* stream, paris_index** out);
+
+/* Releases the index and everything it owns. NULL-safe. Waits for the index's pending work. */
+void paris_free(paris_index* idx);
+
+/* ------------------------------------------------------------------------------------------
+ * Exact k-NN (Sec. 3.3, Alg. 7-9): approximate search seeds the best-so-far (BSF); a
+ * MINDIST_PAA_iSAX lower-bound scan over every summary keeps the rows that can still beat it
+ * (Alg. 8); the kept rows are refined with early-abandoning Euclidean distance while the BSF
+ * is lowered atomically (Alg. 9). The answer is the exact brute-force answer: the k rows with
+ * the smallest Euclidean distance, ties ordered by the lower row number. Distances are decided
+ * on their exact real values (near ties are re-ranked in exact integer arithmetic).
+ *
+ *   queries   device or host, [nq][len] fp32, len as built.
+ *   nq        >= 0 (0 is a no-op);  1 <= k <= min(n, 1024).
+ *   out_idx   device or host, [nq][k] int64: neighbour rows, ascending (distance, row).
+ *   out_dist  device or host, [nq][k] fp32: their Euclidean distances (may be NULL).
+ * ---------------------------------------------------------------------------------------- */
+paris_status paris_exact_knn(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                             int64_t* out_idx, float* out_dist, void* stream);
+
+enum {
+  PARIS_MODE_PLAIN = 0,   /* one query per lower-bound pass, as in Alg. 7 */
+  PARIS_MODE_BATCHED = 1, /* a tile of queries per pass over the summaries (one read per tile) */
+};
+
+typedef struct paris_query_opts {
+  int32_t mode;        /* PARIS_MODE_*; default PLAIN */
+  int32_t query_tile;  /* queries per pass in BATCHED mode; 0 = pick automatically */
+  int32_t chunk;       /* queries whose candidate lists are resident at once; 0 = automatic */
+  int32_t reserved[5]; /* must be zero */
+} paris_query_opts;
+
+typedef struct paris_query_stats {
+  int64_t candidates;  /* rows kept by the lower-bound scans (sum over queries) */
+  int64_t refined;     /* candidates whose distance was computed to the end */
+  int64_t contenders;  /* rows re-ranked exactly */
+  int64_t leaf_rows;   /* rows visited by the approximate searches */
+  double ms_prep, ms_descent, ms_lbscan, ms_refine, ms_select; /* device time per phase */
+} paris_query_stats;
+
+/* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */
+paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, int64_t nq,
+                                int32_t k, int64_t* out_idx, float* out_dist,
+                                const paris_query_opts* opts, paris_query_stats* stats,
+                                void* stream);
+
+/* Number of GPU kernels the library has launched since it was loaded (all threads). */
+uint64_t paris_kernel_launches(void);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* paris_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Memory: route the library's device allocations through the caller (e.g. a framework's
+ * caching allocator). alloc returns NULL on failure. Passing NULL functions restores the
+ * default. Not thread-safe with respect to concurrent library calls.
+ * ---------------------------------------------------------------------------------------- */
+typedef void* (*paris_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*paris_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+paris_status paris_set_allocator(paris_alloc_fn alloc, paris_free_fn free_fn, void* ctx);
+
+/* ------------------------------------------------------------------------------------------
+ * Inspection and step-level entry points: the same kernels the build and query paths run,
+ * exposed so each step can be checked on its own.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct paris_index_view {
+  int64_t n;
+  int32_t len, w, card, leaf_capacity;
+  const float* series;          /* device [n][len] */
+  const uint64_t* keys_sorted;  /* device [n]: top 64 key bits in index order */
+  const uint32_t* rows_sorted;  /* device [n]: rows in index order (key, row) */
+} paris_index_view;
+
+paris_status paris_index_describe(const paris_index* idx, paris_index_view* out);
+
+/* Breakpoints beta_1..beta_{card-1} = Phi^-1(j/card) as FP64 (Wichura's AS241, 1988), host. */
+paris_status paris_breakpoints(int32_t card, double* out_host);
+
+/* The index's summary array as plain symbols, device [n][w] uint8 (Alg. 2: SAX[r]). */
+paris_status paris_export_sax(const paris_index* idx, uint8_t* out_sax, void* stream);
+
+/* The index order (Sec. 3.1-3.2 leaves as runs of the key order): keys_sorted (top 64 key bits)
+ * and rows_sorted, copied to caller buffers (device or host, [n] each; either may be NULL). */
+paris_status paris_export_order(const paris_index* idx, uint64_t* out_keys, uint32_t* out_rows,
+                                void* stream);
+
+/* Encode without building: device [n][len] series -> device SAX [n][w] uint8, device keys [n]
+ * (top 64 interleaved key bits), and, if out_paa is not NULL, device PAA [n][w] FP64. */
+paris_status paris_encode(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
+                          uint8_t* out_sax, uint64_t* out_key64, double* out_paa, void* stream);
+
+/* Approximate search alone (Sec. 3.3): per query, the sorted-position range [lo, hi) of its
+ * leaf (device or host [nq][2] int64) and the seed -- the k-th smallest fp32 squared distance
+ * among the leaf rows (device or host [nq] fp32, may be NULL). */
+paris_status paris_approx_search(const paris_index* idx, const float* queries, int64_t nq,
+                                 int32_t k, int64_t* out_leaf, float* out_seed_sq, void* stream);
+
+/* Lower-bound scan alone (Alg. 8) for one query against a squared threshold: every row whose
+ * conservative fp32 MINDIST^2 lower bound is <= threshold_sq is kept. Writes up to `capacity`
+ * (row, lb_sq) pairs in no particular order to out_rows/out_lb (device) and the number of kept
+ * rows (which may exceed capacity) to *out_count (host). */
+paris_status paris_lb_scan(const paris_index* idx, const float* query, float threshold_sq,
+                           uint32_t* out_rows, float* out_lb, int64_t capacity, int64_t* out_count,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARIS_H */

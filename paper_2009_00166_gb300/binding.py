@@ -1,0 +1,277 @@
+"""ctypes marshalling for ``libparis.so`` (declarations in ``include/paris.h``)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libparis.so")
+
+PARIS_MODE_PLAIN = 0
+PARIS_MODE_BATCHED = 1
+
+_STATUS = {0: "PARIS_OK", 1: "PARIS_EINVAL", 2: "PARIS_ENOMEM", 3: "PARIS_ECUDA", 4: "PARIS_ETIMEOUT",
+           5: "PARIS_EINTERNAL"}
+
+
+class ParisError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("leaf_capacity", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class QueryOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("query_tile", C.c_int32), ("chunk", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("candidates", C.c_int64), ("refined", C.c_int64), ("contenders", C.c_int64),
+                ("leaf_rows", C.c_int64), ("ms_prep", C.c_double), ("ms_descent", C.c_double),
+                ("ms_lbscan", C.c_double), ("ms_refine", C.c_double), ("ms_select", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class IndexView(C.Structure):
+    _fields_ = [("n", C.c_int64), ("len", C.c_int32), ("w", C.c_int32), ("card", C.c_int32),
+                ("leaf_capacity", C.c_int32), ("series", C.c_void_p), ("keys_sorted", C.c_void_p),
+                ("rows_sorted", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libparis.so``; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libparis.so is missing ({LIB_PATH}); run paper_2009_00166_gb300._build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, F32, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_void_p
+        sig = {
+            "paris_build": ([P, I64, I32, I32, I32, VP, C.POINTER(VP)], I32),
+            "paris_build_ex": ([P, I64, I32, I32, I32, C.POINTER(BuildOpts), VP, C.POINTER(VP)], I32),
+            "paris_free": ([VP], None),
+            "paris_exact_knn": ([VP, P, I64, I32, P, P, VP], I32),
+            "paris_exact_knn_ex": ([VP, P, I64, I32, P, P, C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
+            "paris_last_error": ([], C.c_char_p),
+            "paris_kernel_launches": ([], C.c_uint64),
+            "paris_set_allocator": ([ALLOC_FN, FREE_FN, VP], I32),
+            "paris_index_describe": ([VP, C.POINTER(IndexView)], I32),
+            "paris_breakpoints": ([I32, P], I32),
+            "paris_export_sax": ([VP, P, VP], I32),
+            "paris_encode": ([P, I64, I32, I32, I32, P, P, P, VP], I32),
+            "paris_export_order": ([VP, P, P, VP], I32),
+            "paris_approx_search": ([VP, P, I64, I32, P, P, VP], I32),
+            "paris_lb_scan": ([VP, P, F32, P, P, I64, C.POINTER(I64), VP], I32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def paris_kernel_launches() -> int:
+    return int(lib().paris_kernel_launches())
+
+
+def paris_last_error() -> str:
+    return lib().paris_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise ParisError(status, paris_last_error())
+
+
+def _ptr(t) -> int | None:
+    """Address of a torch tensor (device or host) or numpy array; None for None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+        return t.data_ptr()
+    import numpy as np
+    a = t
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _stream(stream) -> int | None:
+    import torch
+    if stream is None:
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+@dataclass
+class ParisIndex:
+    """Handle returned by paris_build; keeps the borrowed series tensor alive."""
+    handle: int
+    n: int
+    len: int
+    w: int
+    card: int
+    series: object = None
+
+    def free(self):
+        if self.handle:
+            lib().paris_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def paris_build_ex(series, w: int = 16, card: int = 256, leaf_capacity: int = 0, stream=None) -> ParisIndex:
+    """paris_build_ex: series is a contiguous [n][len] float32 tensor (device: borrowed; host: copied)."""
+    n, length = int(series.shape[0]), int(series.shape[1])
+    opts = BuildOpts(leaf_capacity=leaf_capacity)
+    out = C.c_void_p()
+    _check(lib().paris_build_ex(_ptr(series), n, length, w, card, C.byref(opts), _stream(stream), C.byref(out)))
+    return ParisIndex(out.value, n, length, w, card, series)
+
+
+def paris_build(series, w: int = 16, card: int = 256, stream=None) -> ParisIndex:
+    return paris_build_ex(series, w, card, 0, stream)
+
+
+def paris_free(index: ParisIndex):
+    index.free()
+
+
+def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, mode: int = PARIS_MODE_PLAIN,
+                       query_tile: int = 0, chunk: int = 0, want_stats: bool = False, stream=None):
+    """paris_exact_knn_ex: returns (idx [nq][k] int64, dist [nq][k] float32[, stats dict]).
+
+    Outputs are allocated like the queries (same device) when not given.
+    """
+    import torch
+    nq = int(queries.shape[0])
+    dev = queries.device if hasattr(queries, "device") else torch.device("cpu")
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk)
+    stats = QueryStats()
+    _check(lib().paris_exact_knn_ex(index.handle, _ptr(queries), nq, k, _ptr(out_idx), _ptr(out_dist),
+                                    C.byref(opts), C.byref(stats) if want_stats else None, _stream(stream)))
+    if want_stats:
+        return out_idx, out_dist, stats.as_dict()
+    return out_idx, out_dist
+
+
+def paris_exact_knn(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, stream=None):
+    return paris_exact_knn_ex(index, queries, k, out_idx, out_dist, stream=stream)
+
+
+def paris_index_describe(index: ParisIndex) -> dict:
+    v = IndexView()
+    _check(lib().paris_index_describe(index.handle, C.byref(v)))
+    return {f: getattr(v, f) for f, _ in v._fields_}
+
+
+def paris_breakpoints(card: int):
+    import numpy as np
+    out = np.empty(card - 1, dtype=np.float64)
+    _check(lib().paris_breakpoints(card, out.ctypes.data))
+    return out
+
+
+def paris_export_sax(index: ParisIndex, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty((index.n, index.w), dtype=torch.uint8, device="cuda")
+    _check(lib().paris_export_sax(index.handle, _ptr(out), _stream(stream)))
+    return out
+
+
+def paris_export_order(index: ParisIndex):
+    """paris_export_order into host arrays: (keys_sorted uint64 [n], rows_sorted int64 [n])."""
+    import numpy as np
+    keys = np.empty(index.n, np.uint64)
+    rows = np.empty(index.n, np.uint32)
+    _check(lib().paris_export_order(index.handle, keys.ctypes.data, rows.ctypes.data, _stream(None)))
+    return keys, rows.astype(np.int64)
+
+
+def paris_encode(series, w: int = 16, card: int = 256, want_paa: bool = False, stream=None):
+    """paris_encode on a device [n][len] float32 tensor: (sax [n][w] uint8, key64 [n] int64 bits[, paa])."""
+    import torch
+    n, length = int(series.shape[0]), int(series.shape[1])
+    sax = torch.empty((n, w), dtype=torch.uint8, device=series.device)
+    key = torch.empty((n,), dtype=torch.int64, device=series.device)
+    paa = torch.empty((n, w), dtype=torch.float64, device=series.device) if want_paa else None
+    _check(lib().paris_encode(_ptr(series), n, length, w, card, _ptr(sax), _ptr(key), _ptr(paa), _stream(stream)))
+    return (sax, key, paa) if want_paa else (sax, key)
+
+
+def paris_approx_search(index: ParisIndex, queries, k: int = 1, stream=None):
+    """paris_approx_search: (leaf [nq][2] int64 sorted-position ranges, seed [nq] float32)."""
+    import torch
+    nq = int(queries.shape[0])
+    leaf = torch.empty((nq, 2), dtype=torch.int64, device=queries.device)
+    seed = torch.empty((nq,), dtype=torch.float32, device=queries.device)
+    _check(lib().paris_approx_search(index.handle, _ptr(queries), nq, k, _ptr(leaf), _ptr(seed), _stream(stream)))
+    return leaf, seed
+
+
+def paris_lb_scan(index: ParisIndex, query, threshold_sq: float, capacity: int | None = None, stream=None):
+    """paris_lb_scan: (rows uint32-as-int64 [m], lb [m] float32, total count) for one query."""
+    import torch
+    cap = index.n if capacity is None else capacity
+    rows = torch.empty((max(cap, 1),), dtype=torch.int32, device="cuda")
+    lbs = torch.empty((max(cap, 1),), dtype=torch.float32, device="cuda")
+    cnt = C.c_int64()
+    _check(lib().paris_lb_scan(index.handle, _ptr(query), C.c_float(threshold_sq), _ptr(rows), _ptr(lbs), cap,
+                               C.byref(cnt), _stream(stream)))
+    m = min(cnt.value, cap)
+    return rows[:m].to(torch.int64) & 0xFFFFFFFF, lbs[:m], cnt.value
+
+
+_alloc_keepalive = []
+
+
+def paris_set_allocator(alloc_fn, free_fn, ctx=None):
+    """Install ctypes-compatible allocation callbacks (or None, None for the default)."""
+    if alloc_fn is None:
+        _check(lib().paris_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+    a, f = ALLOC_FN(alloc_fn), FREE_FN(free_fn)
+    _alloc_keepalive[:] = [a, f]
+    _check(lib().paris_set_allocator(a, f, ctx))
+
+
+def use_torch_allocator():
+    """Route the library's device scratch through PyTorch's caching allocator."""
+    import torch
+
+    def _a(nbytes, stream, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _f(ptr, _nbytes, _stream, _ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    paris_set_allocator(_a, _f)

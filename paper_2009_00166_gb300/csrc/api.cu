@@ -1,0 +1,570 @@
+// C ABI of the GB300 ParIS+ library: argument checking, memory, staging and orchestration of
+// the build (encode -> sort) and query (prep -> approximate search -> LB scan -> refine ->
+// select/re-rank) kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
+#include <new>
+#include <string>
+
+#include "query.cuh"
+
+namespace paris {
+
+namespace {
+thread_local std::string g_err;
+paris_alloc_fn g_alloc = nullptr;
+paris_free_fn g_free = nullptr;
+void* g_ctx = nullptr;
+}  // namespace
+
+paris_status fail(paris_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+void clear_error() { g_err.clear(); }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void note_launches(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+  if (g_alloc) return g_alloc(bytes, st, g_ctx);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  if (g_free) {
+    g_free(p, bytes, st, g_ctx);
+    return;
+  }
+  cudaFreeAsync(p, st);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace paris
+
+using namespace paris;
+
+namespace {
+
+float gamma_scale(int len) {
+  // (1 + gamma) / (1 - gamma) with gamma = gamma_{len+2} = m u / (1 - m u), u = 2^-24, rounded up
+  double m = (double)len + 2.0, u = std::ldexp(1.0, -24);
+  double g = m * u / (1.0 - m * u);
+  double cg = (1.0 + g) / (1.0 - g) * (1.0 + std::ldexp(1.0, -20));
+  return std::nextafter((float)cg, INFINITY);
+}
+
+paris_status check_status_word(const uint32_t* dev_status, cudaStream_t st, const char* what) {
+  uint32_t s = 0;
+  PARIS_CUDA(cudaMemcpyAsync(&s, dev_status, sizeof s, cudaMemcpyDeviceToHost, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  if (s & DEV_NONFINITE) return fail(PARIS_EINVAL, "%s: input holds a NaN or infinite value", what);
+  if (s & DEV_CONT_OVERFLOW)
+    return fail(PARIS_EINTERNAL, "%s: more than %d rows tie with the k-th neighbour within the fp32 bound",
+                what, kContCap);
+  if (s & DEV_CAND_OVERFLOW) return fail(PARIS_EINTERNAL, "%s: candidate list overflow", what);
+  if (s & DEV_TIMEOUT) return fail(PARIS_ETIMEOUT, "%s: a device-side wait expired", what);
+  return PARIS_OK;
+}
+
+bool valid_card(int card) { return card >= 2 && card <= 256 && (card & (card - 1)) == 0; }
+
+paris_status upload_breakpoints(paris_index* idx, cudaStream_t st) {
+  idx->beta_host = normal_breakpoints(idx->card);
+  std::vector<uint64_t> keys;
+  std::vector<double> ext;
+  breakpoint_tables(idx->beta_host, keys, ext);
+  idx->beta_keys = (uint64_t*)dev_alloc(keys.size() * 8, st);
+  idx->beta_ext = (double*)dev_alloc(ext.size() * 8, st);
+  if (!idx->beta_keys || !idx->beta_ext) return fail(PARIS_ENOMEM, "breakpoint tables");
+  PARIS_CUDA(cudaMemcpyAsync(idx->beta_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, st));
+  PARIS_CUDA(cudaMemcpyAsync(idx->beta_ext, ext.data(), ext.size() * 8, cudaMemcpyHostToDevice, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));  // host vectors die with this scope
+  return PARIS_OK;
+}
+
+void release_index(paris_index* idx) {
+  if (!idx) return;
+  cudaStream_t st = nullptr;
+  dev_free(idx->series_owned, idx->series_owned_bytes, st);
+  dev_free(idx->sax, (size_t)idx->n * PARIS_SAX_BYTES, st);
+  dev_free(idx->keys_sorted, (size_t)idx->n * 8, st);
+  dev_free(idx->rows_sorted, (size_t)idx->n * 4, st);
+  dev_free(idx->beta_keys, (size_t)(idx->card - 1) * 8, st);
+  dev_free(idx->beta_ext, (size_t)(idx->card + 1) * 8, st);
+  delete idx;
+}
+
+// A device view of a caller buffer that may live on the host (staged through device memory).
+struct Staged {
+  DevBuf buf;
+  void* dev = nullptr;
+  void* host = nullptr;
+  size_t bytes = 0;
+  paris_status in(const void* p, size_t b, cudaStream_t st) {
+    bytes = b;
+    if (is_device_ptr(p)) {
+      dev = const_cast<void*>(p);
+      return PARIS_OK;
+    }
+    if (!buf.alloc(b, st)) return fail(PARIS_ENOMEM, "staging %zu bytes", b);
+    dev = buf.p;
+    PARIS_CUDA(cudaMemcpyAsync(dev, p, b, cudaMemcpyHostToDevice, st));
+    return PARIS_OK;
+  }
+  paris_status out(void* p, size_t b, cudaStream_t st) {
+    bytes = b;
+    if (!p) return PARIS_OK;
+    if (is_device_ptr(p)) {
+      dev = p;
+      return PARIS_OK;
+    }
+    if (!buf.alloc(b, st)) return fail(PARIS_ENOMEM, "staging %zu bytes", b);
+    dev = buf.p;
+    host = p;
+    return PARIS_OK;
+  }
+  paris_status finish(cudaStream_t st) {
+    if (host) PARIS_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
+    return PARIS_OK;
+  }
+};
+
+// Per-phase device time: events recorded on the call's stream, summed once the call is done,
+// so that timing adds no host synchronisation inside the call.
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[5];
+  explicit PhaseTimer(bool enable, cudaStream_t s) : on(enable), st(s) {}
+  void begin(int phase) {
+    if (!on) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    ev[phase].push_back({a, b});
+  }
+  void end(int phase) {
+    if (on) cudaEventRecord(ev[phase].back().second, st);
+  }
+  void collect(double* out5) {
+    for (int p = 0; p < 5; ++p) {
+      for (auto& e : ev[p]) {
+        float ms = 0.f;
+        cudaEventSynchronize(e.second);
+        cudaEventElapsedTime(&ms, e.first, e.second);
+        if (out5) out5[p] += ms;
+      }
+    }
+  }
+  ~PhaseTimer() {
+    for (auto& v : ev)
+      for (auto& e : v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* paris_last_error(void) { return g_err.c_str(); }
+
+uint64_t paris_kernel_launches(void) { return launch_count(); }
+
+paris_status paris_set_allocator(paris_alloc_fn alloc, paris_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(PARIS_EINVAL, "paris_set_allocator: give both functions or neither");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_ctx = ctx;
+  return PARIS_OK;
+}
+
+paris_status paris_breakpoints(int32_t card, double* out_host) {
+  clear_error();
+  if (!valid_card(card)) return fail(PARIS_EINVAL, "card must be a power of two in [2, 256], got %d", card);
+  if (!out_host) return fail(PARIS_EINVAL, "out_host is NULL");
+  std::vector<double> b = normal_breakpoints(card);
+  std::memcpy(out_host, b.data(), b.size() * sizeof(double));
+  return PARIS_OK;
+}
+
+static paris_status check_shape(int64_t n, int32_t len, int32_t w, int32_t card) {
+  if (n < 1 || n > 0xffffffffll) return fail(PARIS_EINVAL, "n must be in [1, 2^32), got %lld", (long long)n);
+  if (len < 1) return fail(PARIS_EINVAL, "len must be >= 1, got %d", len);
+  if (w < 1 || w > 16) return fail(PARIS_EINVAL, "w must be in [1, 16], got %d", w);
+  if (len % w) return fail(PARIS_EINVAL, "len (%d) must be a multiple of w (%d)", len, w);
+  if (!valid_card(card)) return fail(PARIS_EINVAL, "card must be a power of two in [2, 256], got %d", card);
+  if ((int64_t)len / w > 65536) return fail(PARIS_EINVAL, "segments longer than 65536 points are not supported");
+  return PARIS_OK;
+}
+
+paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
+                            const paris_build_opts* opts, void* stream, paris_index** out) {
+  clear_error();
+  if (!out) return fail(PARIS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!series) return fail(PARIS_EINVAL, "series is NULL");
+  PARIS_TRY(check_shape(n, len, w, card));
+  int leaf = opts && opts->leaf_capacity ? opts->leaf_capacity : 2048;
+  if (leaf < 1 || leaf > kMaxLeaf) return fail(PARIS_EINVAL, "leaf_capacity must be in [1, %d]", kMaxLeaf);
+  if (opts)
+    for (int i = 0; i < 7; ++i)
+      if (opts->reserved[i]) return fail(PARIS_EINVAL, "paris_build_opts.reserved must be zero");
+  cudaStream_t st = (cudaStream_t)stream;
+  paris_index* idx = new (std::nothrow) paris_index();
+  if (!idx) return fail(PARIS_ENOMEM, "index object");
+  idx->n = n;
+  idx->len = len;
+  idx->w = w;
+  idx->card = card;
+  idx->bits = __builtin_ctz((unsigned)card);
+  idx->leaf_cap = leaf;
+  cudaGetDevice(&idx->device);
+  auto bail = [&](paris_status s) {
+    cudaStreamSynchronize(st);
+    release_index(idx);
+    return s;
+  };
+  const size_t series_bytes = (size_t)n * len * sizeof(float);
+  if (is_device_ptr(series)) {
+    idx->series = series;
+  } else {
+    idx->series_owned = dev_alloc(series_bytes, st);
+    if (!idx->series_owned) return bail(fail(PARIS_ENOMEM, "device copy of the series (%zu bytes)", series_bytes));
+    idx->series_owned_bytes = series_bytes;
+    if (cudaMemcpyAsync(idx->series_owned, series, series_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return bail(fail(PARIS_ECUDA, "copying the series to the device"));
+    idx->series = (const float*)idx->series_owned;
+  }
+  paris_status s = upload_breakpoints(idx, st);
+  if (s != PARIS_OK) return bail(s);
+  idx->sax = (uint8_t*)dev_alloc((size_t)n * PARIS_SAX_BYTES, st);
+  idx->keys_sorted = (uint64_t*)dev_alloc((size_t)n * 8, st);
+  idx->rows_sorted = (uint32_t*)dev_alloc((size_t)n * 4, st);
+  DevBuf status;
+  if (!idx->sax || !idx->keys_sorted || !idx->rows_sorted || !status.alloc(4, st))
+    return bail(fail(PARIS_ENOMEM, "index arrays for %lld series", (long long)n));
+  if (cudaMemsetAsync(status.p, 0, 4, st) != cudaSuccess) return bail(fail(PARIS_ECUDA, "memset"));
+  RowShape sh = make_row_shape(len, w, idx->series);
+  s = launch_encode(idx->series, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr, idx->keys_sorted,
+                    nullptr, status.as<uint32_t>(), st);
+  if (s != PARIS_OK) return bail(s);
+  s = radix_sort_index(idx->keys_sorted, idx->rows_sorted, n, st);
+  if (s != PARIS_OK) return bail(s);
+  s = check_status_word(status.as<uint32_t>(), st, "paris_build");
+  if (s != PARIS_OK) return bail(s);
+  *out = idx;
+  return PARIS_OK;
+}
+
+paris_status paris_build(const float* series, int64_t n, int32_t len, int32_t w, int32_t card, void* stream,
+                         paris_index** out) {
+  return paris_build_ex(series, n, len, w, card, nullptr, stream, out);
+}
+
+void paris_free(paris_index* idx) {
+  if (!idx) return;
+  cudaDeviceSynchronize();
+  release_index(idx);
+  cudaDeviceSynchronize();
+}
+
+paris_status paris_index_describe(const paris_index* idx, paris_index_view* out) {
+  clear_error();
+  if (!idx || !out) return fail(PARIS_EINVAL, "NULL argument");
+  out->n = idx->n;
+  out->len = idx->len;
+  out->w = idx->w;
+  out->card = idx->card;
+  out->leaf_capacity = idx->leaf_cap;
+  out->series = idx->series;
+  out->keys_sorted = idx->keys_sorted;
+  out->rows_sorted = idx->rows_sorted;
+  return PARIS_OK;
+}
+
+paris_status paris_export_sax(const paris_index* idx, uint8_t* out_sax, void* stream) {
+  clear_error();
+  if (!idx || !out_sax) return fail(PARIS_EINVAL, "NULL argument");
+  if (!is_device_ptr(out_sax)) return fail(PARIS_EINVAL, "out_sax must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  PARIS_TRY(launch_unrotate_sax(idx->sax, idx->n, idx->w, out_sax, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  return PARIS_OK;
+}
+
+paris_status paris_export_order(const paris_index* idx, uint64_t* out_keys, uint32_t* out_rows, void* stream) {
+  clear_error();
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (out_keys) PARIS_CUDA(cudaMemcpyAsync(out_keys, idx->keys_sorted, (size_t)idx->n * 8, cudaMemcpyDefault, st));
+  if (out_rows) PARIS_CUDA(cudaMemcpyAsync(out_rows, idx->rows_sorted, (size_t)idx->n * 4, cudaMemcpyDefault, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  return PARIS_OK;
+}
+
+paris_status paris_encode(const float* series, int64_t n, int32_t len, int32_t w, int32_t card, uint8_t* out_sax,
+                          uint64_t* out_key64, double* out_paa, void* stream) {
+  clear_error();
+  if (!series || !out_sax || !out_key64) return fail(PARIS_EINVAL, "NULL argument");
+  PARIS_TRY(check_shape(n, len, w, card));
+  if (!is_device_ptr(series) || !is_device_ptr(out_sax) || !is_device_ptr(out_key64) ||
+      (out_paa && !is_device_ptr(out_paa)))
+    return fail(PARIS_EINVAL, "paris_encode takes device pointers");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> beta = normal_breakpoints(card);
+  std::vector<uint64_t> keys;
+  std::vector<double> ext;
+  breakpoint_tables(beta, keys, ext);
+  DevBuf bk, rot, status;
+  if (!bk.alloc(keys.size() * 8 + 8, st) || !rot.alloc((size_t)n * PARIS_SAX_BYTES, st) || !status.alloc(4, st))
+    return fail(PARIS_ENOMEM, "encode scratch");
+  PARIS_CUDA(cudaMemcpyAsync(bk.p, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, st));
+  PARIS_CUDA(cudaMemsetAsync(status.p, 0, 4, st));
+  RowShape sh = make_row_shape(len, w, series);
+  PARIS_TRY(launch_encode(series, n, sh, card, __builtin_ctz((unsigned)card), bk.as<uint64_t>(), rot.as<uint8_t>(),
+                          out_sax, out_key64, out_paa, status.as<uint32_t>(), st));
+  return check_status_word(status.as<uint32_t>(), st, "paris_encode");
+}
+
+// Allocates the per-call query state for nq queries.
+static paris_status alloc_query_state(const paris_index* idx, int64_t nq, int k, const float* dq, QueryState& qs,
+                                      DevBuf& block, cudaStream_t st) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  size_t o_paa = take((size_t)nq * 16 * 8), o_key = take((size_t)nq * 8),
+         o_tab = take((size_t)nq * idx->card * 16 * 4), o_thr = take((size_t)nq * 4), o_bsf = take((size_t)nq * 8),
+         o_leaf = take((size_t)nq * 16), o_seed = take((size_t)nq * 4), o_stat = take(4), o_cnt = take(4 * 8);
+  if (!block.alloc(off, st)) return fail(PARIS_ENOMEM, "query state (%zu bytes)", off);
+  char* b = block.as<char>();
+  qs.nq = nq;
+  qs.k = k;
+  qs.queries = dq;
+  qs.qpaa = (double*)(b + o_paa);
+  qs.qkey = (uint64_t*)(b + o_key);
+  qs.qtable = (float*)(b + o_tab);
+  qs.thr = (uint32_t*)(b + o_thr);
+  qs.bsf = (unsigned long long*)(b + o_bsf);
+  qs.leaf = (int64_t*)(b + o_leaf);
+  qs.seed = (float*)(b + o_seed);
+  qs.status = (uint32_t*)(b + o_stat);
+  qs.counters = (unsigned long long*)(b + o_cnt);
+  qs.cg = gamma_scale(idx->len);
+  PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
+  PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+  return PARIS_OK;
+}
+
+static paris_status check_query_args(const paris_index* idx, const float* queries, int64_t nq, int32_t k) {
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  if (nq < 0) return fail(PARIS_EINVAL, "nq must be >= 0");
+  if (nq > 0 && !queries) return fail(PARIS_EINVAL, "queries is NULL");
+  if (k < 1 || k > 1024 || (int64_t)k > idx->n)
+    return fail(PARIS_EINVAL, "k must be in [1, min(n, 1024)], got %d (n = %lld)", k, (long long)idx->n);
+  return PARIS_OK;
+}
+
+paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                                int64_t* out_idx, float* out_dist, const paris_query_opts* opts,
+                                paris_query_stats* stats, void* stream) {
+  clear_error();
+  PARIS_TRY(check_query_args(idx, queries, nq, k));
+  if (nq > 0 && !out_idx) return fail(PARIS_EINVAL, "out_idx is NULL");
+  paris_query_opts o{};
+  if (opts) o = *opts;
+  for (int i = 0; i < 5; ++i)
+    if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.mode != PARIS_MODE_PLAIN && o.mode != PARIS_MODE_BATCHED)
+    return fail(PARIS_EINVAL, "unknown mode %d", o.mode);
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (nq == 0) return PARIS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t qbytes = (size_t)nq * idx->len * sizeof(float);
+  Staged sq, si, sd;
+  PARIS_TRY(sq.in(queries, qbytes, st));
+  PARIS_TRY(si.out(out_idx, (size_t)nq * k * sizeof(int64_t), st));
+  PARIS_TRY(sd.out(out_dist, (size_t)nq * k * sizeof(float), st));
+  QueryState qs;
+  DevBuf qblock;
+  PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
+  PhaseTimer timer(stats != nullptr, st);
+  timer.begin(0);
+  PARIS_TRY(launch_query_prep(idx, qs, st));
+  timer.end(0);
+  timer.begin(1);
+  PARIS_TRY(launch_descent(idx, qs, st));
+  timer.end(1);
+  // chunks of queries whose candidate lists are resident together
+  const int64_t cap = idx->n;
+  int64_t qc = o.chunk;
+  if (qc <= 0) {
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    double budget = std::min((double)freeb * 0.25, 8.0e9);
+    qc = (int64_t)(budget / ((double)cap * 12.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0));
+    qc = std::max<int64_t>(1, std::min<int64_t>(qc, 1024));
+  }
+  qc = std::min(qc, nq);
+  DevBuf cblock;
+  ChunkState cs;
+  {
+    size_t off = 0;
+    auto take = [&](size_t b) {
+      size_t o2 = off;
+      off += (b + 255) & ~(size_t)255;
+      return o2;
+    };
+    size_t o_count = take((size_t)qc * 4), o_rows = take((size_t)qc * cap * 4), o_lb = take((size_t)qc * cap * 4),
+           o_F = take((size_t)qc * cap * 4), o_pre = take((size_t)(qc + 1) * 4), o_kth = take((size_t)qc * 4),
+           o_hist = take((size_t)qc * 2048 * 4), o_sel = take((size_t)qc * 8), o_cc = take((size_t)qc * 4),
+           o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4);
+    if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
+    char* b = cblock.as<char>();
+    cs.cap = cap;
+    cs.count = (uint32_t*)(b + o_count);
+    cs.rows = (uint32_t*)(b + o_rows);
+    cs.lb = (float*)(b + o_lb);
+    cs.F = (float*)(b + o_F);
+    cs.prefix = (uint32_t*)(b + o_pre);
+    cs.kth = (uint32_t*)(b + o_kth);
+    cs.sel_hist = (uint32_t*)(b + o_hist);
+    cs.sel_state = (uint32_t*)(b + o_sel);
+    cs.cont_count = (uint32_t*)(b + o_cc);
+    cs.cont_rows = (uint32_t*)(b + o_cr);
+    cs.cont_limbs = (uint32_t*)(b + o_cl);
+  }
+  for (int64_t q0 = 0; q0 < nq; q0 += qc) {
+    cs.q0 = q0;
+    cs.qc = (int)std::min<int64_t>(qc, nq - q0);
+    PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
+    timer.begin(2);
+    for (int j = 0; j < cs.qc; ++j)
+      PARIS_TRY(launch_lbscan(idx, qs, q0 + j, cs.count + j, cs.rows + (int64_t)j * cap, cs.lb + (int64_t)j * cap,
+                              cap, st));
+    timer.end(2);
+    timer.begin(3);
+    PARIS_TRY(launch_refine(idx, qs, cs, st));
+    timer.end(3);
+    timer.begin(4);
+    PARIS_TRY(launch_select(idx, qs, cs, (int64_t*)si.dev, (float*)sd.dev, st));
+    timer.end(4);
+  }
+  PARIS_TRY(si.finish(st));
+  PARIS_TRY(sd.finish(st));
+  PARIS_TRY(check_status_word(qs.status, st, "paris_exact_knn"));
+  if (stats) {
+    double ms[5] = {0, 0, 0, 0, 0};
+    timer.collect(ms);
+    stats->ms_prep = ms[0];
+    stats->ms_descent = ms[1];
+    stats->ms_lbscan = ms[2];
+    stats->ms_refine = ms[3];
+    stats->ms_select = ms[4];
+    unsigned long long c[4];
+    PARIS_CUDA(cudaMemcpyAsync(c, qs.counters, sizeof c, cudaMemcpyDeviceToHost, st));
+    PARIS_CUDA(cudaStreamSynchronize(st));
+    stats->candidates = (int64_t)c[0];
+    stats->refined = (int64_t)c[1];
+    stats->contenders = (int64_t)c[2];
+    stats->leaf_rows = (int64_t)c[3];
+  }
+  return PARIS_OK;
+}
+
+paris_status paris_exact_knn(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                             int64_t* out_idx, float* out_dist, void* stream) {
+  return paris_exact_knn_ex(idx, queries, nq, k, out_idx, out_dist, nullptr, nullptr, stream);
+}
+
+paris_status paris_approx_search(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                                 int64_t* out_leaf, float* out_seed_sq, void* stream) {
+  clear_error();
+  PARIS_TRY(check_query_args(idx, queries, nq, k));
+  if (nq == 0) return PARIS_OK;
+  if (!out_leaf) return fail(PARIS_EINVAL, "out_leaf is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sq, sl, ss;
+  PARIS_TRY(sq.in(queries, (size_t)nq * idx->len * 4, st));
+  PARIS_TRY(sl.out(out_leaf, (size_t)nq * 16, st));
+  PARIS_TRY(ss.out(out_seed_sq, (size_t)nq * 4, st));
+  QueryState qs;
+  DevBuf qblock;
+  PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
+  PARIS_TRY(launch_query_prep(idx, qs, st));
+  PARIS_TRY(launch_descent(idx, qs, st));
+  PARIS_CUDA(cudaMemcpyAsync(sl.dev, qs.leaf, (size_t)nq * 16, cudaMemcpyDeviceToDevice, st));
+  if (out_seed_sq) PARIS_CUDA(cudaMemcpyAsync(ss.dev, qs.seed, (size_t)nq * 4, cudaMemcpyDeviceToDevice, st));
+  PARIS_TRY(sl.finish(st));
+  PARIS_TRY(ss.finish(st));
+  return check_status_word(qs.status, st, "paris_approx_search");
+}
+
+paris_status paris_lb_scan(const paris_index* idx, const float* query, float threshold_sq, uint32_t* out_rows,
+                           float* out_lb, int64_t capacity, int64_t* out_count, void* stream) {
+  clear_error();
+  PARIS_TRY(check_query_args(idx, query, 1, 1));
+  if (!out_count || capacity < 0 || (capacity > 0 && (!out_rows || !out_lb)))
+    return fail(PARIS_EINVAL, "bad output arguments");
+  if (capacity > 0 && (!is_device_ptr(out_rows) || !is_device_ptr(out_lb)))
+    return fail(PARIS_EINVAL, "out_rows/out_lb must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sq;
+  PARIS_TRY(sq.in(query, (size_t)idx->len * 4, st));
+  QueryState qs;
+  DevBuf qblock, cnt;
+  PARIS_TRY(alloc_query_state(idx, 1, 1, (const float*)sq.dev, qs, qblock, st));
+  if (!cnt.alloc(4, st)) return fail(PARIS_ENOMEM, "counter");
+  PARIS_CUDA(cudaMemsetAsync(cnt.p, 0, 4, st));
+  PARIS_TRY(launch_query_prep(idx, qs, st));
+  PARIS_TRY(launch_lbscan_threshold(idx, qs.qtable, threshold_sq, cnt.as<uint32_t>(), out_rows, out_lb, capacity,
+                                    qs.status, st));
+  uint32_t c = 0;
+  PARIS_CUDA(cudaMemcpyAsync(&c, cnt.p, 4, cudaMemcpyDeviceToHost, st));
+  paris_status s = check_status_word(qs.status, st, "paris_lb_scan");
+  *out_count = c;
+  if (s == PARIS_EINTERNAL) return PARIS_OK;  // overflow of the caller's capacity is reported by the count
+  return s;
+}
+
+}  // extern "C"

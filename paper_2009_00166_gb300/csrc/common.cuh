@@ -1,0 +1,305 @@
+// Device-side building blocks shared by the build and query kernels of the GB300 ParIS+ path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PARIS_FULL_MASK 0xffffffffu
+#define PARIS_SAX_BYTES 16  // one summary slot per row: up to 16 segments of 8 bits
+
+namespace paris {
+
+// Device status word bits (written with atomicOr, read back by the host after a call).
+enum : uint32_t {
+  DEV_NONFINITE = 1u,      // a NaN or infinite input value
+  DEV_CAND_OVERFLOW = 2u,  // a candidate list overflowed its capacity
+  DEV_CONT_OVERFLOW = 4u,  // too many exact-re-rank contenders
+  DEV_TIMEOUT = 8u,        // a bounded wait expired
+};
+
+__device__ __forceinline__ uint64_t double_order_key(double v) {
+  // Monotone map of IEEE doubles to unsigned integers (-0 normalised to +0 first).
+  uint64_t u = (uint64_t)__double_as_longlong(v == 0.0 ? 0.0 : v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// RN64(S) * 2^e for a signed 64-bit integer S, built bit by bit (round to nearest even).
+// Requires the result to be a normal double (|S| * 2^e within [2^-1022, 2^1023]).
+__device__ __forceinline__ double fixed_to_double(int64_t S, int e) {
+  if (S == 0) return 0.0;
+  uint64_t sign = S < 0 ? 0x8000000000000000ull : 0ull;
+  uint64_t m = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
+  int p = 63 - __clzll((long long)m);  // position of the leading one
+  uint64_t mant;
+  if (p <= 52) {
+    mant = m << (52 - p);
+  } else {
+    int sh = p - 52;
+    mant = m >> sh;
+    uint64_t rem = m & ((1ull << sh) - 1ull);
+    uint64_t half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      mant += 1ull;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        p += 1;
+      }
+    }
+  }
+  uint64_t biased = (uint64_t)(p + e + 1023);
+  return __longlong_as_double((long long)(sign | (biased << 52) | (mant & ((1ull << 52) - 1ull))));
+}
+
+// --- exact wide accumulator: 320-bit two's complement, least significant bit 2^-149 --------
+// Holds any exact sum of up to 2^16 finite fp32 values (|sum| < 2^144).
+struct Wide {
+  uint32_t limb[10];
+};
+
+__device__ __forceinline__ void wide_zero(Wide& a) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) a.limb[i] = 0u;
+}
+
+__device__ __forceinline__ void wide_add_f32(Wide& a, float x) {
+  uint32_t u = __float_as_uint(x);
+  uint32_t be = (u >> 23) & 0xffu;
+  uint32_t mant = (u & 0x7fffffu) | (be ? 0x800000u : 0u);
+  if (mant == 0u) return;
+  int off = (be ? (int)be : 1) - 150 + 149;  // bit offset of the mantissa's unit in the limbs
+  int li = off >> 5, sh = off & 31;
+  uint64_t v = (uint64_t)mant << sh;  // < 2^55
+  uint32_t part[3] = {(uint32_t)v, (uint32_t)(v >> 32), 0u};
+  if (!(u >> 31)) {
+    uint64_t carry = 0;
+    for (int i = li; i < 10; ++i) {
+      uint64_t t = (uint64_t)a.limb[i] + (i - li < 3 ? part[i - li] : 0u) + carry;
+      a.limb[i] = (uint32_t)t;
+      carry = t >> 32;
+      if (i - li >= 2 && carry == 0) break;
+    }
+  } else {
+    uint64_t borrow = 0;
+    for (int i = li; i < 10; ++i) {
+      uint64_t sub = (uint64_t)(i - li < 3 ? part[i - li] : 0u) + borrow;
+      uint64_t cur = a.limb[i];
+      a.limb[i] = (uint32_t)(cur - sub);
+      borrow = cur < sub ? 1 : 0;
+      if (i - li >= 2 && borrow == 0) break;
+    }
+  }
+}
+
+// Correctly rounded (nearest even) FP64 value of the accumulator.
+__device__ __forceinline__ double wide_to_double(const Wide& a0) {
+  Wide a = a0;
+  bool neg = (a.limb[9] >> 31) != 0u;
+  if (neg) {  // two's complement negate
+    uint64_t carry = 1;
+    for (int i = 0; i < 10; ++i) {
+      uint64_t t = (uint64_t)(~a.limb[i]) + carry;
+      a.limb[i] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+  int top = -1;
+  for (int i = 9; i >= 0; --i)
+    if (a.limb[i]) {
+      top = i;
+      break;
+    }
+  if (top < 0) return 0.0;
+  int p = top * 32 + (31 - __clz(a.limb[top]));  // leading one position
+  // gather bits [p-63, p] into a 64-bit window and a sticky flag for the rest
+  auto bit_window = [&](int lo) -> uint64_t {  // 64 bits starting at bit `lo` (may be < 0)
+    uint64_t r = 0;
+    for (int b = 0; b < 64; b += 32) {
+      int pos = lo + b;  // fetch 32 bits at pos
+      uint32_t w32;
+      if (pos >= 0) {
+        int li = pos >> 5, sh = pos & 31;
+        uint32_t lo32 = li < 10 ? a.limb[li] : 0u;
+        uint32_t hi32 = li + 1 < 10 ? a.limb[li + 1] : 0u;
+        w32 = sh ? (lo32 >> sh) | (hi32 << (32 - sh)) : lo32;
+      } else if (pos > -32) {
+        w32 = a.limb[0] << (-pos);
+      } else {
+        w32 = 0u;
+      }
+      r |= (uint64_t)w32 << b;
+    }
+    return r;
+  };
+  int lo = p - 63;
+  uint64_t win = bit_window(lo);  // bit 63 of win is the leading one
+  bool sticky = false;
+  if (lo > 0) {
+    for (int i = 0; i < 10 && !sticky; ++i) {
+      int b0 = i * 32;
+      if (b0 >= lo) break;
+      uint32_t m = a.limb[i];
+      if (b0 + 32 > lo) m &= (1u << (lo - b0)) - 1u;
+      sticky = m != 0u;
+    }
+  }
+  uint64_t mant = win >> 11;  // 53 bits
+  uint64_t rest = win & 0x7ffull;
+  // round to nearest, ties to even: above half, or exactly half with an odd last bit
+  bool up = (rest > 0x400ull) || (rest == 0x400ull && (sticky || (mant & 1ull)));
+  if (up) {
+    mant += 1ull;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      p += 1;
+    }
+  }
+  int e = p - 149;  // value = 1.mant * 2^(p-149)
+  uint64_t biased = (uint64_t)(e + 1023);
+  return __longlong_as_double(
+      (long long)((neg ? 0x8000000000000000ull : 0ull) | (biased << 52) | (mant & ((1ull << 52) - 1ull))));
+}
+
+// --- fixed-point conversion for the fast exact path ------------------------------------------
+// x as an integer multiple of 2^lambda; sets `inexact` if x has bits below 2^lambda.
+__device__ __forceinline__ int64_t to_fixed(float x, int lambda, bool& inexact) {
+  uint32_t u = __float_as_uint(x);
+  uint32_t be = (u >> 23) & 0xffu;
+  uint32_t mant = (u & 0x7fffffu) | (be ? 0x800000u : 0u);
+  int e_lsb = (be ? (int)be : 1) - 150;
+  int sh = e_lsb - lambda;
+  if (mant == 0u) return 0;
+  if (sh < 0) {
+    inexact = true;
+    return 0;
+  }
+  int64_t v = (int64_t)((uint64_t)mant << sh);
+  return (u >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ int64_t shfl_xor_i64(int64_t v, int off) {
+  return (int64_t)__shfl_xor_sync(PARIS_FULL_MASK, (long long)v, off);
+}
+__device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
+  return (int64_t)__shfl_sync(PARIS_FULL_MASK, (long long)v, src);
+}
+
+// Number of breakpoints <= v (upper region on ties): binary search over order keys.
+__device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, int card) {
+  uint64_t key = double_order_key(v);
+  int lo = 0, cnt = card - 1;  // upper_bound over beta_keys[0, card-1)
+  while (cnt > 0) {
+    int half = cnt >> 1;
+    if (beta_keys[lo + half] <= key) {
+      lo += half + 1;
+      cnt -= half + 1;
+    } else {
+      cnt = half;
+    }
+  }
+  return lo;
+}
+
+struct RowShape {
+  int len, w, s, log2s;  // log2s = -1 when s is not a power of two
+  int fast;              // 1: vectorised fixed-point path applies
+};
+
+// Exact PAA of one row (Sec. 2.2), computed by a whole warp. On return lane i < w holds
+// PAA_i = RN64(exact sum of segment i) / s. Returns false if the row holds a NaN or infinity.
+// The fast path keeps the row in registers as fixed-point integers scaled by a per-row power
+// of two; rows with values too small for that scale take the exact wide-accumulator path.
+template <int ITERS>
+__device__ __forceinline__ bool warp_row_paa(const float* __restrict__ row, const RowShape& sh,
+                                             int lane, double& paa_out) {
+  const int len = sh.len, w = sh.w, s = sh.s;
+  bool finite = true;
+  if (sh.fast) {
+    float4 v[ITERS];
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t) {
+      int i4 = lane + 32 * t;
+      if (4 * i4 < len)
+        v[t] = __ldcs(reinterpret_cast<const float4*>(row) + i4);
+      else
+        v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    uint32_t emax = 1;
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t) {
+      uint32_t e0 = (__float_as_uint(v[t].x) >> 23) & 0xffu, e1 = (__float_as_uint(v[t].y) >> 23) & 0xffu;
+      uint32_t e2 = (__float_as_uint(v[t].z) >> 23) & 0xffu, e3 = (__float_as_uint(v[t].w) >> 23) & 0xffu;
+      emax = max(emax, max(max(e0, e1), max(e2, e3)));
+    }
+    emax = __reduce_max_sync(PARIS_FULL_MASK, emax);
+    if (emax == 255u) return false;
+    // sums of <= s values below 2^(emax-126) stay below 2^63 * 2^lambda
+    const int lambda = (int)emax - 126 + sh.log2s - 63;
+    bool inexact = false;
+    int64_t part[ITERS];
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t)
+      part[t] = to_fixed(v[t].x, lambda, inexact) + to_fixed(v[t].y, lambda, inexact) +
+                to_fixed(v[t].z, lambda, inexact) + to_fixed(v[t].w, lambda, inexact);
+    if (!__any_sync(PARIS_FULL_MASK, inexact)) {
+      const int g = s >> 2;  // lanes per segment within one 128-value sweep
+#pragma unroll
+      for (int t = 0; t < ITERS; ++t)
+        for (int off = g >> 1; off > 0; off >>= 1) part[t] += shfl_xor_i64(part[t], off);
+      // lane i collects segment i: sweep t holds segments t*(32/g) + lane/g in lanes (.)*g
+      const int per = 32 / g;
+      int64_t mine = 0;
+#pragma unroll
+      for (int t = 0; t < ITERS; ++t) {
+        int64_t val = shfl_i64(part[t], (lane % per) * g);
+        if (lane / per == t) mine = val;
+      }
+      paa_out = fixed_to_double(mine, lambda - sh.log2s);  // s is a power of two here
+      (void)w;
+      return true;
+    }
+    // fall through to the exact wide path for this row
+  }
+  // general path: lane i < w sums its own segment exactly
+  double r = 0.0;
+  bool bad = false;
+  if (lane < w) {
+    Wide acc;
+    wide_zero(acc);
+    const float* p = row + (int64_t)lane * s;
+    for (int j = 0; j < s; ++j) {
+      float x = p[j];
+      if (((__float_as_uint(x) >> 23) & 0xffu) == 0xffu) bad = true;
+      wide_add_f32(acc, x);
+    }
+    double S = wide_to_double(acc);
+    r = sh.log2s >= 0 ? S * (1.0 / (double)(1 << sh.log2s)) : __ddiv_rn(S, (double)s);
+  }
+  finite = !__any_sync(PARIS_FULL_MASK, bad);
+  paa_out = r;
+  return finite;
+}
+
+// Bit-plane interleaved key (top 64 bits): plane j = bit (bits-1-j) of segments 0..w-1.
+// Every lane must call; lane i < w passes its symbol.
+__device__ __forceinline__ uint64_t warp_key64(int sym, int lane, int w, int bits) {
+  uint64_t hi = 0, lo = 0;  // 128-bit key, filled from the top
+  int filled = 0;
+  for (int j = 0; j < bits; ++j) {
+    int b = bits - 1 - j;
+    uint32_t m = __ballot_sync(PARIS_FULL_MASK, lane < w && ((sym >> b) & 1));
+    uint64_t plane = (uint64_t)(__brev(m) >> (32 - w));  // segment 0 first
+    // shift the 128-bit (hi, lo) left by w and or in the plane
+    hi = (hi << w) | (lo >> (64 - w));
+    lo = (lo << w) | plane;
+    filled += w;
+  }
+  // left-align the filled bits within 128
+  int sh = 128 - filled;
+  if (sh >= 64) {
+    hi = lo << (sh - 64);
+  } else if (sh > 0) {
+    hi = (hi << sh) | (lo >> (64 - sh));
+  }
+  return hi;
+}
+
+}  // namespace paris

@@ -1,0 +1,852 @@
+// Query-path kernels: query preparation, approximate search, lower-bound scan with compaction,
+// early-abandoning refinement with an atomic best-so-far, k-th selection and exact re-rank
+// (ParIS+ Sec. 3.3, Alg. 7-9).
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "query.cuh"
+
+namespace paris {
+
+namespace {
+
+constexpr float kKeepScale = 1.0f - 1.0f / 65536.0f;  // LB^2 * (1 - 2^-16): fp32 LB error margin
+constexpr int kDescentThreads = 256;
+constexpr int kLbThreads = 512;
+constexpr int kLbUnroll = 4;
+constexpr int kRefineThreads = 256;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(PARIS_FULL_MASK, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+__device__ __forceinline__ uint32_t up_scaled_bits(float f, float cg) {
+  return __float_as_uint(__fmul_ru(f, cg));
+}
+
+// Query vector of one warp: lane holds float4 number lane + 32 t (vector path) .
+template <int ITERS>
+struct QVec {
+  float4 v[ITERS];
+  __device__ __forceinline__ void load(const float* q, int len, int lane) {
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t) {
+      int i4 = lane + 32 * t;
+      v[t] = (4 * i4 < len) ? reinterpret_cast<const float4*>(q)[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+};
+
+__device__ __forceinline__ float sq4(float4 a, float4 b, float acc) {
+  float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+  acc = fmaf(d0, d0, acc);
+  acc = fmaf(d1, d1, acc);
+  acc = fmaf(d2, d2, acc);
+  acc = fmaf(d3, d3, acc);
+  return acc;
+}
+
+// fp32 squared Euclidean distance of one row to the warp's query, abandoning (returning +inf)
+// once a prefix sum exceeds `abandon` (Alg. 9 refinement with early abandoning).
+template <int ITERS>
+__device__ __forceinline__ float warp_sq_dist_vec(const float* __restrict__ x, const QVec<ITERS>& q,
+                                                  int len, int lane, float abandon) {
+  constexpr int CH = ITERS >= 4 ? ITERS / 4 : 1;  // sweeps between abandon checks
+  float acc = 0.f;
+#pragma unroll
+  for (int t0 = 0; t0 < ITERS; t0 += CH) {
+    float4 xv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      int i4 = lane + 32 * (t0 + c);
+      xv[c] = (4 * i4 < len) ? __ldcs(reinterpret_cast<const float4*>(x) + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc = sq4(xv[c], q.v[t0 + c], acc);
+    if (t0 + CH < ITERS) {
+      float part = warp_sum(acc);
+      if (part > abandon) return CUDART_INF_F;
+    }
+  }
+  float tot = warp_sum(acc);
+  return tot > abandon ? CUDART_INF_F : tot;
+}
+
+__device__ __forceinline__ float warp_sq_dist_scalar(const float* __restrict__ x, const float* __restrict__ q,
+                                                     int len, int lane, float abandon) {
+  float acc = 0.f;
+  for (int j = lane; j < len; j += 32) {
+    float d = x[j] - q[j];
+    acc = fmaf(d, d, acc);
+  }
+  float tot = warp_sum(acc);
+  return tot > abandon ? CUDART_INF_F : tot;
+}
+
+// ------------------------------------------------------------------------------ query prep
+// PAA, symbols and key of each query (as in the build), and its lower-bound table:
+// T[c][i] = (len/w) * d_i(c)^2, d_i(c) = distance from PAA_i to the interval of symbol c
+// (Sec. 3.3.1: ABOVE / BELOW / IN), shrunk by a bound on the FP64 rounding of both PAA values
+// and rounded down to fp32, so that every table sum stays below the exact MINDIST^2.
+template <int ITERS>
+__global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ queries, int64_t nq, RowShape sh,
+                                                   int card, int bits, const uint64_t* __restrict__ beta_keys_g,
+                                                   const double* __restrict__ beta_ext, double* __restrict__ qpaa,
+                                                   uint64_t* __restrict__ qkey, float* __restrict__ qtable,
+                                                   uint32_t* __restrict__ status) {
+  __shared__ uint64_t beta_keys[255];
+  for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const double scale = (double)(sh.len / sh.w);
+  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += warps) {
+    double paa = 0.0;
+    bool ok = warp_row_paa<ITERS>(queries + q * (int64_t)sh.len, sh, lane, paa);
+    if (!ok && lane == 0) atomicOr(status, DEV_NONFINITE);
+    int sym = lane < sh.w ? symbol_of(paa, beta_keys, card) : 0;
+    uint64_t key = warp_key64(sym, lane, sh.w, bits);
+    if (lane < 16) qpaa[q * 16 + lane] = lane < sh.w ? paa : 0.0;
+    if (lane == 0) qkey[q] = key;
+    const int i = lane & 15;
+    const double P = __shfl_sync(PARIS_FULL_MASK, paa, i);
+    float* T = qtable + q * (int64_t)card * 16;
+    for (int e = lane; e < card * 16; e += 32) {
+      int c = e >> 4;
+      float val = 0.f;
+      if (i < sh.w) {
+        double lo = beta_ext[c], hi = beta_ext[c + 1];
+        double d = 0.0;
+        if (P < lo) d = lo - P;
+        else if (P > hi) d = P - hi;
+        double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
+        d = fmax(0.0, d - mag * 0x1p-50);
+        val = __double2float_rd(scale * d * d);
+      }
+      T[e] = val;
+    }
+  }
+}
+
+// --------------------------------------------------------------------- approximate search
+__device__ int64_t cta_lower_bound(const uint64_t* __restrict__ keys, int64_t n, uint64_t x,
+                                   int64_t* s_bounds) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_bounds[0] = 0;
+    s_bounds[1] = n;
+  }
+  __syncthreads();
+  while (true) {
+    int64_t lo = s_bounds[0], hi = s_bounds[1];
+    if (hi - lo <= kDescentThreads) break;
+    int64_t p = lo + ((hi - lo) * (t + 1)) / (kDescentThreads + 1);
+    int pred = keys[p] < x;
+    int cnt = __syncthreads_count(pred);
+    if (t == cnt - 1) s_bounds[0] = p + 1;
+    if (t == cnt) s_bounds[1] = p;
+    __syncthreads();
+  }
+  int64_t lo = s_bounds[0], hi = s_bounds[1];
+  int pred = (lo + t < hi) && keys[lo + t] < x;
+  int cnt = __syncthreads_count(pred);
+  return lo + cnt;
+}
+
+__device__ __forceinline__ int smem_lower_bound(const uint64_t* a, int m, uint64_t x) {
+  int lo = 0;
+  while (m > 0) {
+    int h = m >> 1;
+    if (a[lo + h] < x) {
+      lo += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return lo;
+}
+__device__ __forceinline__ int smem_upper_bound(const uint64_t* a, int m, uint64_t x) {
+  int lo = 0;
+  while (m > 0) {
+    int h = m >> 1;
+    if (a[lo + h] <= x) {
+      lo += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return lo;
+}
+
+// One CTA per query: find the leaf of the fixed-order trie that holds the query key's
+// position (Sec. 3.3 approximate search), compute the distance to every series in it and
+// seed the best-so-far with the k-th smallest.
+template <int ITERS>
+__global__ void __launch_bounds__(kDescentThreads) descent_kernel(
+    const float* __restrict__ series, int64_t n, int len, int vec, const uint64_t* __restrict__ keys,
+    const uint32_t* __restrict__ rows_sorted, int leaf_cap, int k, const float* __restrict__ queries,
+    const uint64_t* __restrict__ qkey, int64_t* __restrict__ leaf_out, float* __restrict__ seed_out,
+    uint32_t* __restrict__ thr, unsigned long long* __restrict__ bsf, float cg,
+    unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) uint64_t s_buf[];
+  __shared__ int64_t s_bounds[2];
+  __shared__ int64_t s_lo[65], s_hi[65];
+  __shared__ int s_best;
+  __shared__ int64_t s_leaf[2];
+  const int64_t q = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint64_t x = qkey[q];
+  const int Lp = max(leaf_cap, k);
+
+  int64_t pos0 = cta_lower_bound(keys, n, x, s_bounds);
+  const bool clamped = pos0 >= n;
+  const int64_t pos = clamped ? n - 1 : pos0;
+  const uint64_t anchor = keys[pos];
+  const int64_t wa = max((int64_t)0, pos - Lp), wb = min(n, pos + Lp + 1);
+  const int wn = (int)(wb - wa);
+  for (int i = t; i < wn; i += blockDim.x) s_buf[i] = keys[wa + i];
+  if (t == 0) s_best = 65;
+  __syncthreads();
+  if (t <= 64) {
+    uint64_t mask = t == 0 ? 0ull : (~0ull << (64 - t));
+    int64_t lo = wa + smem_lower_bound(s_buf, wn, anchor & mask);
+    int64_t hi = wa + smem_upper_bound(s_buf, wn, anchor | ~mask);
+    bool inside = !(lo == wa && wa > 0) && !(hi == wb && wb < n);
+    s_lo[t] = lo;
+    s_hi[t] = hi;
+    if (inside && hi - lo <= Lp) atomicMin(&s_best, t);
+  }
+  __syncthreads();
+  int best = s_best;
+  int64_t lo, hi;
+  if (best <= 64) {
+    lo = s_lo[best];
+    hi = s_hi[best];
+    if (hi - lo < k) {
+      lo = min(lo, n - k);
+      hi = lo + k;
+    }
+  } else {
+    // even the full key is shared by more than Lp rows: take the first Lp rows of that run
+    int64_t start = clamped ? cta_lower_bound(keys, n, anchor, s_bounds) : pos;
+    lo = start;
+    hi = start + Lp;
+  }
+  __syncthreads();  // s_buf (window) is reused below
+  const int m = (int)(hi - lo);
+  int P2 = 1;
+  while (P2 < m) P2 <<= 1;
+  const float* qp = queries + q * (int64_t)len;
+  QVec<ITERS> qv;
+  if (vec) qv.load(qp, len, lane);
+  for (int i = warp; i < P2; i += blockDim.x >> 5) {
+    if (i < m) {
+      uint32_t row = rows_sorted[lo + i];
+      const float* xr = series + (int64_t)row * len;
+      float F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, CUDART_INF_F)
+                    : warp_sq_dist_scalar(xr, qp, len, lane, CUDART_INF_F);
+      if (lane == 0) s_buf[i] = ((unsigned long long)__float_as_uint(F) << 32) | row;
+    } else if (lane == 0) {
+      s_buf[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  // bitonic sort of (F, row) pairs, ascending
+  for (int size = 2; size <= P2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = t; i < (P2 >> 1); i += blockDim.x) {
+        int p = 2 * i - (i & (stride - 1));
+        int r = p + stride;
+        bool asc = (p & size) == 0;
+        uint64_t a = s_buf[p], b = s_buf[r];
+        if ((a > b) == asc) {
+          s_buf[p] = b;
+          s_buf[r] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (t == 0) {
+    uint64_t kth = s_buf[k - 1];
+    float Fk = __uint_as_float((uint32_t)(kth >> 32));
+    leaf_out[2 * q] = lo;
+    leaf_out[2 * q + 1] = hi;
+    seed_out[q] = Fk;
+    thr[q] = up_scaled_bits(Fk, cg);
+    bsf[q] = s_buf[0];
+    atomicAdd(&counters[3], (unsigned long long)m);
+  }
+}
+
+// ------------------------------------------------------------------ lower-bound scan (Alg. 8)
+// One pass over the summary array for one query. Each lane owns one row of a 32-row group;
+// the table is stored twice, symbol-major, so that the 16 lookups of a row never collide in
+// a shared-memory bank: row r keeps its symbols rotated by r mod 16 (build), so at step k the
+// 16 lanes of a half-warp read 16 different segments, and the two half-warps read different
+// copies. A byte permute forms each lookup address from the symbol byte and a per-lane offset.
+__global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
+    const uint4* __restrict__ sax, int64_t n, const float* __restrict__ table, int card,
+    const uint32_t* __restrict__ thr_ptr, float thr_value, uint32_t* __restrict__ count,
+    uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap,
+    uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) float s_tab[];
+  for (int e = threadIdx.x; e < card * 16; e += blockDim.x) {
+    float v = table[e];
+    int c = e >> 4, i = e & 15;
+    s_tab[c * 64 + i] = v;
+    s_tab[c * 64 + 16 + i] = v;
+  }
+  __syncthreads();
+  const float thr = thr_ptr ? __uint_as_float(*thr_ptr) : thr_value;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t offp[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    uint32_t o0 = 4u * (16u * (lane >> 4) + ((2 * m + lane) & 15));
+    uint32_t o1 = 4u * (16u * (lane >> 4) + ((2 * m + 1 + lane) & 15));
+    offp[m] = o0 | (o1 << 16);
+  }
+  const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
+  const int64_t groups = (n + 31) >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t it = gw * kLbUnroll; it < groups; it += W * kLbUnroll) {
+    uint4 word[kLbUnroll];
+#pragma unroll
+    for (int u = 0; u < kLbUnroll; ++u) {
+      int64_t row = (it + u) * 32 + lane;
+      word[u] = (row < n) ? __ldcs(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kLbUnroll; ++u) {
+      const uint32_t wv[4] = {word[u].x, word[u].y, word[u].z, word[u].w};
+      float lb = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
+        uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
+        float v;
+        asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+        lb += v;
+      }
+      const int64_t row = (it + u) * 32 + lane;
+      const bool keep = row < n && lb * kKeepScale <= thr;
+      const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
+      if (mk) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(mk));
+        base = __shfl_sync(PARIS_FULL_MASK, base, 0);
+        if (keep) {
+          uint32_t p = base + __popc(mk & lt_mask);
+          if ((int64_t)p < cap) {
+            out_rows[p] = (uint32_t)row;
+            out_lb[p] = lb;
+          } else {
+            atomicOr(status, DEV_CAND_OVERFLOW);
+          }
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------- refinement (Alg. 9)
+__global__ void chunk_prefix_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap,
+                                    uint32_t* __restrict__ prefix, unsigned long long* __restrict__ counters) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    uint64_t acc = 0, raw = 0;
+    for (int j = 0; j < qc; ++j) {
+      prefix[j] = (uint32_t)acc;
+      uint64_t c = count[j];
+      raw += c;
+      acc += c < (uint64_t)cap ? c : (uint64_t)cap;
+    }
+    prefix[qc] = (uint32_t)acc;
+    atomicAdd(&counters[0], (unsigned long long)raw);
+  }
+}
+
+// Warps take equal contiguous slices of the chunk's flattened candidate lists; each candidate
+// is re-tested against the current BSF threshold, then refined with early abandoning; a
+// completed distance lowers the query's BSF (k = 1: packed atomicMin; k <= 32: through a
+// warp-private top-k whose k-th value bounds the query's k-th best).
+template <int ITERS>
+__global__ void __launch_bounds__(kRefineThreads) refine_kernel(
+    const float* __restrict__ series, int len, int vec, const float* __restrict__ queries, int64_t q0,
+    int qc, int64_t cap, const uint32_t* __restrict__ prefix, const uint32_t* __restrict__ rows,
+    const float* __restrict__ lbs, float* __restrict__ Fout, uint32_t* __restrict__ thr,
+    unsigned long long* __restrict__ bsf, int k, float cg, unsigned long long* __restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t total = prefix[qc];
+  const int64_t per = (total + W - 1) / W;
+  const int64_t start = gw * per, end = min(total, start + per);
+  int cur = -1;
+  int64_t next_bound = 0;
+  QVec<ITERS> qv;
+  const float* qp = nullptr;
+  float best = CUDART_INF_F;  // lane j < have: j-th best completed F of this warp and query
+  int have = 0;
+  unsigned long long done = 0;
+  for (int64_t item = start; item < end; ++item) {
+    if (cur < 0 || item >= next_bound) {
+      if (cur < 0) {
+        int lo = 0, hi = qc;  // last j with prefix[j] <= item
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if ((int64_t)prefix[mid] <= item) lo = mid; else hi = mid;
+        }
+        cur = lo;
+      } else {
+        while ((int64_t)prefix[cur + 1] <= item) ++cur;
+      }
+      next_bound = prefix[cur + 1];
+      qp = queries + (q0 + cur) * (int64_t)len;
+      if (vec) qv.load(qp, len, lane);
+      best = CUDART_INF_F;
+      have = 0;
+    }
+    const int64_t qi = q0 + cur;
+    const int64_t slot = (int64_t)cur * cap + (item - prefix[cur]);
+    const uint32_t row = rows[slot];
+    const float lbv = lbs[slot];
+    const float t = __uint_as_float(ld_volatile_u32(thr + qi));
+    float F = CUDART_INF_F;
+    if (lbv * kKeepScale <= t) {
+      const float* xr = series + (int64_t)row * len;
+      F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, t) : warp_sq_dist_scalar(xr, qp, len, lane, t);
+    }
+    if (lane == 0) Fout[slot] = F;
+    if (F <= t) {
+      ++done;
+      if (k == 1) {
+        if (lane == 0) {
+          atomicMin(bsf + qi, ((unsigned long long)__float_as_uint(F) << 32) | row);
+          atomicMin(thr + qi, up_scaled_bits(F, cg));
+        }
+      } else if (k <= 32) {
+        uint32_t le = __ballot_sync(PARIS_FULL_MASK, lane < have && best <= F);
+        int p = __popc(le);
+        if (p < k) {
+          float prev = __shfl_up_sync(PARIS_FULL_MASK, best, 1);
+          if (lane == p) best = F;
+          else if (lane > p && lane < k) best = prev;
+          have = min(have + 1, k);
+          if (have == k) {
+            float kth = __shfl_sync(PARIS_FULL_MASK, best, k - 1);
+            uint32_t nb = up_scaled_bits(kth, cg);
+            if (lane == 0 && nb < __float_as_uint(t)) atomicMin(thr + qi, nb);
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0 && done) atomicAdd(&counters[1], done);
+}
+
+// ------------------------------------------------------------- k-th selection and re-rank
+// Radix selection of the k-th smallest F (as fp32 bits, all non-negative) per query.
+__global__ void select_init_kernel(uint32_t* sel_state, uint32_t* hist, int qc, int k) {
+  int j = blockIdx.x;
+  if (threadIdx.x == 0) {
+    sel_state[2 * j] = 0u;
+    sel_state[2 * j + 1] = (uint32_t)k;
+  }
+  for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[(int64_t)j * 2048 + b] = 0u;
+}
+
+__global__ void select_hist_kernel(const float* __restrict__ F, const uint32_t* __restrict__ count,
+                                   int64_t cap, const uint32_t* __restrict__ sel_state,
+                                   uint32_t* __restrict__ hist, int round) {
+  __shared__ uint32_t h[2048];
+  const int j = blockIdx.y;
+  for (int b = threadIdx.x; b < 2048; b += blockDim.x) h[b] = 0u;
+  __syncthreads();
+  const int shift = round == 0 ? 21 : (round == 1 ? 10 : 0);
+  const int width = round == 2 ? 10 : 11;
+  const uint32_t prefix = sel_state[2 * j];
+  const int hs = shift + width;  // bits at and above hs are decided
+  int64_t m = count[j];
+  if (m > cap) m = cap;
+  const float* f = F + (int64_t)j * cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t b = __float_as_uint(f[i]);
+    if (hs >= 32 || (b >> hs) == (prefix >> hs)) atomicAdd(&h[(b >> shift) & ((1u << width) - 1u)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 2048; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[(int64_t)j * 2048 + b], h[b]);
+}
+
+__global__ void select_pick_kernel(uint32_t* __restrict__ hist, uint32_t* __restrict__ sel_state,
+                                   uint32_t* __restrict__ kth, int round) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_found[2];
+  const int j = blockIdx.x;
+  const int shift = round == 0 ? 21 : (round == 1 ? 10 : 0);
+  uint32_t* h = hist + (int64_t)j * 2048;
+  if (threadIdx.x == 0) {
+    s_found[0] = 0u;
+    s_found[1] = 0u;
+  }
+  // each of 256 threads owns 8 consecutive bins
+  uint32_t v[8], tot = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    v[b] = h[threadIdx.x * 8 + b];
+    tot += v[b];
+  }
+  // inclusive prefix over threads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(PARIS_FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w2 = 0; w2 < warp; ++w2) before += s_warp[w2];
+  uint32_t excl = before + x - tot;
+  const uint32_t rank = sel_state[2 * j + 1];  // 1-based rank still to find
+  if (excl < rank && rank <= excl + tot) {
+    uint32_t c = excl;
+    for (int b = 0; b < 8; ++b) {
+      if (c + v[b] >= rank) {
+        s_found[0] = (uint32_t)(threadIdx.x * 8 + b);
+        s_found[1] = c;
+        break;
+      }
+      c += v[b];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t d = s_found[0];
+    sel_state[2 * j] |= d << shift;
+    sel_state[2 * j + 1] = rank - s_found[1];
+    if (round == 2) kth[j] = sel_state[2 * j];
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 2048; b += blockDim.x) h[b] = 0u;
+}
+
+__global__ void kth_from_bsf_kernel(const unsigned long long* __restrict__ bsf, int64_t q0, int qc,
+                                    uint32_t* __restrict__ kth) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < qc) kth[j] = (uint32_t)(bsf[q0 + j] >> 32);
+}
+
+// Rows whose fp32 distance cannot be separated from the k-th best by the fp32 error bound.
+__global__ void contenders_kernel(const float* __restrict__ F, const uint32_t* __restrict__ rows,
+                                  const uint32_t* __restrict__ count, int64_t cap,
+                                  const uint32_t* __restrict__ kth, float cg, uint32_t* __restrict__ cont_count,
+                                  uint32_t* __restrict__ cont_rows, uint32_t* __restrict__ status) {
+  const int j = blockIdx.y;
+  int64_t m = count[j];
+  if (m > cap) m = cap;
+  const float Tc = __fmul_ru(__uint_as_float(kth[j]), cg);
+  const float* f = F + (int64_t)j * cap;
+  const uint32_t* r = rows + (int64_t)j * cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (f[i] <= Tc) {
+      uint32_t p = atomicAdd(&cont_count[j], 1u);
+      if (p < (uint32_t)kContCap) cont_rows[(int64_t)j * kContCap + p] = r[i];
+      else atomicOr(status, DEV_CONT_OVERFLOW);
+    }
+  }
+}
+
+// Adds (hi:lo) * 2^off into a little-endian limb array.
+__device__ __forceinline__ void limbs_add_u128(uint32_t* acc, uint64_t lo, uint64_t hi, int off) {
+  const int li = off >> 5, sh = off & 31;
+  uint32_t p[4] = {(uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32)};
+  uint32_t s[5];
+  if (sh == 0) {
+    s[0] = p[0]; s[1] = p[1]; s[2] = p[2]; s[3] = p[3]; s[4] = 0u;
+  } else {
+    s[0] = p[0] << sh;
+#pragma unroll
+    for (int m = 1; m < 4; ++m) s[m] = (p[m] << sh) | (p[m - 1] >> (32 - sh));
+    s[4] = p[3] >> (32 - sh);
+  }
+  uint64_t carry = 0;
+  for (int m = li; m < kLimbs; ++m) {
+    uint64_t add = (m - li < 5) ? s[m - li] : 0u;
+    uint64_t tsum = (uint64_t)acc[m] + add + carry;
+    acc[m] = (uint32_t)tsum;
+    carry = tsum >> 32;
+    if (m - li >= 4 && carry == 0) break;
+  }
+}
+
+// acc += (a - b)^2 exactly; acc's least significant bit is 2^-298.
+__device__ void add_exact_sq_diff(uint32_t* acc, float a, float b) {
+  uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+  uint32_t ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu;
+  uint64_t ma = (ua & 0x7fffffu) | (ea ? 0x800000u : 0u);
+  uint64_t mb = (ub & 0x7fffffu) | (eb ? 0x800000u : 0u);
+  if (ma == 0 && mb == 0) return;
+  int oa = (ea ? (int)ea : 1) - 1, ob = (eb ? (int)eb : 1) - 1;  // unit offsets above 2^-149
+  int o = ma == 0 ? ob : (mb == 0 ? oa : min(oa, ob));
+  int da = ma ? oa - o : 0, db = mb ? ob - o : 0;
+  if (da <= 38 && db <= 38) {
+    int64_t A = (int64_t)(ma << da), B = (int64_t)(mb << db);
+    if (ua >> 31) A = -A;
+    if (ub >> 31) B = -B;
+    int64_t D = A - B;
+    uint64_t M = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
+    limbs_add_u128(acc, M * M, __umul64hi(M, M), 2 * o);
+    return;
+  }
+  // far-apart magnitudes: exact difference in 320-bit fixed point, then a schoolbook square
+  Wide d;
+  wide_zero(d);
+  wide_add_f32(d, a);
+  wide_add_f32(d, -b);
+  if (d.limb[9] >> 31) {
+    uint64_t carry = 1;
+    for (int i = 0; i < 10; ++i) {
+      uint64_t tt = (uint64_t)(~d.limb[i]) + carry;
+      d.limb[i] = (uint32_t)tt;
+      carry = tt >> 32;
+    }
+  }
+  for (int i = 0; i < 10; ++i) {
+    if (!d.limb[i]) continue;
+    for (int jj = 0; jj < 10; ++jj) {
+      if (!d.limb[jj]) continue;
+      uint64_t pr = (uint64_t)d.limb[i] * d.limb[jj];
+      limbs_add_u128(acc, pr, 0ull, 32 * (i + jj));
+    }
+  }
+}
+
+__device__ __forceinline__ bool limbs_less(const uint32_t* a, uint32_t ra, const uint32_t* b, uint32_t rb) {
+  for (int m = kLimbs - 1; m >= 0; --m)
+    if (a[m] != b[m]) return a[m] < b[m];
+  return ra < rb;
+}
+
+// One CTA per query: exact squared distances of the contenders (warp per contender), then the
+// k best by (exact distance, row).
+__global__ void __launch_bounds__(256) rerank_kernel(
+    const float* __restrict__ series, int len, const float* __restrict__ queries, int64_t q0,
+    const uint32_t* __restrict__ cont_count, const uint32_t* __restrict__ cont_rows,
+    uint32_t* __restrict__ limbs, int k, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
+    unsigned long long* __restrict__ counters) {
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int m = (int)min(cont_count[j], (uint32_t)kContCap);
+  const float* qp = queries + (q0 + j) * (int64_t)len;
+  uint32_t* L = limbs + (int64_t)j * kContCap * kLimbs;
+  const uint32_t* R = cont_rows + (int64_t)j * kContCap;
+  for (int c = warp; c < m; c += blockDim.x >> 5) {
+    uint32_t acc[kLimbs];
+#pragma unroll
+    for (int i = 0; i < kLimbs; ++i) acc[i] = 0u;
+    const float* xr = series + (int64_t)R[c] * len;
+    for (int e = lane; e < len; e += 32) add_exact_sq_diff(acc, xr[e], qp[e]);
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < kLimbs; ++i) {
+      uint64_t s = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(PARIS_FULL_MASK, s, o);
+      s += carry;
+      if (lane == 0) L[(int64_t)c * kLimbs + i] = (uint32_t)s;
+      carry = s >> 32;
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    const uint32_t* la = L + (int64_t)a * kLimbs;
+    uint32_t ra = R[a];
+    int rank = 0;
+    for (int b = 0; b < m; ++b)
+      if (b != a && limbs_less(L + (int64_t)b * kLimbs, R[b], la, ra)) ++rank;
+    if (rank < k) {
+      out_idx[(q0 + j) * (int64_t)k + rank] = (int64_t)ra;
+      if (out_dist) {
+        int top = kLimbs - 1;
+        while (top > 0 && la[top] == 0u) --top;
+        double v = 0.0;
+        for (int i = top; i >= 0 && i >= top - 2; --i) v += ldexp((double)la[i], 32 * i - 298);
+        out_dist[(q0 + j) * (int64_t)k + rank] = (float)sqrt(v);
+      }
+    }
+  }
+  if (threadIdx.x == 0) atomicAdd(&counters[2], (unsigned long long)m);
+}
+
+int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+int iters_for(int len) {
+  int it = (len + 127) / 128;
+  return it <= 1 ? 1 : it <= 2 ? 2 : it <= 4 ? 4 : it <= 8 ? 8 : 16;
+}
+
+}  // namespace
+
+paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st) {
+  if (qs.nq <= 0) return PARIS_OK;
+  RowShape sh = make_row_shape(idx->len, idx->w, qs.queries);
+  int64_t blocks = (qs.nq + 7) / 8;
+  int grid = (int)std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
+  int it = sh.fast ? iters_for(idx->len) : 1;
+#define PREP(IT)                                                                              \
+  prep_kernel<IT><<<grid, 256, 0, st>>>(qs.queries, qs.nq, sh, idx->card, idx->bits, idx->beta_keys, \
+                                         idx->beta_ext, qs.qpaa, qs.qkey, qs.qtable, qs.status)
+  switch (it) {
+    case 1: PREP(1); break;
+    case 2: PREP(2); break;
+    case 4: PREP(4); break;
+    case 8: PREP(8); break;
+    default: PREP(16); break;
+  }
+#undef PREP
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+static bool vec_ok(const paris_index* idx, const float* q) {
+  return idx->len % 4 == 0 && idx->len <= 2048 && ((uintptr_t)idx->series % 16u) == 0u &&
+         ((uintptr_t)q % 16u) == 0u;
+}
+
+paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st) {
+  if (qs.nq <= 0) return PARIS_OK;
+  const int Lp = max(idx->leaf_cap, qs.k);
+  int P2 = 1;
+  while (P2 < Lp) P2 <<= 1;
+  size_t smem = (size_t)max(2 * Lp + 1, P2) * sizeof(uint64_t);
+  int vec = vec_ok(idx, qs.queries) ? 1 : 0;
+  int it = vec ? iters_for(idx->len) : 1;
+#define DESC(IT)                                                                                 \
+  do {                                                                                           \
+    PARIS_CUDA(cudaFuncSetAttribute(descent_kernel<IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)smem));                                                 \
+    descent_kernel<IT><<<(unsigned)qs.nq, kDescentThreads, smem, st>>>(                          \
+        idx->series, idx->n, idx->len, vec, idx->keys_sorted, idx->rows_sorted, idx->leaf_cap, qs.k, \
+        qs.queries, qs.qkey, qs.leaf, qs.seed, qs.thr, qs.bsf, qs.cg, qs.counters);              \
+  } while (0)
+  switch (it) {
+    case 1: DESC(1); break;
+    case 2: DESC(2); break;
+    case 4: DESC(4); break;
+    case 8: DESC(8); break;
+    default: DESC(16); break;
+  }
+#undef DESC
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+static paris_status lbscan_common(const paris_index* idx, const float* table, const uint32_t* thr_ptr,
+                                  float thr_value, uint32_t* count, uint32_t* rows, float* lb,
+                                  int64_t cap, uint32_t* status, cudaStream_t st) {
+  size_t smem = (size_t)idx->card * 64 * sizeof(float);
+  static int configured_smem = 0;
+  if ((int)smem > configured_smem) {
+    PARIS_CUDA(cudaFuncSetAttribute(lbscan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured_smem = (int)smem;
+  }
+  int64_t groups = (idx->n + 31) / 32;
+  int64_t need_blocks = (groups + (kLbThreads / 32) * kLbUnroll - 1) / ((kLbThreads / 32) * kLbUnroll);
+  int grid = (int)std::min<int64_t>(need_blocks, (int64_t)sm_count() * 2);
+  if (grid < 1) grid = 1;
+  lbscan_kernel<<<grid, kLbThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax), idx->n, table,
+                                                idx->card, thr_ptr, thr_value, count, rows, lb, cap, status);
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t q, uint32_t* count,
+                           uint32_t* rows, float* lb, int64_t cap, cudaStream_t st) {
+  return lbscan_common(idx, qs.qtable + q * (int64_t)idx->card * 16, qs.thr + q, 0.f, count, rows, lb, cap,
+                       qs.status, st);
+}
+
+paris_status launch_lbscan_threshold(const paris_index* idx, const float* table, float thr,
+                                     uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
+                                     uint32_t* status, cudaStream_t st) {
+  return lbscan_common(idx, table, nullptr, thr, count, rows, lb, cap, status, st);
+}
+
+paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                           cudaStream_t st) {
+  chunk_prefix_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, cs.prefix, qs.counters);
+  PARIS_CUDA(cudaGetLastError());
+  int vec = vec_ok(idx, qs.queries) ? 1 : 0;
+  int it = vec ? iters_for(idx->len) : 1;
+  int grid = sm_count() * 8;
+#define REF(IT)                                                                                   \
+  refine_kernel<IT><<<grid, kRefineThreads, 0, st>>>(idx->series, idx->len, vec, qs.queries, cs.q0, cs.qc, \
+                                                     cs.cap, cs.prefix, cs.rows, cs.lb, cs.F, qs.thr,      \
+                                                     qs.bsf, qs.k, qs.cg, qs.counters)
+  switch (it) {
+    case 1: REF(1); break;
+    case 2: REF(2); break;
+    case 4: REF(4); break;
+    case 8: REF(8); break;
+    default: REF(16); break;
+  }
+#undef REF
+  note_launches(2);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+paris_status launch_select(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                           int64_t* out_idx, float* out_dist, cudaStream_t st) {
+  const int qc = cs.qc;
+  if (qs.k == 1) {
+    kth_from_bsf_kernel<<<(qc + 127) / 128, 128, 0, st>>>(qs.bsf, cs.q0, qc, cs.kth);
+    note_launches(1);
+  } else {
+    select_init_kernel<<<qc, 256, 0, st>>>(cs.sel_state, cs.sel_hist, qc, qs.k);
+    int64_t blocks_x = std::min<int64_t>((cs.cap + 255) / 256, 64);
+    dim3 g((unsigned)std::max<int64_t>(blocks_x, 1), (unsigned)qc);
+    for (int r = 0; r < 3; ++r) {
+      select_hist_kernel<<<g, 256, 0, st>>>(cs.F, cs.count, cs.cap, cs.sel_state, cs.sel_hist, r);
+      select_pick_kernel<<<qc, 256, 0, st>>>(cs.sel_hist, cs.sel_state, cs.kth, r);
+    }
+    note_launches(7);
+  }
+  PARIS_CUDA(cudaGetLastError());
+  PARIS_CUDA(cudaMemsetAsync(cs.cont_count, 0, (size_t)qc * sizeof(uint32_t), st));
+  {
+    int64_t blocks_x = std::min<int64_t>((cs.cap + 255) / 256, 64);
+    dim3 g((unsigned)std::max<int64_t>(blocks_x, 1), (unsigned)qc);
+    contenders_kernel<<<g, 256, 0, st>>>(cs.F, cs.rows, cs.count, cs.cap, cs.kth, qs.cg, cs.cont_count,
+                                         cs.cont_rows, qs.status);
+  }
+  rerank_kernel<<<qc, 256, 0, st>>>(idx->series, idx->len, qs.queries, cs.q0, cs.cont_count, cs.cont_rows,
+                                    cs.cont_limbs, qs.k, out_idx, out_dist, qs.counters);
+  note_launches(2);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+}  // namespace paris

@@ -1,0 +1,58 @@
+// Query-path kernels of the GB300 ParIS+ library (host-side launch interface).
+#pragma once
+#include "internal.h"
+
+namespace paris {
+
+constexpr int kContCap = 512;   // exact re-rank contenders per query
+constexpr int kLimbs = 20;      // 640-bit exact squared distances, least significant bit 2^-298
+constexpr int kMaxLeaf = 4096;  // leaf capacity limit
+
+// Per-call query state, all device pointers.
+struct QueryState {
+  int64_t nq = 0;
+  int k = 1;
+  const float* queries = nullptr;  // device [nq][len]
+  double* qpaa = nullptr;          // [nq][16]
+  uint64_t* qkey = nullptr;        // [nq]
+  float* qtable = nullptr;         // [nq][card][16] conservative MINDIST^2 contributions
+  uint32_t* thr = nullptr;         // [nq] fp32 bits: prune/abandon threshold on squared ED
+  unsigned long long* bsf = nullptr;  // [nq] packed (F bits << 32 | row), k = 1
+  int64_t* leaf = nullptr;         // [nq][2]
+  float* seed = nullptr;           // [nq]
+  uint32_t* status = nullptr;      // [1]
+  unsigned long long* counters = nullptr;  // [4]: candidates, refined, contenders, leaf rows
+  float cg = 1.f;                  // (1+gamma)/(1-gamma), rounded up, gamma = gamma_{len+2}
+};
+
+// Candidate lists of a chunk of queries [q0, q0 + qc).
+struct ChunkState {
+  int64_t q0 = 0;
+  int qc = 0;
+  int64_t cap = 0;                 // candidates per query
+  uint32_t* count = nullptr;       // [qc]
+  uint32_t* rows = nullptr;        // [qc][cap]
+  float* lb = nullptr;             // [qc][cap]
+  float* F = nullptr;              // [qc][cap]
+  uint32_t* prefix = nullptr;      // [qc + 1]
+  uint32_t* kth = nullptr;         // [qc] fp32 bits of the k-th smallest F
+  uint32_t* sel_hist = nullptr;    // [qc][2048]
+  uint32_t* sel_state = nullptr;   // [qc][2]: prefix bits, remaining rank
+  uint32_t* cont_count = nullptr;  // [qc]
+  uint32_t* cont_rows = nullptr;   // [qc][kContCap]
+  uint32_t* cont_limbs = nullptr;  // [qc][kContCap][kLimbs]
+};
+
+paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
+paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st);
+paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t q, uint32_t* count,
+                           uint32_t* rows, float* lb, int64_t cap, cudaStream_t st);
+paris_status launch_lbscan_threshold(const paris_index* idx, const float* table, float thr,
+                                     uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
+                                     uint32_t* status, cudaStream_t st);
+paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                           cudaStream_t st);
+paris_status launch_select(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                           int64_t* out_idx, float* out_dist, cudaStream_t st);
+
+}  // namespace paris

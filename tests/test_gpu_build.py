@@ -1,0 +1,83 @@
+"""GPU parity of the index build (PAA, iSAX symbols, keys, index order) against the oracle.
+Bit-exact: symbols, keys, sorted order, and the FP64 PAA values themselves."""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu, rw, small_dataset, torch
+from oracle import index as oindex
+from oracle import isax
+
+pytestmark = pytest.mark.gpu
+
+
+def encode_gpu(x, w, card):
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    sax, key, paa = P.paris_encode(torch.from_numpy(np.ascontiguousarray(x)).to(dev), w, card, want_paa=True)
+    torch.cuda.synchronize()
+    return sax.cpu().numpy(), key.cpu().numpy().view(np.uint64), paa.cpu().numpy()
+
+
+def check_encode(x, w, card):
+    sax, key, paa = encode_gpu(x, w, card)
+    want_paa = isax.paa(x, w)
+    assert paa.tobytes() == want_paa.tobytes(), "PAA differs from the exactly rounded segment sums"
+    want_sax = isax.symbols(want_paa, card)
+    assert np.array_equal(sax, want_sax)
+    assert np.array_equal(key, isax.key64(want_sax, card))
+
+
+def test_encode_random_walk_100k():
+    check_encode(small_dataset(), 16, 256)
+
+
+@pytest.mark.parametrize("n,length,w,card", [
+    (1000, 128, 16, 256), (777, 1024, 16, 256), (513, 256, 4, 4), (300, 96, 8, 256),
+    (257, 200, 10, 16), (33, 64, 16, 256), (5, 16, 16, 2), (1, 256, 16, 256), (100, 2048, 16, 256),
+    (64, 4096, 16, 256), (100, 48, 16, 64)])
+def test_encode_shapes(n, length, w, card):
+    check_encode(rw(n, length, 7 + length), w, card)
+
+
+def test_encode_tiny_and_exact_values():
+    x = rw(200, 256, 5)
+    x[3, 5] = np.float32(1e-30)            # far below the fast path's fixed-point step
+    x[4, 17] = np.float32(-3e-40)          # subnormal
+    x[5, :16] = np.float32([2.0 ** 60, 1.0, -(2.0 ** 60), 2.0 ** -20] + [0.0] * 12)
+    x[6, :16] = np.float32([1.0, -1.0] * 8)  # PAA exactly 0 = the middle breakpoint
+    x[7, 16:32] = 0.0
+    x[8, :] = -0.0
+    x[9, 32:48] = np.float32(3.0e38)        # large but finite
+    x[9, 48:64] = np.float32(-3.0e38)
+    check_encode(x, 16, 256)
+
+
+def test_encode_rejects_nonfinite():
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    x = rw(64, 256, 3)
+    x[10, 100] = np.inf
+    with pytest.raises(P.ParisError) as e:
+        P.paris_encode(torch.from_numpy(x).to(dev), 16, 256)
+    assert e.value.status == 1
+    x[10, 100] = np.nan
+    with pytest.raises(P.ParisError):
+        P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+
+
+@pytest.mark.parametrize("n", [100_000, 4096 * 3 + 17, 1, 2])
+def test_build_index_order(n):
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    x = small_dataset()[:n] if n <= 100_000 else rw(n, 256, 1)
+    idx = P.paris_build(torch.from_numpy(np.ascontiguousarray(x)).to(dev), 16, 256)
+    view = P.paris_index_describe(idx)
+    assert view["n"] == n and view["leaf_capacity"] == 2048
+    sax = P.paris_export_sax(idx).cpu().numpy()
+    want_sax = isax.isax_words(x, 16, 256)
+    assert np.array_equal(sax, want_sax)
+    got_keys, got_rows = P.paris_export_order(idx)
+    want_rows, want_keys = oindex.sort_order(isax.key64(want_sax, 256))
+    assert np.array_equal(got_keys, want_keys)
+    assert np.array_equal(got_rows, want_rows)
+    idx.free()
