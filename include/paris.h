@@ -171,6 +171,34 @@ paris_status paris_lb_scan(const paris_index* idx, const float* query, float thr
                            uint32_t* out_rows, float* out_lb, int64_t capacity, int64_t* out_count,
                            void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Lower-bound scan without allocation. The paper has no counterpart: this entry point exists
+ * for callers that cannot have the library allocate device memory while they run -- services
+ * that reserve all their device memory up front and forbid allocation on the request path, or
+ * hosts that hand a library only pre-existing buffers. It runs the same kernels as
+ * paris_lb_scan, for nq queries, but calls no cudaMalloc, cudaFree or other allocating routine:
+ * its scratch (each query's PAA, key and lower-bound table, the counters, a status word) lives
+ * in one static device array of PARIS_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until the process exits.
+ *
+ *   queries        device [nq][len] fp32 (as built).
+ *   thresholds_sq  host [nq]: squared thresholds, one per query.
+ *   out_rows/out_lb device [nq][capacity]: query q writes its first `capacity` kept rows (any
+ *                  order) at offset q*capacity; capacity may be 0 (counts only).
+ *   out_counts     host [nq]: number of kept rows per query (may exceed capacity).
+ * Scratch limit: nq * (card*64 + 140) bytes (rounded up per array) must fit in the static
+ * array; larger requests fail with PARIS_EINVAL and a message naming the limit.
+ * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Sharing: all calls share the one array and it keeps the previous call's contents (the call
+ * clears what must start at zero). Calls that overlap on the GPU -- on different streams or
+ * from different threads -- race on it and must not be issued.
+ * ---------------------------------------------------------------------------------------- */
+#define PARIS_NOALLOC_SCRATCH_BYTES (256 * 1024)
+paris_status paris_lb_scan_noalloc(const paris_index* idx, const float* queries, int64_t nq,
+                                   const float* thresholds_sq, uint32_t* out_rows, float* out_lb,
+                                   int64_t capacity, int64_t* out_counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ def lib():
             "paris_export_order": ([VP, P, P, VP], I32),
             "paris_approx_search": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_lb_scan": ([VP, P, F32, P, P, I64, C.POINTER(I64), VP], I32),
+            "paris_lb_scan_noalloc": ([VP, P, I64, P, P, P, I64, P, VP], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
