@@ -36,6 +36,8 @@ def parse():
     p.add_argument("--per-sigma", type=int, default=1000)
     p.add_argument("--k", type=int, default=1)
     p.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    p.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
+    p.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain fp32 method shown beside")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -110,6 +112,13 @@ def make_workload(n, length, per_sigma, rank, pinned=True):
     if pinned:
         qhost = qhost.pin_memory()
     return host, qhost, sig, src
+
+
+def bf16_peak_sustained():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path)).get("bf16_tflops_sustained", 1700.0))
+    return 1700.0
 
 
 def cpu_baseline(host_np, queries_np, target_s):
@@ -213,6 +222,7 @@ def main():
         _build.build()
     n, length, k = args.n, args.len, args.k
     mode = P.PARIS_MODE_BATCHED if args.mode == "batched" else P.PARIS_MODE_PLAIN
+    precision = P.PARIS_REFINE_MIXED if args.precision == "mixed" else P.PARIS_REFINE_FP32
     host, qhost, sig, _ = make_workload(n, length, args.per_sigma, rank)
     X = host.to(dev)
     Q = qhost.to(dev)
@@ -220,16 +230,18 @@ def main():
     nq = Q.shape[0]
     stream = torch.cuda.current_stream()
 
-    def step(collect=None):
+    def step(collect=None, md=mode, prec=precision, answers=None):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         idx = P.paris_build(X, 16, 256)
         e1.record(stream)
         per_sigma_stats = []
         for g in groups:
-            out = P.paris_exact_knn_ex(idx, g, k, mode=mode, want_stats=collect is not None)
+            out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, want_stats=collect is not None)
             if collect is not None:
                 per_sigma_stats.append(out[2])
+            if answers is not None:
+                answers.append(out[0])
         e2.record(stream)
         e2.synchronize()
         idx.free()
@@ -264,6 +276,19 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
 
+    # ---- the plain method (one query per lower-bound pass, fp32 refinement) beside it
+    plain = None
+    if args.plain_steps > 0 and (args.mode != "plain" or args.precision != "fp32"):
+        ans_fast, ans_plain = [], []
+        step(answers=ans_fast)
+        step(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32, answers=ans_plain)
+        same = all(bool(torch.equal(a, b)) for a, b in zip(ans_fast, ans_plain))
+        torch.cuda.synchronize()
+        ts = [step(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32) for _ in range(args.plain_steps)]
+        plain = {"value": nq * args.plain_steps / (sum(ts) * 1e-3), "unit": "queries/s",
+                 "ms_per_step": sum(ts) / args.plain_steps, "mode": "plain", "precision": "fp32",
+                 "identical_answers": same}
+
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
@@ -277,7 +302,8 @@ def main():
             idx = P.paris_build(host, 16, 256)                      # host series: copied in by the library
             for i in range(len(SIGMAS)):
                 sl = slice(i * args.per_sigma, (i + 1) * args.per_sigma)
-                P.paris_exact_knn_ex(idx, qhost[sl], k, out_idx=out_i[sl], out_dist=out_d[sl], mode=mode)
+                P.paris_exact_knn_ex(idx, qhost[sl], k, out_idx=out_i[sl], out_dist=out_d[sl], mode=mode,
+                                     precision=precision)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             idx.free()
@@ -295,8 +321,8 @@ def main():
     # ---- roofline of the dominant kernel, from the per-phase device times of the timed steps
     hbm_peak, peak_kind = measured_peaks()
     steps = len(recs)
-    ph = {"prep": 0.0, "descent": 0.0, "lbscan": 0.0, "refine": 0.0, "select": 0.0}
-    cands = refined = leaf_rows = 0
+    ph = {"prep": 0.0, "descent": 0.0, "lbscan": 0.0, "refine": 0.0, "select": 0.0, "dense": 0.0}
+    cands = refined = leaf_rows = dense_q = 0
     for r in recs:
         for s in r["stats"]:
             for key in ph:
@@ -304,23 +330,37 @@ def main():
             cands += s["candidates"]
             refined += s["refined"]
             leaf_rows += s["leaf_rows"]
+            dense_q += s["dense_queries"]
     build_ms = sum(r["build_ms"] for r in recs) / steps
     query_ms = sum(r["query_ms"] for r in recs) / steps
-    launches_lb = nq * steps
-    lb_bytes = 16.0 * n + 8.0 * cands / launches_lb
-    lb_launch_ms = ph["lbscan"] / launches_lb
+    # LB-scan roofline from the scans that run to completion: the sigma = 0.01 group (in MIXED
+    # precision the scans of queries sent to the tensor-core path stop early)
+    launches_lb = args.per_sigma * steps
+    lb_ms0 = sum(r["stats"][0]["ms_lbscan"] for r in recs)
+    cands0 = sum(r["stats"][0]["candidates"] for r in recs)
+    lb_bytes = 16.0 * n + 8.0 * cands0 / launches_lb
+    lb_launch_ms = lb_ms0 / launches_lb
     lb_gbs = lb_bytes / (lb_launch_ms * 1e-3) / 1e9
     refine_bytes_total = refined * (length * 4.0) + cands * 12.0
     refine_gbs = refine_bytes_total / (ph["refine"] * 1e-3) / 1e9 if ph["refine"] > 0 else 0.0
     per_sigma = []
     for i, s in enumerate(SIGMAS):
         tot = sum(r["stats"][i]["ms_prep"] + r["stats"][i]["ms_descent"] + r["stats"][i]["ms_lbscan"] +
-                  r["stats"][i]["ms_refine"] + r["stats"][i]["ms_select"] for r in recs)
+                  r["stats"][i]["ms_refine"] + r["stats"][i]["ms_select"] + r["stats"][i]["ms_dense"] for r in recs)
         c = sum(r["stats"][i]["candidates"] for r in recs) / (steps * args.per_sigma)
+        dq = sum(r["stats"][i]["dense_queries"] for r in recs) / steps
         per_sigma.append({"sigma": s, "queries_per_s": args.per_sigma * steps / (tot * 1e-3),
-                          "candidates_per_query": c, "pruning_ratio": 1.0 - c / n})
+                          "candidates_per_query": c, "pruning_ratio": 1.0 - c / n, "dense_queries": dq})
     dominant = max(ph, key=ph.get)
-    if dominant == "refine":
+    if dominant == "dense":
+        # algorithmic work of the BF16 screening: two passes (threshold, emission) of 2*len flops
+        # per (query, row) pair over the dense queries
+        flops = 2.0 * 2.0 * length * n * dense_q
+        tf = flops / (ph["dense"] * 1e-3) / 1e12
+        peak_tf = bf16_peak_sustained()
+        roof = {"kernel": "dense_kernel", "bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": tf / peak_tf, "traffic": traffic_for("dense_kernel")}
+    elif dominant == "refine":
         roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel")}
     else:
@@ -339,10 +379,14 @@ def main():
                    "parallelism": f"replicas x{world} (independent collections per GPU)"},
         "roofline": roof,
         "lb_scan": {"achieved_gbs": lb_gbs, "frac_of_hbm": lb_gbs / hbm_peak, "peak_kind": peak_kind,
-                    "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes},
+                    "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes,
+                    "launches": "the sigma=0.01 group's complete scans"},
         "build": {"ms": build_ms, "gb_per_s": n * length * 4 / (build_ms * 1e-3) / 1e9,
                   "series_per_s": n / (build_ms * 1e-3)},
         "query_ms_per_step": query_ms,
+        "precision": args.precision,
+        "plain_method": plain,
+        "dense_queries_per_step": dense_q / steps,
         "phase_ms_per_step": {kk: v / steps for kk, v in ph.items()},
         "per_sigma": per_sigma,
         "refine_gbs": refine_gbs,

@@ -91,19 +91,30 @@ enum {
   PARIS_MODE_BATCHED = 1, /* a tile of queries per pass over the summaries (one read per tile) */
 };
 
+enum {
+  PARIS_REFINE_FP32 = 0,  /* every kept candidate is refined by an fp32 gather (Alg. 9) */
+  PARIS_REFINE_MIXED = 1, /* queries whose lower bounds keep many rows are screened by BF16
+                             tensor-core |q|^2+|x|^2-2q.x tiles (FP32 accumulation); only rows
+                             within the proven BF16 error margin of the best-so-far are
+                             re-checked in fp32. Same exact answers. k <= 16. */
+};
+
 typedef struct paris_query_opts {
   int32_t mode;        /* PARIS_MODE_*; default PLAIN */
   int32_t query_tile;  /* queries per pass in BATCHED mode; 0 = pick automatically */
   int32_t chunk;       /* queries whose candidate lists are resident at once; 0 = automatic */
-  int32_t reserved[5]; /* must be zero */
+  int32_t precision;   /* PARIS_REFINE_*; default FP32 */
+  int32_t reserved[4]; /* must be zero */
 } paris_query_opts;
 
 typedef struct paris_query_stats {
   int64_t candidates;  /* rows kept by the lower-bound scans (sum over queries) */
-  int64_t refined;     /* candidates whose distance was computed to the end */
+  int64_t refined;     /* candidates whose raw series was read (refinement started) */
   int64_t contenders;  /* rows re-ranked exactly */
   int64_t leaf_rows;   /* rows visited by the approximate searches */
+  int64_t dense_queries; /* queries screened by the BF16 tensor-core path */
   double ms_prep, ms_descent, ms_lbscan, ms_refine, ms_select; /* device time per phase */
+  double ms_dense;     /* device time of the BF16 screening (MIXED) */
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */

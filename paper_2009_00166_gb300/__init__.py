@@ -11,6 +11,8 @@ function that needs it raises ``RuntimeError`` when ``libparis.so`` is missing.
 from .binding import (  # noqa: F401
     PARIS_MODE_BATCHED,
     PARIS_MODE_PLAIN,
+    PARIS_REFINE_FP32,
+    PARIS_REFINE_MIXED,
     ParisError,
     ParisIndex,
     QueryStats,

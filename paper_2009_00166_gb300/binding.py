@@ -10,6 +10,8 @@ LIB_PATH = os.path.join(HERE, "libparis.so")
 
 PARIS_MODE_PLAIN = 0
 PARIS_MODE_BATCHED = 1
+PARIS_REFINE_FP32 = 0
+PARIS_REFINE_MIXED = 1
 
 _STATUS = {0: "PARIS_OK", 1: "PARIS_EINVAL", 2: "PARIS_ENOMEM", 3: "PARIS_ECUDA", 4: "PARIS_ETIMEOUT",
            5: "PARIS_EINTERNAL"}
@@ -27,13 +29,14 @@ class BuildOpts(C.Structure):
 
 class QueryOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("query_tile", C.c_int32), ("chunk", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("precision", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class QueryStats(C.Structure):
     _fields_ = [("candidates", C.c_int64), ("refined", C.c_int64), ("contenders", C.c_int64),
-                ("leaf_rows", C.c_int64), ("ms_prep", C.c_double), ("ms_descent", C.c_double),
-                ("ms_lbscan", C.c_double), ("ms_refine", C.c_double), ("ms_select", C.c_double)]
+                ("leaf_rows", C.c_int64), ("dense_queries", C.c_int64), ("ms_prep", C.c_double),
+                ("ms_descent", C.c_double), ("ms_lbscan", C.c_double), ("ms_refine", C.c_double),
+                ("ms_select", C.c_double), ("ms_dense", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -160,7 +163,8 @@ def paris_free(index: ParisIndex):
 
 
 def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, mode: int = PARIS_MODE_PLAIN,
-                       query_tile: int = 0, chunk: int = 0, want_stats: bool = False, stream=None):
+                       query_tile: int = 0, chunk: int = 0, precision: int = PARIS_REFINE_FP32,
+                       want_stats: bool = False, stream=None):
     """paris_exact_knn_ex: returns (idx [nq][k] int64, dist [nq][k] float32[, stats dict]).
 
     Outputs are allocated like the queries (same device) when not given.
@@ -172,7 +176,7 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
         out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk)
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision)
     stats = QueryStats()
     _check(lib().paris_exact_knn_ex(index.handle, _ptr(queries), nq, k, _ptr(out_idx), _ptr(out_dist),
                                     C.byref(opts), C.byref(stats) if want_stats else None, _stream(stream)))

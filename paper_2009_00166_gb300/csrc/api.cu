@@ -124,6 +124,7 @@ void release_index(paris_index* idx) {
   dev_free(idx->rows_sorted, (size_t)idx->n * 4, st);
   dev_free(idx->beta_keys, (size_t)(idx->card - 1) * 8, st);
   dev_free(idx->beta_ext, (size_t)(idx->card + 1) * 8, st);
+  release_shadow(idx);
   delete idx;
 }
 
@@ -167,7 +168,7 @@ struct Staged {
 struct PhaseTimer {
   bool on = false;
   cudaStream_t st = nullptr;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[5];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[6];
   explicit PhaseTimer(bool enable, cudaStream_t s) : on(enable), st(s) {}
   void begin(int phase) {
     if (!on) return;
@@ -180,13 +181,13 @@ struct PhaseTimer {
   void end(int phase) {
     if (on) cudaEventRecord(ev[phase].back().second, st);
   }
-  void collect(double* out5) {
-    for (int p = 0; p < 5; ++p) {
+  void collect(double* out6) {
+    for (int p = 0; p < 6; ++p) {
       for (auto& e : ev[p]) {
         float ms = 0.f;
         cudaEventSynchronize(e.second);
         cudaEventElapsedTime(&ms, e.first, e.second);
-        if (out5) out5[p] += ms;
+        if (out6) out6[p] += ms;
       }
     }
   }
@@ -413,8 +414,10 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   if (nq > 0 && !out_idx) return fail(PARIS_EINVAL, "out_idx is NULL");
   paris_query_opts o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.precision != PARIS_REFINE_FP32 && o.precision != PARIS_REFINE_MIXED)
+    return fail(PARIS_EINVAL, "unknown precision %d", o.precision);
   if (o.mode != PARIS_MODE_PLAIN && o.mode != PARIS_MODE_BATCHED)
     return fail(PARIS_EINVAL, "unknown mode %d", o.mode);
   if (stats) std::memset(stats, 0, sizeof *stats);
@@ -435,14 +438,20 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   timer.begin(1);
   PARIS_TRY(launch_descent(idx, qs, st));
   timer.end(1);
-  // chunks of queries whose candidate lists are resident together
-  const int64_t cap = idx->n;
+  // chunks of queries whose candidate lists are resident together; in MIXED precision the lists
+  // are short and a query whose list overflows is screened by the BF16 tensor-core pass instead
+  const bool mixed = o.precision == PARIS_REFINE_MIXED && dense_supported(idx, k);
+  const int64_t cap = mixed ? std::min<int64_t>(idx->n, std::max<int64_t>(idx->n / 128, 8192)) : idx->n;
+  DevBuf lbstatus;
+  if (!lbstatus.alloc(4, st)) return fail(PARIS_ENOMEM, "status word");
+  uint32_t* lb_status = mixed ? lbstatus.as<uint32_t>() : qs.status;  // overflow is the signal in MIXED
+  int64_t dense_total = 0;
   int64_t qc = o.chunk;
   if (qc <= 0) {
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
     double budget = std::min((double)freeb * 0.25, 8.0e9);
-    qc = (int64_t)(budget / ((double)cap * 12.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0));
+    qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0));
     qc = std::max<int64_t>(1, std::min<int64_t>(qc, 1024));
   }
   qc = std::min(qc, nq);
@@ -458,7 +467,8 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     size_t o_count = take((size_t)qc * 4), o_rows = take((size_t)qc * cap * 4), o_lb = take((size_t)qc * cap * 4),
            o_F = take((size_t)qc * cap * 4), o_pre = take((size_t)(qc + 1) * 4), o_kth = take((size_t)qc * 4),
            o_hist = take((size_t)qc * 2048 * 4), o_sel = take((size_t)qc * 8), o_cc = take((size_t)qc * 4),
-           o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4);
+           o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4),
+           o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
     char* b = cblock.as<char>();
     cs.cap = cap;
@@ -473,6 +483,9 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     cs.cont_count = (uint32_t*)(b + o_cc);
     cs.cont_rows = (uint32_t*)(b + o_cr);
     cs.cont_limbs = (uint32_t*)(b + o_cl);
+    cs.rows2 = (uint32_t*)(b + o_r2);
+    cs.lb2 = (float*)(b + o_l2);
+    cs.bucket = (uint32_t*)(b + o_bk);
   }
   for (int64_t q0 = 0; q0 < nq; q0 += qc) {
     cs.q0 = q0;
@@ -481,8 +494,15 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     timer.begin(2);
     for (int j = 0; j < cs.qc; ++j)
       PARIS_TRY(launch_lbscan(idx, qs, q0 + j, cs.count + j, cs.rows + (int64_t)j * cap, cs.lb + (int64_t)j * cap,
-                              cap, st));
+                              cap, lb_status, mixed ? 1 : 0, st));
     timer.end(2);
+    if (mixed) {
+      int nd = 0;
+      timer.begin(5);
+      PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, &nd, st));
+      timer.end(5);
+      dense_total += nd;
+    }
     timer.begin(3);
     PARIS_TRY(launch_refine(idx, qs, cs, st));
     timer.end(3);
@@ -494,8 +514,10 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   PARIS_TRY(sd.finish(st));
   PARIS_TRY(check_status_word(qs.status, st, "paris_exact_knn"));
   if (stats) {
-    double ms[5] = {0, 0, 0, 0, 0};
+    double ms[6] = {0, 0, 0, 0, 0, 0};
     timer.collect(ms);
+    stats->ms_dense = ms[5];
+    stats->dense_queries = dense_total;
     stats->ms_prep = ms[0];
     stats->ms_descent = ms[1];
     stats->ms_lbscan = ms[2];

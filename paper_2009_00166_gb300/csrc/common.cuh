@@ -17,8 +17,10 @@ enum : uint32_t {
 };
 
 __device__ __forceinline__ uint64_t double_order_key(double v) {
-  // Monotone map of IEEE doubles to unsigned integers (-0 normalised to +0 first).
-  uint64_t u = (uint64_t)__double_as_longlong(v == 0.0 ? 0.0 : v);
+  // Monotone map of IEEE doubles to unsigned integers (-0 normalised to +0 first); integer
+  // operations only.
+  uint64_t u = (uint64_t)__double_as_longlong(v);
+  if ((u << 1) == 0ull) u = 0ull;
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
@@ -200,105 +202,105 @@ __device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, in
 
 struct RowShape {
   int len, w, s, log2s;  // log2s = -1 when s is not a power of two
-  int fast;              // 1: vectorised fixed-point path applies
+  int fast;              // 1: vectorised fixed-point path applies (s = 4 * SEGV, aligned rows)
 };
 
-// Exact PAA of one row (Sec. 2.2), computed by a whole warp. On return lane i < w holds
-// PAA_i = RN64(exact sum of segment i) / s. Returns false if the row holds a NaN or infinity.
-// The fast path keeps the row in registers as fixed-point integers scaled by a per-row power
-// of two; rows with values too small for that scale take the exact wide-accumulator path.
-template <int ITERS>
-__device__ __forceinline__ bool warp_row_paa(const float* __restrict__ row, const RowShape& sh,
-                                             int lane, double& paa_out) {
-  const int len = sh.len, w = sh.w, s = sh.s;
+// Exact PAA (Sec. 2.2) of one (row, segment) per lane. A warp holds two rows: lanes 0-15 the
+// segments of `row0`, lanes 16-31 those of `row1` (NULL past the end). Lane l returns, when its
+// segment i = l & 15 is < w, PAA_i = RN64(exact sum of the s values of segment i) / s.
+// Fast path: the segment's values are integer multiples of 2^lambda, lambda picked from the
+// segment's largest exponent so that the sum fits in 63 bits; they are summed exactly in int64
+// and rounded once. Segments holding values finer than 2^lambda (or subnormals) take the
+// 320-bit exact accumulator instead. Returns false if the lane's segment holds a NaN or infinity.
+template <int SEGV>
+__device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0, const float* __restrict__ row1,
+                                                 const RowShape& sh, int lane, double& paa_out) {
+  const int seg = lane & 15;
+  const float* row = (lane >> 4) ? row1 : row0;
+  const bool active = row != nullptr && seg < sh.w;
+  const int s = sh.s;
+  paa_out = 0.0;
   bool finite = true;
+  bool done = false;
   if (sh.fast) {
-    float4 v[ITERS];
+    const float4* p = reinterpret_cast<const float4*>(row + (active ? (int64_t)seg * s : 0));
+    constexpr bool kCache = SEGV <= 4;
+    float4 cache[kCache ? SEGV : 1];
+    uint32_t emax = 1u, emin = 255u, anysub = 0u;
 #pragma unroll
-    for (int t = 0; t < ITERS; ++t) {
-      int i4 = lane + 32 * t;
-      if (4 * i4 < len)
-        v[t] = __ldcs(reinterpret_cast<const float4*>(row) + i4);
-      else
-        v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    uint32_t emax = 1;
+    for (int v = 0; v < SEGV; ++v) {
+      float4 x = active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kCache) cache[kCache ? v : 0] = x;
+      const uint32_t u[4] = {__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), __float_as_uint(x.w)};
 #pragma unroll
-    for (int t = 0; t < ITERS; ++t) {
-      uint32_t e0 = (__float_as_uint(v[t].x) >> 23) & 0xffu, e1 = (__float_as_uint(v[t].y) >> 23) & 0xffu;
-      uint32_t e2 = (__float_as_uint(v[t].z) >> 23) & 0xffu, e3 = (__float_as_uint(v[t].w) >> 23) & 0xffu;
-      emax = max(emax, max(max(e0, e1), max(e2, e3)));
-    }
-    emax = __reduce_max_sync(PARIS_FULL_MASK, emax);
-    if (emax == 255u) return false;
-    // sums of <= s values below 2^(emax-126) stay below 2^63 * 2^lambda
-    const int lambda = (int)emax - 126 + sh.log2s - 63;
-    bool inexact = false;
-    int64_t part[ITERS];
-#pragma unroll
-    for (int t = 0; t < ITERS; ++t)
-      part[t] = to_fixed(v[t].x, lambda, inexact) + to_fixed(v[t].y, lambda, inexact) +
-                to_fixed(v[t].z, lambda, inexact) + to_fixed(v[t].w, lambda, inexact);
-    if (!__any_sync(PARIS_FULL_MASK, inexact)) {
-      const int g = s >> 2;  // lanes per segment within one 128-value sweep
-#pragma unroll
-      for (int t = 0; t < ITERS; ++t)
-        for (int off = g >> 1; off > 0; off >>= 1) part[t] += shfl_xor_i64(part[t], off);
-      // lane i collects segment i: sweep t holds segments t*(32/g) + lane/g in lanes (.)*g
-      const int per = 32 / g;
-      int64_t mine = 0;
-#pragma unroll
-      for (int t = 0; t < ITERS; ++t) {
-        int64_t val = shfl_i64(part[t], (lane % per) * g);
-        if (lane / per == t) mine = val;
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t be = (u[c] >> 23) & 0xffu;
+        const bool nz = (u[c] & 0x7fffffffu) != 0u;
+        emax = max(emax, be);
+        emin = nz ? min(emin, be) : emin;
+        anysub |= (uint32_t)(nz && be == 0u);
       }
-      paa_out = fixed_to_double(mine, lambda - sh.log2s);  // s is a power of two here
-      (void)w;
-      return true;
     }
-    // fall through to the exact wide path for this row
+    if (emax == 255u) {
+      finite = false;
+      done = true;
+    } else {
+      const int lambda = (int)emax - 126 + sh.log2s - 63;
+      // every nonzero value has its least significant bit at 2^(be-150) >= 2^lambda
+      if (!anysub && (emin == 255u || (int)emin - 150 >= lambda)) {
+        int64_t S = 0;
+#pragma unroll
+        for (int v = 0; v < SEGV; ++v) {
+          float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
+          const uint32_t u[4] = {__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), __float_as_uint(x.w)};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t be = (u[c] >> 23) & 0xffu;
+            const uint64_t mant = (uint64_t)((u[c] & 0x7fffffu) | 0x800000u);
+            const int sh_ = max((int)be - 150 - lambda, 0);
+            const int64_t mag = (u[c] & 0x7fffffffu) ? (int64_t)(mant << sh_) : 0;
+            S += (u[c] >> 31) ? -mag : mag;
+          }
+        }
+        paa_out = fixed_to_double(S, lambda - sh.log2s);  // s is a power of two on this path
+        done = true;
+      }
+    }
   }
-  // general path: lane i < w sums its own segment exactly
-  double r = 0.0;
-  bool bad = false;
-  if (lane < w) {
+  if (!done && active) {
     Wide acc;
     wide_zero(acc);
-    const float* p = row + (int64_t)lane * s;
+    const float* p = row + (int64_t)seg * s;
     for (int j = 0; j < s; ++j) {
       float x = p[j];
-      if (((__float_as_uint(x) >> 23) & 0xffu) == 0xffu) bad = true;
+      if (((__float_as_uint(x) >> 23) & 0xffu) == 0xffu) finite = false;
       wide_add_f32(acc, x);
     }
     double S = wide_to_double(acc);
-    r = sh.log2s >= 0 ? S * (1.0 / (double)(1 << sh.log2s)) : __ddiv_rn(S, (double)s);
+    paa_out = sh.log2s >= 0 ? S * (1.0 / (double)(1 << sh.log2s)) : __ddiv_rn(S, (double)s);
   }
-  finite = !__any_sync(PARIS_FULL_MASK, bad);
-  paa_out = r;
   return finite;
 }
 
-// Bit-plane interleaved key (top 64 bits): plane j = bit (bits-1-j) of segments 0..w-1.
-// Every lane must call; lane i < w passes its symbol.
-__device__ __forceinline__ uint64_t warp_key64(int sym, int lane, int w, int bits) {
-  uint64_t hi = 0, lo = 0;  // 128-bit key, filled from the top
+// Top 64 bits of the bit-plane interleaved key of both rows of a warp (lanes 0-15: row 0,
+// lanes 16-31: row 1; lane i of a half passes the symbol of segment i, 0 when i >= w).
+// Plane j holds bit (bits-1-j) of segments 0..w-1, segment 0 first.
+__device__ __forceinline__ uint64_t warp_pair_key64(int sym, int lane, int w, int bits) {
+  uint64_t hi = 0, lo = 0;
   int filled = 0;
   for (int j = 0; j < bits; ++j) {
-    int b = bits - 1 - j;
-    uint32_t m = __ballot_sync(PARIS_FULL_MASK, lane < w && ((sym >> b) & 1));
-    uint64_t plane = (uint64_t)(__brev(m) >> (32 - w));  // segment 0 first
-    // shift the 128-bit (hi, lo) left by w and or in the plane
+    const int b = bits - 1 - j;
+    const uint32_t m = __brev(__ballot_sync(PARIS_FULL_MASK, (sym >> b) & 1));
+    // row 0's lanes 0..15 are now bits 31..16, row 1's lanes 16..31 are bits 15..0
+    const uint32_t half = (lane >> 4) ? (m & 0xffffu) : (m >> 16);
+    const uint64_t plane = (uint64_t)(half >> (16 - w));
     hi = (hi << w) | (lo >> (64 - w));
     lo = (lo << w) | plane;
     filled += w;
   }
-  // left-align the filled bits within 128
-  int sh = 128 - filled;
-  if (sh >= 64) {
-    hi = lo << (sh - 64);
-  } else if (sh > 0) {
-    hi = (hi << sh) | (lo >> (64 - sh));
-  }
+  const int sh = 128 - filled;
+  if (sh >= 64) return lo << (sh - 64);
+  if (sh > 0) return (hi << sh) | (lo >> (64 - sh));
   return hi;
 }
 

@@ -1,0 +1,562 @@
+// Mixed-precision screening for queries whose lower bounds keep many rows.
+//
+// For a query q and a row x the kernel forms d~ = |q|^2 + |x|^2 - 2 (q~ . x~) with q~, x~ the
+// BF16 roundings of q and x, the dot product taken on the 5th-generation tensor cores
+// (tcgen05.mma, FP32 accumulation in tensor memory) and |q|^2, |x|^2 taken in fp32 from the
+// fp32 values. A proven bound M(q, x) on |d~ - |q - x|^2| then gives, per pair, the interval
+// [d~ - M, d~ + M] that holds the exact squared distance:
+//   pass 1 keeps, per query, the k smallest upper ends d~ + M and lowers the query's
+//          best-so-far threshold with the k-th (k distinct rows bound the k-th best distance);
+//   pass 2 emits every row whose lower end d~ - M does not exceed that threshold as a
+//          candidate (with d~ - M as its lower bound) for the exact fp32 re-check (Alg. 9).
+// Rows are only discarded when provably farther than the k-th neighbour, so answers stay exact.
+//
+// Kernel shape: one persistent CTA per SM; warp 0 streams 64-row tiles of the BF16 shadow of
+// the series into a 4-stage shared-memory ring with TMA (128-byte swizzle), warp 1 issues the
+// tensor-core MMAs (one thread) into two TMEM accumulators of 128 x 64 fp32, and warps 2-5 read
+// the accumulators back (tcgen05.ld) and run the screening epilogue, one query per thread.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "query.cuh"
+
+namespace paris {
+
+namespace {
+
+constexpr int BM = 128;             // queries per tile (MMA M)
+constexpr int BN = 64;              // series rows per tile (MMA N)
+constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
+constexpr int STAGES = 4;           // shared-memory ring depth for row tiles
+constexpr int DENSE_THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr int KMAX = 16;            // largest k the screening supports
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr int MAX_KB = 4;           // len <= 256
+constexpr size_t A_BYTES = (size_t)MAX_KB * BM * 128;
+constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
+constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * B_STAGE_BYTES + 256;
+constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
+
+struct DenseParams {
+  int64_t n;
+  int len, nkb;
+  int qtile, nd;
+  const float2* xnorm;  // [n]: (|x|^2, |x|)
+  const float2* qnorm;  // [nd_pad]
+  const int* qslot;     // [nd]: chunk-local slot of dense query d
+  int64_t q0;           // thresholds of slot j live at thr[q0 + j]
+  uint32_t* thr;
+  int k;
+  float cg, c1, c2;
+  uint32_t* count;
+  uint32_t* rows;
+  float* lb;
+  int64_t cap;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity; gives up (returning false) after kWaitNs or when
+// another role has already given up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer() > deadline) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout written by
+// TMA (8-row x 128-byte atoms, 1024 bytes apart).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int PHASE>
+__global__ void __launch_bounds__(DENSE_THREADS, 1)
+    dense_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DenseParams P) {
+  extern __shared__ uint8_t dsm_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smA = base;
+  uint8_t* smB = base + A_BYTES;
+  uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
+  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + STAGES), b_accf = smem_u32(bars + 2 * STAGES),
+                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(b_full + 8 * s, 1);
+      mbar_init(b_empty + 8 * s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(b_accf + 8 * a, 1);
+      mbar_init(b_acce + 8 * a, 4);
+    }
+    mbar_init(b_afull, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const int64_t ntiles = (P.n + BN - 1) / BN;
+  const uint64_t deadline = globaltimer() + kWaitNs;
+  const int nkb = P.nkb;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      mbar_expect_tx(b_afull, (uint32_t)(nkb * BM * 128));
+      for (int kb = 0; kb < nkb; ++kb)
+        tma_load_2d(smem_u32(smA + (size_t)kb * BM * 128), &tmA, kb * BKE, P.qtile * BM, b_afull);
+      int i = 0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128));
+        for (int kb = 0; kb < nkb; ++kb)
+          tma_load_2d(smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128), &tmB, kb * BKE,
+                      (int)(t * BN), b_full + 8 * s);
+      }
+      // drain: the last loads must land before the CTA may exit
+      const int issued = i;
+      for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
+        mbar_wait(b_full + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), abort_flag, deadline + 100000000ull);
+      mbar_wait(b_afull, 0u, abort_flag, deadline + 100000000ull);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      bool ok = mbar_wait(b_afull, 0u, abort_flag, deadline);
+      int i = 0;
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+        const int ab = i & 1;
+        const uint32_t aph = (uint32_t)((i >> 1) & 1);
+        if (!mbar_wait(b_full + 8 * s, ph, abort_flag, deadline) ||
+            !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag, deadline)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint32_t a0 = smem_u32(smA + (size_t)kb * BM * 128);
+          const uint32_t b0 = smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)  // 16 BF16 = 32 bytes per MMA step along K
+            umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
+                      (kb | ks) ? 1u : 0u);
+        }
+        umma_commit(b_empty + 8 * s);
+        umma_commit(b_accf + 8 * ab);
+      }
+      if (!ok) *abort_flag = 1;
+      // drain: wait for the last MMAs before the TMEM is released
+      if (i > 0) mbar_wait(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag,
+                           deadline + 100000000ull);
+    }
+  } else {  // ---- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+    const int qd = warp & 3;
+    const int m = qd * 32 + lane;
+    const int d = P.qtile * BM + m;
+    const bool valid = d < P.nd;
+    float qn = 0.f, qrt = 0.f, thr_q = 0.f;
+    int slot = 0;
+    uint32_t* thr_ptr = nullptr;
+    if (valid) {
+      const float2 qq = P.qnorm[d];
+      qn = qq.x;
+      qrt = qq.y;
+      slot = P.qslot[d];
+      thr_ptr = P.thr + P.q0 + slot;
+      thr_q = __uint_as_float(*(volatile uint32_t*)thr_ptr);
+    }
+    const float c1q = __fmul_ru(P.c1, qrt);
+    float best[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) best[j] = CUDART_INF_F;
+    float kth = CUDART_INF_F;
+    // row norms of a tile: lane l holds rows 32c + l (c = 0, 1), prefetched one tile ahead and
+    // broadcast with shuffles
+    auto load_norms = [&](int64_t t, float2 (&xr)[BN / 32]) {
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        const int64_t row = t * BN + c * 32 + lane;
+        xr[c] = (t < ntiles && row < P.n) ? P.xnorm[row] : make_float2(0.f, 0.f);
+      }
+    };
+    float2 xnext[BN / 32];
+    load_norms(blockIdx.x, xnext);
+    int i = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      float2 xcur[BN / 32];
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) xcur[c] = xnext[c];
+      load_norms(t + gridDim.x, xnext);
+      const int ab = i & 1;
+      const uint32_t aph = (uint32_t)((i >> 1) & 1);
+      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);
+        const int64_t row0 = t * BN + c * 32;
+        const int64_t left = P.n - row0;
+        const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);  // rows of this chunk inside the series
+        // common path, unrolled: the per-pair interval end and a mask of the pairs that need work
+        float val[32];
+        uint32_t hit = 0u;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const float xn = __shfl_sync(PARIS_FULL_MASK, xcur[c].x, jj);
+          const float xrt = __shfl_sync(PARIS_FULL_MASK, xcur[c].y, jj);
+          const float d2 = fmaf(-2.0f, __uint_as_float(v[jj]), qn + xn);
+          const float M = __fmaf_ru(c1q, xrt, __fmul_ru(P.c2, __fadd_ru(qn, xn)));
+          if (PHASE == 1) {
+            val[jj] = __fadd_ru(d2, M);  // upper end: the exact squared distance is below it
+            hit |= (val[jj] < kth ? 1u : 0u) << jj;
+          } else {
+            val[jj] = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
+            hit |= (val[jj] <= thr_q ? 1u : 0u) << jj;
+          }
+        }
+        const uint32_t row_mask = nrow >= 32 ? 0xffffffffu : (nrow <= 0 ? 0u : ((1u << nrow) - 1u));
+        hit = valid ? (hit & row_mask) : 0u;
+        // rare path, not unrolled: insert into the top-k (pass 1) or emit a candidate (pass 2)
+        while (hit) {
+          const int jj = __ffs(hit) - 1;
+          hit &= hit - 1u;
+          float x = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) x = (j == jj) ? val[j] : x;
+          if (PHASE == 1) {
+            if (x < kth) {
+#pragma unroll
+              for (int j = 0; j < KMAX; ++j) {
+                if (j < P.k) {
+                  const float lo = fminf(best[j], x);
+                  x = fmaxf(best[j], x);
+                  best[j] = lo;
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < KMAX; ++j)
+                if (j == P.k - 1) kth = best[j];
+            }
+          } else {
+            const uint32_t p = atomicAdd(P.count + slot, 1u);
+            if ((int64_t)p < P.cap) {
+              P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
+              P.lb[(int64_t)slot * P.cap + p] = x;
+            } else {
+              atomicOr(P.status, DEV_CAND_OVERFLOW);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+    }
+    if (PHASE == 1 && valid && kth < CUDART_INF_F) atomicMin(thr_ptr, __float_as_uint(__fmul_ru(kth, P.cg)));
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, DEV_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// BF16 shadow of the series and fp32 (|x|^2, |x|) per row; one warp per row.
+__global__ void shadow_kernel(const float* __restrict__ x, int64_t n, int len, __nv_bfloat16* __restrict__ out,
+                              float2* __restrict__ norms, const int* __restrict__ gather, int64_t q0, int64_t rows_pad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows_pad; r += warps) {
+    const bool real = r < n;
+    const int64_t src = real ? (gather ? q0 + gather[r] : r) : 0;
+    const float* xr = x + src * (int64_t)len;
+    __nv_bfloat16* o = out + r * (int64_t)len;
+    float acc = 0.f;
+    for (int j = 2 * lane; j < len; j += 64) {
+      float a = real ? xr[j] : 0.f, b = real ? xr[j + 1] : 0.f;
+      acc = fmaf(a, a, acc);
+      acc = fmaf(b, b, acc);
+      *reinterpret_cast<__nv_bfloat162*>(o + j) = __floats2bfloat162_rn(a, b);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(PARIS_FULL_MASK, acc, s);
+    if (lane == 0) norms[r] = make_float2(acc, __fsqrt_ru(acc));
+  }
+}
+
+__global__ void dense_select_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap, int* __restrict__ slots,
+                                    int* __restrict__ nd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int m = 0;
+  for (int j = 0; j < qc; ++j)
+    if ((int64_t)count[j] > cap) slots[m++] = j;
+  *nd = m;
+}
+
+__global__ void dense_reset_kernel(uint32_t* __restrict__ count, const int* __restrict__ slots, int nd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nd) count[slots[i]] = 0u;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+paris_status make_bf16_map(CUtensorMap* map, const void* base, int64_t rows, int len, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return fail(PARIS_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)len, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)len * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BKE, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PARIS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return PARIS_OK;
+}
+
+std::mutex g_shadow_mutex;
+
+int sm_count_dense() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+}  // namespace
+
+bool dense_supported(const paris_index* idx, int k) {
+  return k <= KMAX && idx->len % BKE == 0 && idx->len <= MAX_KB * BKE;
+}
+
+void dense_margins(int len, float* c1, float* c2) {
+  // |d~ - |q-x|^2| <= c1 |q||x| + c2 (|q|^2 + |x|^2):
+  //  BF16 rounding of q and x (unit roundoff 2^-8) perturbs each product by (2^-7 + 2^-16)|q_j x_j|;
+  //  the tensor-core FP32 accumulation of `len` products is bounded as if every addition could
+  //  lose 2^-23 (truncation): gamma' = len 2^-23 / (1 - len 2^-23), on sum |q~_j x~_j|;
+  //  |q|^2, |x|^2 in fp32 (gamma_len, u = 2^-24) and the two final fp32 operations (2u);
+  //  sum |q_j x_j| <= |q||x| (Cauchy-Schwarz). Everything is inflated by 2^-10 for the
+  //  rounding of the margin itself.
+  const double ub = std::ldexp(1.0, -8), u = std::ldexp(1.0, -24);
+  const double gp = len * std::ldexp(1.0, -23) / (1.0 - len * std::ldexp(1.0, -23));
+  const double gl = len * u / (1.0 - len * u);
+  const double prod = 2.0 * ub + ub * ub;
+  double a = 2.0 * (prod + gp * (1.0 + prod)) + 2.0 * u * (1.0 + prod) * (1.0 + gp);
+  double b = gl + 2.0 * u;
+  *c1 = std::nextafter((float)(a * (1.0 + std::ldexp(1.0, -10))), INFINITY);
+  *c2 = std::nextafter((float)(b * (1.0 + std::ldexp(1.0, -10))), INFINITY);
+}
+
+paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_shadow_mutex);
+  if (idx->shadow) return PARIS_OK;
+  const size_t bytes = (size_t)idx->n * idx->len * 2;
+  void* sh = dev_alloc(bytes, st);
+  float2* nm = (float2*)dev_alloc((size_t)idx->n * sizeof(float2), st);
+  if (!sh || !nm) {
+    dev_free(sh, bytes, st);
+    dev_free(nm, (size_t)idx->n * sizeof(float2), st);
+    return fail(PARIS_ENOMEM, "BF16 shadow of the series (%zu bytes)", bytes);
+  }
+  int grid = sm_count_dense() * 8;
+  shadow_kernel<<<grid, 256, 0, st>>>(idx->series, idx->n, idx->len, (__nv_bfloat16*)sh, nm, nullptr, 0, idx->n);
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  CUtensorMap* map = new CUtensorMap;
+  paris_status s = make_bf16_map(map, sh, idx->n, idx->len, BN);
+  if (s != PARIS_OK) {
+    delete map;
+    return s;
+  }
+  idx->shadow = sh;
+  idx->xnorm = nm;
+  idx->shadow_map = map;
+  return PARIS_OK;
+}
+
+void release_shadow(paris_index* idx) {
+  if (idx->shadow) dev_free(idx->shadow, (size_t)idx->n * idx->len * 2, nullptr);
+  if (idx->xnorm) dev_free(idx->xnorm, (size_t)idx->n * sizeof(float2), nullptr);
+  delete (CUtensorMap*)idx->shadow_map;
+  idx->shadow = nullptr;
+  idx->xnorm = nullptr;
+  idx->shadow_map = nullptr;
+}
+
+// Screens the chunk's queries whose candidate lists overflowed `cap`: their lists are rebuilt
+// from the BF16 pass. Returns the number of such queries in *nd_out.
+paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, int* nd_out, cudaStream_t st) {
+  *nd_out = 0;
+  DevBuf slots, ndbuf;
+  if (!slots.alloc((size_t)cs.qc * 4, st) || !ndbuf.alloc(4, st)) return fail(PARIS_ENOMEM, "dense scratch");
+  dense_select_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, slots.as<int>(), ndbuf.as<int>());
+  note_launches(1);
+  int nd = 0;
+  PARIS_CUDA(cudaMemcpyAsync(&nd, ndbuf.p, 4, cudaMemcpyDeviceToHost, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  *nd_out = nd;
+  if (nd == 0) return PARIS_OK;
+  PARIS_TRY(ensure_shadow(idx, st));
+  const int64_t nd_pad = ((int64_t)nd + BM - 1) / BM * BM;
+  DevBuf qbf, qnm;
+  if (!qbf.alloc((size_t)nd_pad * idx->len * 2, st) || !qnm.alloc((size_t)nd_pad * sizeof(float2), st))
+    return fail(PARIS_ENOMEM, "dense query tiles");
+  shadow_kernel<<<(unsigned)std::max<int64_t>(1, (nd_pad + 7) / 8), 256, 0, st>>>(
+      qs.queries, nd, idx->len, qbf.as<__nv_bfloat16>(), qnm.as<float2>(), slots.as<int>(), cs.q0, nd_pad);
+  dense_reset_kernel<<<(nd + 255) / 256, 256, 0, st>>>(cs.count, slots.as<int>(), nd);
+  note_launches(2);
+  PARIS_CUDA(cudaGetLastError());
+  CUtensorMap mapA;
+  PARIS_TRY(make_bf16_map(&mapA, qbf.p, nd_pad, idx->len, BM));
+  static bool attr = false;
+  if (!attr) {
+    PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
+    PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
+    attr = true;
+  }
+  DenseParams P;
+  P.n = idx->n;
+  P.len = idx->len;
+  P.nkb = idx->len / BKE;
+  P.nd = nd;
+  P.xnorm = idx->xnorm;
+  P.qnorm = qnm.as<float2>();
+  P.qslot = slots.as<int>();
+  P.q0 = cs.q0;
+  P.thr = qs.thr;
+  P.k = qs.k;
+  P.cg = qs.cg;
+  dense_margins(idx->len, &P.c1, &P.c2);
+  P.count = cs.count;
+  P.rows = cs.rows;
+  P.lb = cs.lb;
+  P.cap = cs.cap;
+  P.status = qs.status;
+  const int64_t ntiles = (idx->n + BN - 1) / BN;
+  const int grid = (int)std::min<int64_t>(ntiles, sm_count_dense());
+  const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;
+  for (int phase = 1; phase <= 2; ++phase) {
+    for (int t = 0; t < (int)(nd_pad / BM); ++t) {
+      P.qtile = t;
+      if (phase == 1)
+        dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);
+      else
+        dense_kernel<2><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);
+      note_launches(1);
+      PARIS_CUDA(cudaGetLastError());
+    }
+  }
+  return PARIS_OK;
+}
+
+}  // namespace paris

@@ -8,7 +8,8 @@ namespace {
 
 constexpr int kEncodeThreads = 256;
 
-template <int ITERS>
+// Two series per warp: lanes 0-15 hold the segments of series 2p, lanes 16-31 those of 2p+1.
+template <int SEGV>
 __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     const float* __restrict__ series, int64_t n, RowShape sh, int card, int bits,
     const uint64_t* __restrict__ beta_keys_g, uint8_t* __restrict__ sax_rot,
@@ -17,25 +18,32 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
   __shared__ uint64_t beta_keys[255];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = lane >> 4, seg = lane & 15;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t pairs = (n + 1) >> 1;
   bool nonfinite = false;
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
-    const float* row = series + r * (int64_t)sh.len;
+  for (int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pr < pairs; pr += warps) {
+    const int64_t r0 = 2 * pr;
+    const bool has1 = r0 + 1 < n;
+    const float* row0 = series + r0 * (int64_t)sh.len;
+    const float* row1 = has1 ? row0 + sh.len : nullptr;
     double paa = 0.0;
-    bool ok = warp_row_paa<ITERS>(row, sh, lane, paa);
-    if (!ok) nonfinite = true;
-    int sym = (lane < sh.w) ? symbol_of(paa, beta_keys, card) : 0;
-    uint64_t key = warp_key64(sym, lane, sh.w, bits);
+    if (!lane_segment_paa<SEGV>(row0, row1, sh, lane, paa)) nonfinite = true;
+    const int64_t r = r0 + half;
+    const bool rv = half == 0 || has1;
+    const int sym = (rv && seg < sh.w) ? symbol_of(paa, beta_keys, card) : 0;
+    const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     // rotated summary slot: slot j holds segment (j + r) mod 16 (0 when that segment >= w)
-    int seg = (lane + (int)(r & 15)) & 15;
-    int b = __shfl_sync(PARIS_FULL_MASK, sym, seg);
-    if (lane < PARIS_SAX_BYTES) sax_rot[r * PARIS_SAX_BYTES + lane] = (uint8_t)(seg < sh.w ? b : 0);
-    if (sax_plain && lane < sh.w) sax_plain[r * sh.w + lane] = (uint8_t)sym;
-    if (paa_out && lane < sh.w) paa_out[r * sh.w + lane] = paa;
-    if (lane == 0) key64[r] = key;
+    const int src = (seg + (int)(r & 15)) & 15;
+    const int b = __shfl_sync(PARIS_FULL_MASK, sym, (half << 4) | src);
+    if (rv) {
+      sax_rot[r * PARIS_SAX_BYTES + seg] = (uint8_t)(src < sh.w ? b : 0);
+      if (sax_plain && seg < sh.w) sax_plain[r * sh.w + seg] = (uint8_t)sym;
+      if (paa_out && seg < sh.w) paa_out[r * sh.w + seg] = paa;
+      if (seg == 0) key64[r] = key;
+    }
   }
-  if (nonfinite && lane == 0) atomicOr(status, DEV_NONFINITE);
+  if (nonfinite) atomicOr(status, DEV_NONFINITE);
 }
 
 __global__ void unrotate_kernel(const uint8_t* __restrict__ sax_rot, int64_t n, int w,
@@ -52,7 +60,7 @@ int encode_grid(int64_t n) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t want = (n + (kEncodeThreads / 32) - 1) / (kEncodeThreads / 32);
+  int64_t want = ((n + 1) / 2 + (kEncodeThreads / 32) - 1) / (kEncodeThreads / 32);
   int64_t cap = (int64_t)sms * 8;  // 8 resident blocks of 256 threads per SM
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
@@ -66,7 +74,7 @@ RowShape make_row_shape(int len, int w, const void* base_ptr) {
   sh.s = len / w;
   sh.log2s = ((sh.s & (sh.s - 1)) == 0) ? __builtin_ctz((unsigned)sh.s) : -1;
   bool aligned = ((uintptr_t)base_ptr % 16u) == 0u;
-  sh.fast = (len % 4 == 0) && aligned && sh.log2s >= 2 && sh.s <= 128 && len <= 128 * 16;
+  sh.fast = (len % 4 == 0) && aligned && sh.log2s >= 2 && sh.s <= 128;
   return sh;
 }
 
@@ -75,17 +83,19 @@ paris_status launch_encode(const float* series, int64_t n, const RowShape& sh, i
                            uint64_t* key64, double* paa, uint32_t* status, cudaStream_t st) {
   if (n <= 0) return PARIS_OK;
   int grid = encode_grid(n);
-  int iters = sh.fast ? (sh.len + 127) / 128 : 1;
-  if (iters <= 1)
-    encode_kernel<1><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, sax_plain, key64, paa, status);
-  else if (iters <= 2)
-    encode_kernel<2><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, sax_plain, key64, paa, status);
-  else if (iters <= 4)
-    encode_kernel<4><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, sax_plain, key64, paa, status);
-  else if (iters <= 8)
-    encode_kernel<8><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, sax_plain, key64, paa, status);
-  else
-    encode_kernel<16><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, sax_plain, key64, paa, status);
+  const int segv = sh.fast ? sh.s / 4 : 1;
+#define ENC(SV)                                                                                     \
+  encode_kernel<SV><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, \
+                                                     sax_plain, key64, paa, status)
+  switch (segv) {
+    case 1: ENC(1); break;
+    case 2: ENC(2); break;
+    case 4: ENC(4); break;
+    case 8: ENC(8); break;
+    case 16: ENC(16); break;
+    default: ENC(32); break;
+  }
+#undef ENC
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;

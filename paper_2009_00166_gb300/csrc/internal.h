@@ -22,6 +22,10 @@ struct paris_index {
   uint64_t* beta_keys = nullptr;    // device [card-1] order keys of the breakpoints
   double* beta_ext = nullptr;       // device [card+1]: -inf, beta_1..beta_{card-1}, +inf
   std::vector<double> beta_host;
+  // BF16 shadow of the series and fp32 row norms for the mixed-precision path (made on first use)
+  void* shadow = nullptr;       // device [n][len] bf16
+  float2* xnorm = nullptr;      // device [n]: (|x|^2, |x|) in fp32
+  void* shadow_map = nullptr;   // host copy of the TMA descriptor of the shadow (CUtensorMap)
 };
 
 namespace paris {

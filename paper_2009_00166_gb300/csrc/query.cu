@@ -95,7 +95,7 @@ __device__ __forceinline__ float warp_sq_dist_scalar(const float* __restrict__ x
 // T[c][i] = (len/w) * d_i(c)^2, d_i(c) = distance from PAA_i to the interval of symbol c
 // (Sec. 3.3.1: ABOVE / BELOW / IN), shrunk by a bound on the FP64 rounding of both PAA values
 // and rounded down to fp32, so that every table sum stays below the exact MINDIST^2.
-template <int ITERS>
+template <int SEGV>
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ queries, int64_t nq, RowShape sh,
                                                    int card, int bits, const uint64_t* __restrict__ beta_keys_g,
                                                    const double* __restrict__ beta_ext, double* __restrict__ qpaa,
@@ -104,33 +104,37 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
   __shared__ uint64_t beta_keys[255];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = lane >> 4, seg = lane & 15;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const double scale = (double)(sh.len / sh.w);
-  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += warps) {
+  const int64_t pairs = (nq + 1) >> 1;
+  for (int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pr < pairs; pr += warps) {
+    const int64_t q0 = 2 * pr;
+    const bool has1 = q0 + 1 < nq;
+    const float* row0 = queries + q0 * (int64_t)sh.len;
     double paa = 0.0;
-    bool ok = warp_row_paa<ITERS>(queries + q * (int64_t)sh.len, sh, lane, paa);
-    if (!ok && lane == 0) atomicOr(status, DEV_NONFINITE);
-    int sym = lane < sh.w ? symbol_of(paa, beta_keys, card) : 0;
-    uint64_t key = warp_key64(sym, lane, sh.w, bits);
-    if (lane < 16) qpaa[q * 16 + lane] = lane < sh.w ? paa : 0.0;
-    if (lane == 0) qkey[q] = key;
-    const int i = lane & 15;
-    const double P = __shfl_sync(PARIS_FULL_MASK, paa, i);
+    if (!lane_segment_paa<SEGV>(row0, has1 ? row0 + sh.len : nullptr, sh, lane, paa)) atomicOr(status, DEV_NONFINITE);
+    const int64_t q = q0 + half;
+    const bool qv = half == 0 || has1;
+    const int sym = (qv && seg < sh.w) ? symbol_of(paa, beta_keys, card) : 0;
+    const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
+    if (!qv) continue;
+    qpaa[q * 16 + seg] = seg < sh.w ? paa : 0.0;
+    if (seg == 0) qkey[q] = key;
+    const double P = paa;
     float* T = qtable + q * (int64_t)card * 16;
-    for (int e = lane; e < card * 16; e += 32) {
-      int c = e >> 4;
+    for (int c = 0; c < card; ++c) {
       float val = 0.f;
-      if (i < sh.w) {
-        double lo = beta_ext[c], hi = beta_ext[c + 1];
+      if (seg < sh.w) {
+        const double lo = beta_ext[c], hi = beta_ext[c + 1];
         double d = 0.0;
         if (P < lo) d = lo - P;
         else if (P > hi) d = P - hi;
-        double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
+        const double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
         d = fmax(0.0, d - mag * 0x1p-50);
         val = __double2float_rd(scale * d * d);
       }
-      T[e] = val;
+      T[c * 16 + seg] = val;
     }
   }
 }
@@ -294,12 +298,37 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
 // a shared-memory bank: row r keeps its symbols rotated by r mod 16 (build), so at step k the
 // 16 lanes of a half-warp read 16 different segments, and the two half-warps read different
 // copies. A byte permute forms each lookup address from the symbol byte and a per-lane offset.
+// Kept rows are staged per warp in shared memory and written out 32 at a time, so the global
+// candidate counter sees one atomic per 32 kept rows.
+constexpr int kStage = 64;  // staged (row, lb) pairs per warp
+
+// Writes out nflush staged pairs; returns false once the list has overflowed its capacity.
+__device__ __forceinline__ bool flush_stage(uint32_t* s_row, float* s_lb, int nflush, int lane,
+                                            uint32_t* count, uint32_t* out_rows, float* out_lb, int64_t cap,
+                                            uint32_t* status) {
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, (uint32_t)nflush);
+  base = __shfl_sync(PARIS_FULL_MASK, base, 0);
+  for (int i = lane; i < nflush; i += 32) {
+    uint32_t p = base + i;
+    if ((int64_t)p < cap) {
+      out_rows[p] = s_row[i];
+      out_lb[p] = s_lb[i];
+    } else {
+      atomicOr(status, DEV_CAND_OVERFLOW);
+    }
+  }
+  return (int64_t)base + nflush <= cap;
+}
+
 __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
     const uint4* __restrict__ sax, int64_t n, const float* __restrict__ table, int card,
     const uint32_t* __restrict__ thr_ptr, float thr_value, uint32_t* __restrict__ count,
     uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap,
-    uint32_t* __restrict__ status) {
+    uint32_t* __restrict__ status, int stop_on_overflow) {
   extern __shared__ __align__(16) float s_tab[];
+  __shared__ uint32_t s_stage_row[kLbThreads / 32][kStage];
+  __shared__ float s_stage_lb[kLbThreads / 32][kStage];
   for (int e = threadIdx.x; e < card * 16; e += blockDim.x) {
     float v = table[e];
     int c = e >> 4, i = e & 15;
@@ -308,7 +337,10 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
   }
   __syncthreads();
   const float thr = thr_ptr ? __uint_as_float(*thr_ptr) : thr_value;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* st_row = s_stage_row[wib];
+  float* st_lb = s_stage_lb[wib];
+  int fill = 0;  // warp-uniform number of staged pairs
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t offp[8];
 #pragma unroll
@@ -319,7 +351,7 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
   }
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
   const int64_t groups = (n + 31) >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t it = gw * kLbUnroll; it < groups; it += W * kLbUnroll) {
     uint4 word[kLbUnroll];
@@ -344,24 +376,33 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
       const bool keep = row < n && lb * kKeepScale <= thr;
       const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
       if (mk) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(mk));
-        base = __shfl_sync(PARIS_FULL_MASK, base, 0);
         if (keep) {
-          uint32_t p = base + __popc(mk & lt_mask);
-          if ((int64_t)p < cap) {
-            out_rows[p] = (uint32_t)row;
-            out_lb[p] = lb;
-          } else {
-            atomicOr(status, DEV_CAND_OVERFLOW);
+          int p = fill + __popc(mk & lt_mask);
+          st_row[p] = (uint32_t)row;
+          st_lb[p] = lb;
+        }
+        fill += __popc(mk);
+        __syncwarp();
+        if (fill >= 32) {
+          // an overflowed list is only a signal (the caller falls back); stop scanning early
+          if (!flush_stage(st_row, st_lb, 32, lane, count, out_rows, out_lb, cap, status) && stop_on_overflow) return;
+          __syncwarp();
+          if (lane < fill - 32) {
+            st_row[lane] = st_row[32 + lane];
+            st_lb[lane] = st_lb[32 + lane];
           }
+          fill -= 32;
+          __syncwarp();
         }
       }
     }
   }
+  if (fill > 0) flush_stage(st_row, st_lb, fill, lane, count, out_rows, out_lb, cap, status);
 }
 
 // --------------------------------------------------------------------- refinement (Alg. 9)
+// Per-query candidate segments are padded to multiples of 32 in the flat work space so that a
+// 32-candidate step of a warp never spans two queries.
 __global__ void chunk_prefix_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap,
                                     uint32_t* __restrict__ prefix, unsigned long long* __restrict__ counters) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -370,90 +411,172 @@ __global__ void chunk_prefix_kernel(const uint32_t* __restrict__ count, int qc, 
       prefix[j] = (uint32_t)acc;
       uint64_t c = count[j];
       raw += c;
-      acc += c < (uint64_t)cap ? c : (uint64_t)cap;
+      uint64_t m = c < (uint64_t)cap ? c : (uint64_t)cap;
+      acc += (m + 31) & ~(uint64_t)31;
     }
     prefix[qc] = (uint32_t)acc;
     atomicAdd(&counters[0], (unsigned long long)raw);
   }
 }
 
-// Warps take equal contiguous slices of the chunk's flattened candidate lists; each candidate
-// is re-tested against the current BSF threshold, then refined with early abandoning; a
-// completed distance lowers the query's BSF (k = 1: packed atomicMin; k <= 32: through a
-// warp-private top-k whose k-th value bounds the query's k-th best).
+// Each warp step takes 32 candidates of one query (one per lane), re-tests their lower bounds
+// against the query's current threshold (Alg. 9: minDist < BSF), then computes, one row at a
+// time with the whole warp, the early-abandoning distance of the survivors. A completed
+// distance lowers the query's BSF (k = 1: packed atomicMin; k <= 32: through a warp-private
+// top-k whose k-th value bounds the query's k-th best). Steps are interleaved across warps, so
+// all warps move through the lower-bound-ordered lists together.
 template <int ITERS>
 __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
     const float* __restrict__ series, int len, int vec, const float* __restrict__ queries, int64_t q0,
-    int qc, int64_t cap, const uint32_t* __restrict__ prefix, const uint32_t* __restrict__ rows,
-    const float* __restrict__ lbs, float* __restrict__ Fout, uint32_t* __restrict__ thr,
-    unsigned long long* __restrict__ bsf, int k, float cg, unsigned long long* __restrict__ counters) {
+    int qc, int64_t cap, const uint32_t* __restrict__ prefix, const uint32_t* __restrict__ count,
+    const uint32_t* __restrict__ rows, const float* __restrict__ lbs, float* __restrict__ Fout,
+    uint32_t* __restrict__ thr, unsigned long long* __restrict__ bsf, int k, float cg,
+    unsigned long long* __restrict__ counters) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = prefix[qc];
-  const int64_t per = (total + W - 1) / W;
-  const int64_t start = gw * per, end = min(total, start + per);
   int cur = -1;
-  int64_t next_bound = 0;
+  int64_t next_bound = 0, m_cur = 0;
   QVec<ITERS> qv;
   const float* qp = nullptr;
   float best = CUDART_INF_F;  // lane j < have: j-th best completed F of this warp and query
   int have = 0;
-  unsigned long long done = 0;
-  for (int64_t item = start; item < end; ++item) {
-    if (cur < 0 || item >= next_bound) {
+  unsigned long long touched = 0;
+  for (int64_t item0 = gw * 32; item0 < total; item0 += W * 32) {
+    if (cur < 0 || item0 >= next_bound) {
       if (cur < 0) {
-        int lo = 0, hi = qc;  // last j with prefix[j] <= item
+        int lo = 0, hi = qc;  // last j with prefix[j] <= item0
         while (hi - lo > 1) {
           int mid = (lo + hi) >> 1;
-          if ((int64_t)prefix[mid] <= item) lo = mid; else hi = mid;
+          if ((int64_t)prefix[mid] <= item0) lo = mid; else hi = mid;
         }
         cur = lo;
       } else {
-        while ((int64_t)prefix[cur + 1] <= item) ++cur;
+        while ((int64_t)prefix[cur + 1] <= item0) ++cur;
       }
       next_bound = prefix[cur + 1];
+      m_cur = count[cur];
+      if (m_cur > cap) m_cur = cap;
       qp = queries + (q0 + cur) * (int64_t)len;
       if (vec) qv.load(qp, len, lane);
       best = CUDART_INF_F;
       have = 0;
     }
     const int64_t qi = q0 + cur;
-    const int64_t slot = (int64_t)cur * cap + (item - prefix[cur]);
-    const uint32_t row = rows[slot];
-    const float lbv = lbs[slot];
-    const float t = __uint_as_float(ld_volatile_u32(thr + qi));
-    float F = CUDART_INF_F;
-    if (lbv * kKeepScale <= t) {
-      const float* xr = series + (int64_t)row * len;
-      F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, t) : warp_sq_dist_scalar(xr, qp, len, lane, t);
-    }
-    if (lane == 0) Fout[slot] = F;
-    if (F <= t) {
-      ++done;
-      if (k == 1) {
-        if (lane == 0) {
-          atomicMin(bsf + qi, ((unsigned long long)__float_as_uint(F) << 32) | row);
-          atomicMin(thr + qi, up_scaled_bits(F, cg));
-        }
-      } else if (k <= 32) {
-        uint32_t le = __ballot_sync(PARIS_FULL_MASK, lane < have && best <= F);
-        int p = __popc(le);
-        if (p < k) {
-          float prev = __shfl_up_sync(PARIS_FULL_MASK, best, 1);
-          if (lane == p) best = F;
-          else if (lane > p && lane < k) best = prev;
-          have = min(have + 1, k);
-          if (have == k) {
-            float kth = __shfl_sync(PARIS_FULL_MASK, best, k - 1);
-            uint32_t nb = up_scaled_bits(kth, cg);
-            if (lane == 0 && nb < __float_as_uint(t)) atomicMin(thr + qi, nb);
+    const int64_t i = item0 - prefix[cur] + lane;
+    const bool valid = i < m_cur;
+    const int64_t slot = (int64_t)cur * cap + i;
+    const uint32_t row = valid ? rows[slot] : 0u;
+    const float lbv = valid ? lbs[slot] : CUDART_INF_F;
+    float t = __uint_as_float(ld_volatile_u32(thr + qi));
+    uint32_t todo = __ballot_sync(PARIS_FULL_MASK, valid && lbv * kKeepScale <= t);
+    float myF = CUDART_INF_F;
+    while (todo) {
+      const int b = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t r = __shfl_sync(PARIS_FULL_MASK, row, b);
+      const float lb_b = __shfl_sync(PARIS_FULL_MASK, lbv, b);
+      t = fminf(t, __uint_as_float(ld_volatile_u32(thr + qi)));
+      if (lb_b * kKeepScale > t) continue;
+      ++touched;
+      const float* xr = series + (int64_t)r * len;
+      const float F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, t) : warp_sq_dist_scalar(xr, qp, len, lane, t);
+      if (lane == b) myF = F;
+      if (F <= t) {
+        if (k == 1) {
+          const uint32_t nb = up_scaled_bits(F, cg);
+          if (lane == 0) {
+            atomicMin(bsf + qi, ((unsigned long long)__float_as_uint(F) << 32) | r);
+            atomicMin(thr + qi, nb);
+          }
+          t = fminf(t, __uint_as_float(nb));
+        } else if (k <= 32) {
+          uint32_t le = __ballot_sync(PARIS_FULL_MASK, lane < have && best <= F);
+          int p = __popc(le);
+          if (p < k) {
+            float prev = __shfl_up_sync(PARIS_FULL_MASK, best, 1);
+            if (lane == p) best = F;
+            else if (lane > p && lane < k) best = prev;
+            have = min(have + 1, k);
+            if (have == k) {
+              float kth = __shfl_sync(PARIS_FULL_MASK, best, k - 1);
+              uint32_t nb = up_scaled_bits(kth, cg);
+              if (lane == 0 && nb < __float_as_uint(t)) atomicMin(thr + qi, nb);
+              t = fminf(t, __uint_as_float(nb));
+            }
           }
         }
       }
     }
+    if (valid) Fout[slot] = myF;
   }
-  if (lane == 0 && done) atomicAdd(&counters[1], done);
+  if (lane == 0 && touched) atomicAdd(&counters[1], touched);
+}
+
+// Candidate order for refinement: 32 buckets of LB / (seed threshold), lowest first, so that
+// the rows most likely to hold the answer tighten the best-so-far before the others are read.
+constexpr int kBuckets = 32;
+
+__device__ __forceinline__ int lb_bucket(float lb, float thr0) {
+  if (!(thr0 > 0.f)) return 0;
+  int b = (int)(lb * ((float)kBuckets / thr0));
+  return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
+}
+
+__global__ void bucket_hist_kernel(const float* __restrict__ lbs, const uint32_t* __restrict__ count, int64_t cap,
+                                   const uint32_t* __restrict__ thr, int64_t q0, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kBuckets];
+  const int j = blockIdx.y;
+  if (threadIdx.x < kBuckets) h[threadIdx.x] = 0u;
+  __syncthreads();
+  int64_t m = count[j];
+  if (m > cap) m = cap;
+  const float thr0 = __uint_as_float(thr[q0 + j]);
+  const float* lb = lbs + (int64_t)j * cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[lb_bucket(lb[i], thr0)], 1u);
+  __syncthreads();
+  if (threadIdx.x < kBuckets && h[threadIdx.x]) atomicAdd(&hist[j * kBuckets + threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void bucket_offsets_kernel(uint32_t* __restrict__ hist, int qc) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= qc) return;
+  uint32_t acc = 0;
+  for (int b = 0; b < kBuckets; ++b) {
+    uint32_t c = hist[j * kBuckets + b];
+    hist[j * kBuckets + b] = acc;  // becomes the running cursor of bucket b
+    acc += c;
+  }
+}
+
+__global__ void bucket_scatter_kernel(const uint32_t* __restrict__ rows, const float* __restrict__ lbs,
+                                      const uint32_t* __restrict__ count, int64_t cap,
+                                      const uint32_t* __restrict__ thr, int64_t q0, uint32_t* __restrict__ cursor,
+                                      uint32_t* __restrict__ rows2, float* __restrict__ lbs2) {
+  const int j = blockIdx.y;
+  int64_t m = count[j];
+  if (m > cap) m = cap;
+  const float thr0 = __uint_as_float(thr[q0 + j]);
+  const int64_t base = (int64_t)j * cap;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < m; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i < m;
+    float lb = valid ? lbs[base + i] : 0.f;
+    uint32_t r = valid ? rows[base + i] : 0u;
+    int b = valid ? lb_bucket(lb, thr0) : kBuckets;
+    uint32_t peers = __match_any_sync(PARIS_FULL_MASK, b);
+    uint32_t pos = 0;
+    if (valid && lane == __ffs(peers) - 1) pos = atomicAdd(&cursor[j * kBuckets + b], (uint32_t)__popc(peers));
+    pos = __shfl_sync(PARIS_FULL_MASK, pos, __ffs(peers) - 1) + __popc(peers & ((1u << lane) - 1u));
+    if (valid) {
+      rows2[base + pos] = r;
+      lbs2[base + pos] = lb;
+    }
+  }
 }
 
 // ------------------------------------------------------------- k-th selection and re-rank
@@ -709,18 +832,19 @@ int iters_for(int len) {
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st) {
   if (qs.nq <= 0) return PARIS_OK;
   RowShape sh = make_row_shape(idx->len, idx->w, qs.queries);
-  int64_t blocks = (qs.nq + 7) / 8;
+  int64_t blocks = ((qs.nq + 1) / 2 + 7) / 8;
   int grid = (int)std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
-  int it = sh.fast ? iters_for(idx->len) : 1;
-#define PREP(IT)                                                                              \
-  prep_kernel<IT><<<grid, 256, 0, st>>>(qs.queries, qs.nq, sh, idx->card, idx->bits, idx->beta_keys, \
-                                         idx->beta_ext, qs.qpaa, qs.qkey, qs.qtable, qs.status)
-  switch (it) {
+  const int segv = sh.fast ? sh.s / 4 : 1;
+#define PREP(SV)                                                                                      \
+  prep_kernel<SV><<<grid, 256, 0, st>>>(qs.queries, qs.nq, sh, idx->card, idx->bits, idx->beta_keys, \
+                                        idx->beta_ext, qs.qpaa, qs.qkey, qs.qtable, qs.status)
+  switch (segv) {
     case 1: PREP(1); break;
     case 2: PREP(2); break;
     case 4: PREP(4); break;
     case 8: PREP(8); break;
-    default: PREP(16); break;
+    case 16: PREP(16); break;
+    default: PREP(32); break;
   }
 #undef PREP
   note_launches(1);
@@ -764,7 +888,7 @@ paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaSt
 
 static paris_status lbscan_common(const paris_index* idx, const float* table, const uint32_t* thr_ptr,
                                   float thr_value, uint32_t* count, uint32_t* rows, float* lb,
-                                  int64_t cap, uint32_t* status, cudaStream_t st) {
+                                  int64_t cap, uint32_t* status, int stop_on_overflow, cudaStream_t st) {
   size_t smem = (size_t)idx->card * 64 * sizeof(float);
   static int configured_smem = 0;
   if ((int)smem > configured_smem) {
@@ -776,34 +900,45 @@ static paris_status lbscan_common(const paris_index* idx, const float* table, co
   int grid = (int)std::min<int64_t>(need_blocks, (int64_t)sm_count() * 2);
   if (grid < 1) grid = 1;
   lbscan_kernel<<<grid, kLbThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax), idx->n, table,
-                                                idx->card, thr_ptr, thr_value, count, rows, lb, cap, status);
+                                                idx->card, thr_ptr, thr_value, count, rows, lb, cap, status,
+                                                stop_on_overflow);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }
 
 paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t q, uint32_t* count,
-                           uint32_t* rows, float* lb, int64_t cap, cudaStream_t st) {
+                           uint32_t* rows, float* lb, int64_t cap, uint32_t* status, int stop_on_overflow,
+                           cudaStream_t st) {
   return lbscan_common(idx, qs.qtable + q * (int64_t)idx->card * 16, qs.thr + q, 0.f, count, rows, lb, cap,
-                       qs.status, st);
+                       status, stop_on_overflow, st);
 }
 
 paris_status launch_lbscan_threshold(const paris_index* idx, const float* table, float thr,
                                      uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
                                      uint32_t* status, cudaStream_t st) {
-  return lbscan_common(idx, table, nullptr, thr, count, rows, lb, cap, status, st);
+  return lbscan_common(idx, table, nullptr, thr, count, rows, lb, cap, status, 0, st);
 }
 
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st) {
   chunk_prefix_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, cs.prefix, qs.counters);
+  PARIS_CUDA(cudaMemsetAsync(cs.bucket, 0, (size_t)cs.qc * kBuckets * sizeof(uint32_t), st));
+  {
+    int64_t blocks_x = std::min<int64_t>((cs.cap + 255) / 256, 128);
+    dim3 g((unsigned)std::max<int64_t>(blocks_x, 1), (unsigned)cs.qc);
+    bucket_hist_kernel<<<g, 256, 0, st>>>(cs.lb, cs.count, cs.cap, qs.thr, cs.q0, cs.bucket);
+    bucket_offsets_kernel<<<(cs.qc + 127) / 128, 128, 0, st>>>(cs.bucket, cs.qc);
+    bucket_scatter_kernel<<<g, 256, 0, st>>>(cs.rows, cs.lb, cs.count, cs.cap, qs.thr, cs.q0, cs.bucket, cs.rows2,
+                                             cs.lb2);
+  }
   PARIS_CUDA(cudaGetLastError());
   int vec = vec_ok(idx, qs.queries) ? 1 : 0;
   int it = vec ? iters_for(idx->len) : 1;
   int grid = sm_count() * 8;
 #define REF(IT)                                                                                   \
   refine_kernel<IT><<<grid, kRefineThreads, 0, st>>>(idx->series, idx->len, vec, qs.queries, cs.q0, cs.qc, \
-                                                     cs.cap, cs.prefix, cs.rows, cs.lb, cs.F, qs.thr,      \
+                                                     cs.cap, cs.prefix, cs.count, cs.rows2, cs.lb2, cs.F, qs.thr, \
                                                      qs.bsf, qs.k, qs.cg, qs.counters)
   switch (it) {
     case 1: REF(1); break;
@@ -813,7 +948,7 @@ paris_status launch_refine(const paris_index* idx, const QueryState& qs, const C
     default: REF(16); break;
   }
 #undef REF
-  note_launches(2);
+  note_launches(5);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }
@@ -839,7 +974,7 @@ paris_status launch_select(const paris_index* idx, const QueryState& qs, const C
   {
     int64_t blocks_x = std::min<int64_t>((cs.cap + 255) / 256, 64);
     dim3 g((unsigned)std::max<int64_t>(blocks_x, 1), (unsigned)qc);
-    contenders_kernel<<<g, 256, 0, st>>>(cs.F, cs.rows, cs.count, cs.cap, cs.kth, qs.cg, cs.cont_count,
+    contenders_kernel<<<g, 256, 0, st>>>(cs.F, cs.rows2, cs.count, cs.cap, cs.kth, qs.cg, cs.cont_count,
                                          cs.cont_rows, qs.status);
   }
   rerank_kernel<<<qc, 256, 0, st>>>(idx->series, idx->len, qs.queries, cs.q0, cs.cont_count, cs.cont_rows,

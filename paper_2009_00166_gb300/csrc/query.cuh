@@ -33,7 +33,10 @@ struct ChunkState {
   uint32_t* count = nullptr;       // [qc]
   uint32_t* rows = nullptr;        // [qc][cap]
   float* lb = nullptr;             // [qc][cap]
-  float* F = nullptr;              // [qc][cap]
+  float* F = nullptr;              // [qc][cap], in the order of rows2
+  uint32_t* rows2 = nullptr;       // [qc][cap] candidates reordered by lower-bound bucket
+  float* lb2 = nullptr;            // [qc][cap]
+  uint32_t* bucket = nullptr;      // [qc][32] bucket counts, then cursors
   uint32_t* prefix = nullptr;      // [qc + 1]
   uint32_t* kth = nullptr;         // [qc] fp32 bits of the k-th smallest F
   uint32_t* sel_hist = nullptr;    // [qc][2048]
@@ -46,12 +49,21 @@ struct ChunkState {
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
 paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st);
 paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t q, uint32_t* count,
-                           uint32_t* rows, float* lb, int64_t cap, cudaStream_t st);
+                           uint32_t* rows, float* lb, int64_t cap, uint32_t* status, int stop_on_overflow,
+                           cudaStream_t st);
 paris_status launch_lbscan_threshold(const paris_index* idx, const float* table, float thr,
                                      uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
                                      uint32_t* status, cudaStream_t st);
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st);
+// Mixed-precision screening (dense.cu).
+bool dense_supported(const paris_index* idx, int k);
+void dense_margins(int len, float* c1, float* c2);
+paris_status ensure_shadow(paris_index* idx, cudaStream_t st);
+void release_shadow(paris_index* idx);
+paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, int* nd_out,
+                          cudaStream_t st);
+
 paris_status launch_select(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            int64_t* out_idx, float* out_dist, cudaStream_t st);
 

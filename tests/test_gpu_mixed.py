@@ -1,0 +1,68 @@
+"""Mixed precision (BF16 tensor-core screening + fp32 re-check): identical exact answers to the
+FP32 path and to the oracle, on queries whose lower bounds keep many rows (noise sigma >= 1),
+with ragged collection sizes, partial query tiles and k up to 16."""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu, rw, small_dataset, torch
+from oracle import knn as oknn
+
+pytestmark = pytest.mark.gpu
+
+
+def run(P, idx, q, k, precision, **kw):
+    Q = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+    i, d, st = P.paris_exact_knn_ex(idx, Q, k, precision=precision, want_stats=True, **kw)
+    torch.cuda.synchronize()
+    return i.cpu().numpy(), d.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("k", [1, 10, 16])
+def test_mixed_equals_oracle_hard_queries(k):
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    x = small_dataset()
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    src = synth.sigma_query_sources(x.shape[0], 70)
+    q = np.concatenate([synth.noisy_queries(x[src[:60]], 1.5, [9, 0]), synth.noisy_queries(x[src[60:]], 0.05, [9, 1]),
+                        synth.random_walk(7, 256, seed=77)])
+    gi, gd, st = run(P, idx, q, k, P.PARIS_REFINE_MIXED)
+    assert st["dense_queries"] > 0
+    fi, fd, _ = run(P, idx, q, k, P.PARIS_REFINE_FP32)
+    assert np.array_equal(gi, fi)
+    assert np.array_equal(gd, fd)
+    want_i, want_d = oknn.knn(x, q, k)
+    assert np.array_equal(gi, want_i)
+    assert np.allclose(gd, want_d, rtol=1e-5, atol=0)
+    idx.free()
+
+
+@pytest.mark.parametrize("n,length", [(30001, 256), (20000 + 63, 128), (9000, 64)])
+def test_mixed_ragged_shapes(n, length):
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    x = rw(n, length, 300 + length)
+    src = synth.sigma_query_sources(n, 131)
+    q = synth.noisy_queries(x[src], 2.0, [10, length])          # 131 queries: one full and one partial tile
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    for k in (1, 3):
+        gi, gd, st = run(P, idx, q, k, P.PARIS_REFINE_MIXED, chunk=200)
+        assert st["dense_queries"] > 0
+        want_i, want_d = oknn.knn(x, q, k)
+        assert np.array_equal(gi, want_i)
+        assert np.allclose(gd, want_d, rtol=1e-5, atol=0)
+    idx.free()
+
+
+def test_mixed_falls_back_when_unsupported():
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    x = rw(5000, 96, 5)                                          # len not a multiple of 64
+    q = rw(4, 96, 6)
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    gi, gd, st = run(P, idx, q, 2, P.PARIS_REFINE_MIXED)
+    assert st["dense_queries"] == 0
+    assert np.array_equal(gi, oknn.knn(x, q, 2)[0])
+    idx.free()
