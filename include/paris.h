@@ -115,6 +115,8 @@ typedef struct paris_query_stats {
   int64_t dense_queries; /* queries screened by the BF16 tensor-core path */
   double ms_prep, ms_descent, ms_lbscan, ms_refine, ms_select; /* device time per phase */
   double ms_dense;     /* device time of the BF16 screening (MIXED) */
+  int32_t query_tile;  /* queries per summary pass used by BATCHED mode (0 in PLAIN) */
+  int32_t reserved_stats;
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */

@@ -36,7 +36,8 @@ class QueryStats(C.Structure):
     _fields_ = [("candidates", C.c_int64), ("refined", C.c_int64), ("contenders", C.c_int64),
                 ("leaf_rows", C.c_int64), ("dense_queries", C.c_int64), ("ms_prep", C.c_double),
                 ("ms_descent", C.c_double), ("ms_lbscan", C.c_double), ("ms_refine", C.c_double),
-                ("ms_select", C.c_double), ("ms_dense", C.c_double)]
+                ("ms_select", C.c_double), ("ms_dense", C.c_double), ("query_tile", C.c_int32),
+                ("reserved_stats", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

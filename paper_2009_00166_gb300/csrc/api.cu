@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -199,6 +200,58 @@ struct PhaseTimer {
       }
   }
 };
+
+// Query tile of the batched scan for a (len, card) shape: the fastest of the candidate tiles per
+// query, timed once per shape on the first chunk that needs it, then remembered.
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, int> g_tuned;
+
+paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, const ChunkState& cs, cudaStream_t st,
+                              int* out) {
+  const auto key = std::make_pair(idx->len, idx->card);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      *out = it->second;
+      return PARIS_OK;
+    }
+  }
+  ChunkState sub = cs;
+  sub.qc = (int)std::min<int64_t>(cs.qc, 24);
+  DevBuf scratch_status;
+  if (!scratch_status.alloc(4, st)) return fail(PARIS_ENOMEM, "tuning scratch");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 2;
+  float best_t = 1e30f;
+  for (int i = 0; i < kNumQueryTiles; ++i) {
+    const int qt = kQueryTiles[i];
+    if (!query_tile_fits(qt, idx->card)) continue;
+    PARIS_CUDA(cudaMemsetAsync(sub.count, 0, (size_t)sub.qc * 4, st));
+    cudaEventRecord(e0, st);
+    paris_status s = launch_lbscan_batched(idx, qs, sub, qt, 1, scratch_status.as<uint32_t>(), st);
+    cudaEventRecord(e1, st);
+    if (s != PARIS_OK) return s;
+    PARIS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const int covered = (sub.qc + qt - 1) / qt * qt;  // queries the launch had room for
+    const float per_query = ms / (float)std::max(sub.qc, std::min(covered, sub.qc));
+    if (per_query < best_t) {
+      best_t = per_query;
+      best = qt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PARIS_CUDA(cudaMemsetAsync(sub.count, 0, (size_t)sub.qc * 4, st));
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned[key] = best;
+  *out = best;
+  return PARIS_OK;
+}
 
 }  // namespace
 
@@ -487,14 +540,27 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     cs.lb2 = (float*)(b + o_l2);
     cs.bucket = (uint32_t*)(b + o_bk);
   }
+  int qt = 0;
+  if (o.mode == PARIS_MODE_BATCHED && o.query_tile) {
+    qt = o.query_tile;
+    bool known = false;
+    for (int i = 0; i < kNumQueryTiles; ++i) known = known || kQueryTiles[i] == qt;
+    if (!known || !query_tile_fits(qt, idx->card))
+      return fail(PARIS_EINVAL, "query_tile %d is not one of 2, 4, 8, 12 or does not fit", qt);
+  }
   for (int64_t q0 = 0; q0 < nq; q0 += qc) {
     cs.q0 = q0;
     cs.qc = (int)std::min<int64_t>(qc, nq - q0);
     PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
+    if (o.mode == PARIS_MODE_BATCHED && qt == 0) PARIS_TRY(tuned_query_tile(idx, qs, cs, st, &qt));
     timer.begin(2);
-    for (int j = 0; j < cs.qc; ++j)
-      PARIS_TRY(launch_lbscan(idx, qs, q0 + j, cs.count + j, cs.rows + (int64_t)j * cap, cs.lb + (int64_t)j * cap,
-                              cap, lb_status, mixed ? 1 : 0, st));
+    if (o.mode == PARIS_MODE_BATCHED) {
+      PARIS_TRY(launch_lbscan_batched(idx, qs, cs, qt, mixed ? 1 : 0, lb_status, st));
+    } else {
+      for (int j = 0; j < cs.qc; ++j)
+        PARIS_TRY(launch_lbscan(idx, qs, q0 + j, cs.count + j, cs.rows + (int64_t)j * cap,
+                                cs.lb + (int64_t)j * cap, cap, lb_status, mixed ? 1 : 0, st));
+    }
     timer.end(2);
     if (mixed) {
       int nd = 0;
@@ -517,6 +583,7 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     double ms[6] = {0, 0, 0, 0, 0, 0};
     timer.collect(ms);
     stats->ms_dense = ms[5];
+    stats->query_tile = qt;
     stats->dense_queries = dense_total;
     stats->ms_prep = ms[0];
     stats->ms_descent = ms[1];

@@ -56,6 +56,13 @@ paris_status launch_lbscan_threshold(const paris_index* idx, const float* table,
                                      uint32_t* status, cudaStream_t st);
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st);
+// Batched lower-bound scan (batched.cu): one persistent launch for a chunk, tiles of qt queries.
+constexpr int kNumQueryTiles = 4;
+extern const int kQueryTiles[kNumQueryTiles];
+bool query_tile_fits(int qt, int card);
+paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,
+                                   int stop_on_overflow, uint32_t* status, cudaStream_t st);
+
 // Mixed-precision screening (dense.cu).
 bool dense_supported(const paris_index* idx, int k);
 void dense_margins(int len, float* c1, float* c2);

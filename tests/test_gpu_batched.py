@@ -1,0 +1,54 @@
+"""Batched lower-bound scans (a tile of queries per pass over the summaries, FP16 pair tables):
+identical exact answers to the plain one-query-per-pass method and to the oracle, for every
+query tile, odd batch sizes, both refinement precisions and k in {1, 10}."""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu, small_dataset, torch
+from oracle import knn as oknn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    x = small_dataset()
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    q, sig, _ = synth.mixed_sigma_queries(x, x.shape[0], 256, 37)
+    q = np.concatenate([q, synth.random_walk(4, 256, seed=2)])
+    want = {k: oknn.knn(x, q, k) for k in (1, 10)}
+    yield P, idx, q, want
+    idx.free()
+
+
+def run(P, idx, q, k, **kw):
+    i, d, st = P.paris_exact_knn_ex(idx, torch.from_numpy(q).cuda(), k, want_stats=True, **kw)
+    torch.cuda.synchronize()
+    return i.cpu().numpy(), d.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("qt", [0, 2, 4, 8, 12])
+@pytest.mark.parametrize("k", [1, 10])
+def test_batched_equals_oracle(setup, qt, k):
+    P, idx, q, want = setup
+    for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
+        gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=prec)
+        assert st["query_tile"] in (2, 4, 8, 12) and (qt == 0 or st["query_tile"] == qt)
+        assert np.array_equal(gi, want[k][0])
+        assert np.allclose(gd, want[k][1], rtol=1e-5, atol=0)
+
+
+def test_batched_equals_plain_and_small_chunks(setup):
+    P, idx, q, _ = setup
+    a = run(P, idx, q, 3, mode=P.PARIS_MODE_PLAIN)
+    b = run(P, idx, q, 3, mode=P.PARIS_MODE_BATCHED, query_tile=8, chunk=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_bad_query_tile(setup):
+    P, idx, q, _ = setup
+    with pytest.raises(P.ParisError):
+        run(P, idx, q, 1, mode=P.PARIS_MODE_BATCHED, query_tile=6)
