@@ -99,12 +99,18 @@ enum {
                              re-checked in fp32. Same exact answers. k <= 16. */
 };
 
+enum {
+  PARIS_SEED_DESCENT = 0, /* the approximate search visits the query key's leaf (Sec. 3.3) */
+  PARIS_SEED_LEARNED = 1, /* ... and the leaves of the attached model's top-r key buckets */
+};
+
 typedef struct paris_query_opts {
   int32_t mode;        /* PARIS_MODE_*; default PLAIN */
   int32_t query_tile;  /* queries per pass in BATCHED mode; 0 = pick automatically */
   int32_t chunk;       /* queries whose candidate lists are resident at once; 0 = automatic */
   int32_t precision;   /* PARIS_REFINE_*; default FP32 */
-  int32_t reserved[4]; /* must be zero */
+  int32_t seed;        /* PARIS_SEED_*; default DESCENT */
+  int32_t reserved[3]; /* must be zero */
 } paris_query_opts;
 
 typedef struct paris_query_stats {
@@ -170,6 +176,12 @@ paris_status paris_export_order(const paris_index* idx, uint64_t* out_keys, uint
 paris_status paris_encode(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
                           uint8_t* out_sax, uint64_t* out_key64, double* out_paa, void* stream);
 
+/* Approximate search with a seed mode (PARIS_SEED_*): as paris_approx_search; with
+ * PARIS_SEED_LEARNED the seed also covers the leaves of the attached model's top-r buckets
+ * (out_leaf still reports the query key's own leaf). */
+paris_status paris_approx_search_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                                    int32_t seed_mode, int64_t* out_leaf, float* out_seed_sq, void* stream);
+
 /* Approximate search alone (Sec. 3.3): per query, the sorted-position range [lo, hi) of its
  * leaf (device or host [nq][2] int64) and the seed -- the k-th smallest fp32 squared distance
  * among the leaf rows (device or host [nq] fp32, may be NULL). */
@@ -183,6 +195,44 @@ paris_status paris_approx_search(const paris_index* idx, const float* queries, i
 paris_status paris_lb_scan(const paris_index* idx, const float* query, float threshold_sq,
                            uint32_t* out_rows, float* out_lb, int64_t capacity, int64_t* out_count,
                            void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned best-so-far proposal (not in the paper; it only chooses which extra leaves the
+ * approximate search of Sec. 3.3 visits, so answers never change). An MLP maps a query's PAA
+ * (16 values) through 256 -> 256 (exact GELU) to 4096 logits over 12-bit key-prefix buckets
+ * (bucket = first 12 bits of the interleaved key = first bit of segments 0..11). BF16 weights
+ * for the GEMMs (tensor cores, FP32 accumulation), FP32 master weights, softmax cross-entropy,
+ * AdamW. Parameters travel as one FP32 host array in the order W1 [256][16], b1 [256],
+ * W2 [256][256], b2 [256], W3 [4096][256], b3 [4096] (1,122,816 values).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct paris_seed_model paris_seed_model;
+#define PARIS_SEED_MODEL_PARAMS 1122816
+
+/* Xavier-uniform weights from a splitmix64 stream seeded by init_seed, zero biases. */
+paris_status paris_seed_model_create(uint64_t init_seed, void* stream, paris_seed_model** out);
+void paris_seed_model_free(paris_seed_model* model); /* NULL-safe */
+paris_status paris_seed_model_set_weights(paris_seed_model* model, const float* params_host, void* stream);
+paris_status paris_seed_model_get_weights(const paris_seed_model* model, float* params_host, void* stream);
+/* Inputs are PAA vectors as paris_encode writes them: device FP64 [m][16] (unused segments 0). */
+/* logits (device [m][4096]) of device PAA inputs [m][16]. */
+paris_status paris_seed_model_forward(const paris_seed_model* model, const double* paa, int64_t m, float* logits,
+                                      void* stream);
+/* Mean cross-entropy of one batch (device paa [m][16], labels [m]) and its gradients (device
+ * [PARIS_SEED_MODEL_PARAMS], parameter order above); *loss_host may be NULL. No update. */
+paris_status paris_seed_model_gradients(const paris_seed_model* model, const double* paa, const int32_t* labels,
+                                        int32_t m, float* grads, float* loss_host, void* stream);
+/* `epochs` passes of AdamW (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay) over full
+ * batches of `batch` pairs visited in a pseudo-random order drawn from order_seed;
+ * loss_per_epoch (host [epochs], may be NULL) receives each epoch's mean loss. */
+paris_status paris_seed_model_train(paris_seed_model* model, const double* paa, const int32_t* labels, int64_t m,
+                                    int32_t batch, int32_t epochs, float lr, float weight_decay,
+                                    uint64_t order_seed, float* loss_per_epoch, void* stream);
+/* Lets PARIS_SEED_LEARNED queries on idx visit the leaves of the model's top_r buckets
+ * (1 <= top_r <= 8). The model is borrowed: keep it alive while attached; NULL detaches. */
+paris_status paris_attach_seed_model(paris_index* idx, const paris_seed_model* model, int32_t top_r);
+/* Training labels: the 12-bit bucket of each given row (device or host rows [m], out [m]). */
+paris_status paris_row_buckets(const paris_index* idx, const int64_t* rows, int64_t m, int32_t* out_buckets,
+                               void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Lower-bound scan without allocation. The paper has no counterpart: this entry point exists

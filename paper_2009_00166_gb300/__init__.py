@@ -13,11 +13,15 @@ from .binding import (  # noqa: F401
     PARIS_MODE_PLAIN,
     PARIS_REFINE_FP32,
     PARIS_REFINE_MIXED,
+    PARIS_SEED_DESCENT,
+    PARIS_SEED_LEARNED,
+    SeedModel,
     ParisError,
     ParisIndex,
     QueryStats,
     lib,
     paris_approx_search,
+    paris_attach_seed_model,
     paris_breakpoints,
     paris_build,
     paris_build_ex,
@@ -30,6 +34,7 @@ from .binding import (  # noqa: F401
     paris_index_describe,
     paris_kernel_launches,
     paris_lb_scan,
+    paris_row_buckets,
     paris_last_error,
     paris_set_allocator,
     use_torch_allocator,

@@ -12,6 +12,11 @@ PARIS_MODE_PLAIN = 0
 PARIS_MODE_BATCHED = 1
 PARIS_REFINE_FP32 = 0
 PARIS_REFINE_MIXED = 1
+PARIS_SEED_DESCENT = 0
+PARIS_SEED_LEARNED = 1
+SEED_MODEL_PARAMS = 1122816
+SEED_MODEL_SHAPES = [("W1", (256, 16)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (4096, 256)),
+                     ("b3", (4096,))]
 
 _STATUS = {0: "PARIS_OK", 1: "PARIS_EINVAL", 2: "PARIS_ENOMEM", 3: "PARIS_ECUDA", 4: "PARIS_ETIMEOUT",
            5: "PARIS_EINTERNAL"}
@@ -29,7 +34,7 @@ class BuildOpts(C.Structure):
 
 class QueryOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("query_tile", C.c_int32), ("chunk", C.c_int32),
-                ("precision", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("precision", C.c_int32), ("seed", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class QueryStats(C.Structure):
@@ -80,6 +85,16 @@ def lib():
             "paris_approx_search": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_lb_scan": ([VP, P, F32, P, P, I64, C.POINTER(I64), VP], I32),
             "paris_lb_scan_noalloc": ([VP, P, I64, P, P, P, I64, P, VP], I32),
+            "paris_approx_search_ex": ([VP, P, I64, I32, I32, P, P, VP], I32),
+            "paris_seed_model_create": ([C.c_uint64, VP, C.POINTER(VP)], I32),
+            "paris_seed_model_free": ([VP], None),
+            "paris_seed_model_set_weights": ([VP, P, VP], I32),
+            "paris_seed_model_get_weights": ([VP, P, VP], I32),
+            "paris_seed_model_forward": ([VP, P, I64, P, VP], I32),
+            "paris_seed_model_gradients": ([VP, P, P, I32, P, C.POINTER(F32), VP], I32),
+            "paris_seed_model_train": ([VP, P, P, I64, I32, I32, F32, F32, C.c_uint64, P, VP], I32),
+            "paris_attach_seed_model": ([VP, VP, I32], I32),
+            "paris_row_buckets": ([VP, P, I64, P, VP], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -165,7 +180,7 @@ def paris_free(index: ParisIndex):
 
 def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, mode: int = PARIS_MODE_PLAIN,
                        query_tile: int = 0, chunk: int = 0, precision: int = PARIS_REFINE_FP32,
-                       want_stats: bool = False, stream=None):
+                       seed: int = PARIS_SEED_DESCENT, want_stats: bool = False, stream=None):
     """paris_exact_knn_ex: returns (idx [nq][k] int64, dist [nq][k] float32[, stats dict]).
 
     Outputs are allocated like the queries (same device) when not given.
@@ -177,7 +192,7 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
         out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision)
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed)
     stats = QueryStats()
     _check(lib().paris_exact_knn_ex(index.handle, _ptr(queries), nq, k, _ptr(out_idx), _ptr(out_dist),
                                     C.byref(opts), C.byref(stats) if want_stats else None, _stream(stream)))
@@ -231,13 +246,14 @@ def paris_encode(series, w: int = 16, card: int = 256, want_paa: bool = False, s
     return (sax, key, paa) if want_paa else (sax, key)
 
 
-def paris_approx_search(index: ParisIndex, queries, k: int = 1, stream=None):
-    """paris_approx_search: (leaf [nq][2] int64 sorted-position ranges, seed [nq] float32)."""
+def paris_approx_search(index: ParisIndex, queries, k: int = 1, seed_mode: int = PARIS_SEED_DESCENT, stream=None):
+    """paris_approx_search(_ex): (leaf [nq][2] int64 sorted-position ranges, seed [nq] float32)."""
     import torch
     nq = int(queries.shape[0])
     leaf = torch.empty((nq, 2), dtype=torch.int64, device=queries.device)
     seed = torch.empty((nq,), dtype=torch.float32, device=queries.device)
-    _check(lib().paris_approx_search(index.handle, _ptr(queries), nq, k, _ptr(leaf), _ptr(seed), _stream(stream)))
+    _check(lib().paris_approx_search_ex(index.handle, _ptr(queries), nq, k, seed_mode, _ptr(leaf), _ptr(seed),
+                                        _stream(stream)))
     return leaf, seed
 
 
@@ -281,3 +297,85 @@ def use_torch_allocator():
         torch.cuda.caching_allocator_delete(ptr)
 
     paris_set_allocator(_a, _f)
+
+
+class SeedModel:
+    """Handle of a learned best-so-far proposal network (paris_seed_model_*)."""
+
+    def __init__(self, init_seed: int = 0, stream=None):
+        out = C.c_void_p()
+        _check(lib().paris_seed_model_create(init_seed, _stream(stream), C.byref(out)))
+        self.handle = out.value
+
+    def free(self):
+        if self.handle:
+            lib().paris_seed_model_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def set_weights(self, params: dict):
+        import numpy as np
+        flat = np.concatenate([np.asarray(params[k], np.float32).ravel() for k, _ in SEED_MODEL_SHAPES])
+        assert flat.size == SEED_MODEL_PARAMS
+        _check(lib().paris_seed_model_set_weights(self.handle, flat.ctypes.data, _stream(None)))
+
+    def get_weights(self) -> dict:
+        import numpy as np
+        flat = np.empty(SEED_MODEL_PARAMS, np.float32)
+        _check(lib().paris_seed_model_get_weights(self.handle, flat.ctypes.data, _stream(None)))
+        return _split(flat)
+
+    def forward(self, paa):
+        """paris_seed_model_forward on device FP64 PAA [m][16]: device logits [m][4096]."""
+        import torch
+        m = int(paa.shape[0])
+        out = torch.empty((m, 4096), dtype=torch.float32, device=paa.device)
+        _check(lib().paris_seed_model_forward(self.handle, _ptr(paa), m, _ptr(out), _stream(None)))
+        return out
+
+    def gradients(self, paa, labels):
+        import torch
+        m = int(paa.shape[0])
+        g = torch.empty(SEED_MODEL_PARAMS, dtype=torch.float32, device=paa.device)
+        loss = C.c_float()
+        _check(lib().paris_seed_model_gradients(self.handle, _ptr(paa), _ptr(labels), m, _ptr(g), C.byref(loss),
+                                                _stream(None)))
+        return float(loss.value), _split(g.cpu().numpy())
+
+    def train(self, paa, labels, batch=256, epochs=1, lr=1e-3, weight_decay=0.0, order_seed=0):
+        import numpy as np
+        losses = np.zeros(max(epochs, 1), np.float32)
+        _check(lib().paris_seed_model_train(self.handle, _ptr(paa), _ptr(labels), int(paa.shape[0]), batch, epochs,
+                                            lr, weight_decay, order_seed, losses.ctypes.data, _stream(None)))
+        return losses[:epochs]
+
+
+def _split(flat):
+    out, o = {}, 0
+    for k, shp in SEED_MODEL_SHAPES:
+        n = 1
+        for d in shp:
+            n *= d
+        out[k] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def paris_attach_seed_model(index: ParisIndex, model, top_r: int = 3):
+    _check(lib().paris_attach_seed_model(index.handle, model.handle if model is not None else None, top_r))
+    index._seed_model = model
+
+
+def paris_row_buckets(index: ParisIndex, rows):
+    """12-bit key-prefix bucket of each row (numpy or device int64 rows)."""
+    import numpy as np
+    rows = np.ascontiguousarray(np.asarray(rows, np.int64))
+    out = np.empty(rows.size, np.int32)
+    _check(lib().paris_row_buckets(index.handle, rows.ctypes.data, rows.size, out.ctypes.data, _stream(None)))
+    return out
+

@@ -467,8 +467,11 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   if (nq > 0 && !out_idx) return fail(PARIS_EINVAL, "out_idx is NULL");
   paris_query_opts o{};
   if (opts) o = *opts;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
+  if (o.seed == PARIS_SEED_LEARNED && !idx->seed_model)
+    return fail(PARIS_EINVAL, "PARIS_SEED_LEARNED needs a model attached with paris_attach_seed_model");
   if (o.precision != PARIS_REFINE_FP32 && o.precision != PARIS_REFINE_MIXED)
     return fail(PARIS_EINVAL, "unknown precision %d", o.precision);
   if (o.mode != PARIS_MODE_PLAIN && o.mode != PARIS_MODE_BATCHED)
@@ -489,6 +492,13 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   PARIS_TRY(launch_query_prep(idx, qs, st));
   timer.end(0);
   timer.begin(1);
+  DevBuf lkeys;
+  if (o.seed == PARIS_SEED_LEARNED) {
+    if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
+    PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
+    qs.keys = lkeys.as<uint64_t>();
+    qs.nk = idx->seed_r + 1;
+  }
   PARIS_TRY(launch_descent(idx, qs, st));
   timer.end(1);
   // chunks of queries whose candidate lists are resident together; in MIXED precision the lists
@@ -608,8 +618,47 @@ paris_status paris_exact_knn(const paris_index* idx, const float* queries, int64
 
 paris_status paris_approx_search(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
                                  int64_t* out_leaf, float* out_seed_sq, void* stream) {
+  return paris_approx_search_ex(idx, queries, nq, k, PARIS_SEED_DESCENT, out_leaf, out_seed_sq, stream);
+}
+
+paris_status paris_attach_seed_model(paris_index* idx, const paris_seed_model* model, int32_t top_r) {
+  clear_error();
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  if (model && (top_r < 1 || top_r > 8)) return fail(PARIS_EINVAL, "top_r must be in [1, 8]");
+  if (model && (int64_t)(top_r + 1) * std::max(idx->leaf_cap, 16) > 16384)
+    return fail(PARIS_EINVAL, "top_r + 1 leaves of %d rows exceed the approximate search's buffer", idx->leaf_cap);
+  idx->seed_model = model;
+  idx->seed_r = model ? top_r : 0;
+  return PARIS_OK;
+}
+
+paris_status paris_row_buckets(const paris_index* idx, const int64_t* rows, int64_t m, int32_t* out_buckets,
+                               void* stream) {
+  clear_error();
+  if (!idx || (m > 0 && (!rows || !out_buckets))) return fail(PARIS_EINVAL, "NULL argument");
+  if (m <= 0) return PARIS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sr, so;
+  PARIS_TRY(sr.in(rows, (size_t)m * 8, st));
+  PARIS_TRY(so.out(out_buckets, (size_t)m * 4, st));
+  DevBuf status;
+  if (!status.alloc(4, st)) return fail(PARIS_ENOMEM, "status");
+  PARIS_CUDA(cudaMemsetAsync(status.p, 0, 4, st));
+  PARIS_TRY(launch_row_buckets(idx, (const int64_t*)sr.dev, m, (int32_t*)so.dev, status.as<uint32_t>(), st));
+  PARIS_TRY(so.finish(st));
+  uint32_t s = 0;
+  PARIS_CUDA(cudaMemcpyAsync(&s, status.p, 4, cudaMemcpyDeviceToHost, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  if (s & DEV_BADROW) return fail(PARIS_EINVAL, "paris_row_buckets: row index outside [0, n)");
+  return PARIS_OK;
+}
+
+paris_status paris_approx_search_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                                    int32_t seed_mode, int64_t* out_leaf, float* out_seed_sq, void* stream) {
   clear_error();
   PARIS_TRY(check_query_args(idx, queries, nq, k));
+  if (seed_mode != PARIS_SEED_DESCENT && seed_mode != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
+  if (seed_mode == PARIS_SEED_LEARNED && !idx->seed_model) return fail(PARIS_EINVAL, "no seed model attached");
   if (nq == 0) return PARIS_OK;
   if (!out_leaf) return fail(PARIS_EINVAL, "out_leaf is NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -621,6 +670,13 @@ paris_status paris_approx_search(const paris_index* idx, const float* queries, i
   DevBuf qblock;
   PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
   PARIS_TRY(launch_query_prep(idx, qs, st));
+  DevBuf lkeys;
+  if (seed_mode == PARIS_SEED_LEARNED) {
+    if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
+    PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
+    qs.keys = lkeys.as<uint64_t>();
+    qs.nk = idx->seed_r + 1;
+  }
   PARIS_TRY(launch_descent(idx, qs, st));
   PARIS_CUDA(cudaMemcpyAsync(sl.dev, qs.leaf, (size_t)nq * 16, cudaMemcpyDeviceToDevice, st));
   if (out_seed_sq) PARIS_CUDA(cudaMemcpyAsync(ss.dev, qs.seed, (size_t)nq * 4, cudaMemcpyDeviceToDevice, st));

@@ -14,6 +14,7 @@ enum : uint32_t {
   DEV_CAND_OVERFLOW = 2u,  // a candidate list overflowed its capacity
   DEV_CONT_OVERFLOW = 4u,  // too many exact-re-rank contenders
   DEV_TIMEOUT = 8u,        // a bounded wait expired
+  DEV_BADROW = 16u,        // a row index outside the collection
 };
 
 __device__ __forceinline__ uint64_t double_order_key(double v) {

@@ -26,6 +26,9 @@ struct paris_index {
   void* shadow = nullptr;       // device [n][len] bf16
   float2* xnorm = nullptr;      // device [n]: (|x|^2, |x|) in fp32
   void* shadow_map = nullptr;   // host copy of the TMA descriptor of the shadow (CUtensorMap)
+  // learned approximate-search proposal (borrowed; see paris_attach_seed_model)
+  const paris_seed_model* seed_model = nullptr;
+  int seed_r = 0;
 };
 
 namespace paris {

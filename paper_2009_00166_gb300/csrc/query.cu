@@ -191,78 +191,98 @@ __device__ __forceinline__ int smem_upper_bound(const uint64_t* a, int m, uint64
   return lo;
 }
 
-// One CTA per query: find the leaf of the fixed-order trie that holds the query key's
-// position (Sec. 3.3 approximate search), compute the distance to every series in it and
-// seed the best-so-far with the k-th smallest.
+// One CTA per query: for each of the query's nk keys (its own key first, then any learned
+// bucket keys), find the leaf of the fixed-order trie that holds that key's position (Sec. 3.3
+// approximate search); compute the distance to every series of the distinct leaves and seed the
+// best-so-far with the k-th smallest. The leaf range reported is the own key's.
 template <int ITERS>
 __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
     const float* __restrict__ series, int64_t n, int len, int vec, const uint64_t* __restrict__ keys,
     const uint32_t* __restrict__ rows_sorted, int leaf_cap, int k, const float* __restrict__ queries,
-    const uint64_t* __restrict__ qkey, int64_t* __restrict__ leaf_out, float* __restrict__ seed_out,
+    const uint64_t* __restrict__ qkeys, int nk, int64_t* __restrict__ leaf_out, float* __restrict__ seed_out,
     uint32_t* __restrict__ thr, unsigned long long* __restrict__ bsf, float cg,
     unsigned long long* __restrict__ counters) {
-  extern __shared__ __align__(16) uint64_t s_buf[];
+  extern __shared__ __align__(16) uint64_t s_mem[];
+  const int Lp = max(leaf_cap, k);
+  uint64_t* s_win = s_mem;               // [2 Lp + 1] keys of the window around a position
+  uint64_t* s_buf = s_mem + (2 * Lp + 2);  // (F, row) pairs of all visited leaves
   __shared__ int64_t s_bounds[2];
   __shared__ int64_t s_lo[65], s_hi[65];
   __shared__ int s_best;
-  __shared__ int64_t s_leaf[2];
+  __shared__ int64_t s_rng[16][2];
+  __shared__ int s_dup;
   const int64_t q = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint64_t x = qkey[q];
-  const int Lp = max(leaf_cap, k);
-
-  int64_t pos0 = cta_lower_bound(keys, n, x, s_bounds);
-  const bool clamped = pos0 >= n;
-  const int64_t pos = clamped ? n - 1 : pos0;
-  const uint64_t anchor = keys[pos];
-  const int64_t wa = max((int64_t)0, pos - Lp), wb = min(n, pos + Lp + 1);
-  const int wn = (int)(wb - wa);
-  for (int i = t; i < wn; i += blockDim.x) s_buf[i] = keys[wa + i];
-  if (t == 0) s_best = 65;
-  __syncthreads();
-  if (t <= 64) {
-    uint64_t mask = t == 0 ? 0ull : (~0ull << (64 - t));
-    int64_t lo = wa + smem_lower_bound(s_buf, wn, anchor & mask);
-    int64_t hi = wa + smem_upper_bound(s_buf, wn, anchor | ~mask);
-    bool inside = !(lo == wa && wa > 0) && !(hi == wb && wb < n);
-    s_lo[t] = lo;
-    s_hi[t] = hi;
-    if (inside && hi - lo <= Lp) atomicMin(&s_best, t);
-  }
-  __syncthreads();
-  int best = s_best;
-  int64_t lo, hi;
-  if (best <= 64) {
-    lo = s_lo[best];
-    hi = s_hi[best];
-    if (hi - lo < k) {
-      lo = min(lo, n - k);
-      hi = lo + k;
-    }
-  } else {
-    // even the full key is shared by more than Lp rows: take the first Lp rows of that run
-    int64_t start = clamped ? cta_lower_bound(keys, n, anchor, s_bounds) : pos;
-    lo = start;
-    hi = start + Lp;
-  }
-  __syncthreads();  // s_buf (window) is reused below
-  const int m = (int)(hi - lo);
-  int P2 = 1;
-  while (P2 < m) P2 <<= 1;
   const float* qp = queries + q * (int64_t)len;
   QVec<ITERS> qv;
   if (vec) qv.load(qp, len, lane);
-  for (int i = warp; i < P2; i += blockDim.x >> 5) {
-    if (i < m) {
-      uint32_t row = rows_sorted[lo + i];
-      const float* xr = series + (int64_t)row * len;
-      float F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, CUDART_INF_F)
-                    : warp_sq_dist_scalar(xr, qp, len, lane, CUDART_INF_F);
-      if (lane == 0) s_buf[i] = ((unsigned long long)__float_as_uint(F) << 32) | row;
-    } else if (lane == 0) {
-      s_buf[i] = ~0ull;
+  int filled = 0;
+  for (int j = 0; j < nk; ++j) {
+    const uint64_t x = qkeys[q * nk + j];
+    int64_t pos0 = cta_lower_bound(keys, n, x, s_bounds);
+    const bool clamped = pos0 >= n;
+    const int64_t pos = clamped ? n - 1 : pos0;
+    const uint64_t anchor = keys[pos];
+    const int64_t wa = max((int64_t)0, pos - Lp), wb = min(n, pos + Lp + 1);
+    const int wn = (int)(wb - wa);
+    for (int i = t; i < wn; i += blockDim.x) s_win[i] = keys[wa + i];
+    if (t == 0) s_best = 65;
+    __syncthreads();
+    if (t <= 64) {
+      uint64_t mask = t == 0 ? 0ull : (~0ull << (64 - t));
+      int64_t lo = wa + smem_lower_bound(s_win, wn, anchor & mask);
+      int64_t hi = wa + smem_upper_bound(s_win, wn, anchor | ~mask);
+      bool inside = !(lo == wa && wa > 0) && !(hi == wb && wb < n);
+      s_lo[t] = lo;
+      s_hi[t] = hi;
+      if (inside && hi - lo <= Lp) atomicMin(&s_best, t);
     }
+    __syncthreads();
+    const int best = s_best;
+    int64_t lo, hi;
+    if (best <= 64) {
+      lo = s_lo[best];
+      hi = s_hi[best];
+      if (hi - lo < k) {
+        lo = min(lo, n - k);
+        hi = lo + k;
+      }
+    } else {
+      // even the full key is shared by more than Lp rows: take the first Lp rows of that run
+      int64_t start = clamped ? cta_lower_bound(keys, n, anchor, s_bounds) : pos;
+      lo = start;
+      hi = start + Lp;
+    }
+    if (t == 0) {
+      int dup = 0;
+      for (int i = 0; i < j && i < 16; ++i) dup |= (s_rng[i][0] == lo && s_rng[i][1] == hi);
+      if (j < 16) {
+        s_rng[j][0] = lo;
+        s_rng[j][1] = hi;
+      }
+      s_dup = dup;
+      if (j == 0) {
+        leaf_out[2 * q] = lo;
+        leaf_out[2 * q + 1] = hi;
+      }
+    }
+    __syncthreads();
+    if (!s_dup) {
+      const int m = (int)(hi - lo);
+      for (int i = warp; i < m; i += blockDim.x >> 5) {
+        uint32_t row = rows_sorted[lo + i];
+        const float* xr = series + (int64_t)row * len;
+        float F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, CUDART_INF_F)
+                      : warp_sq_dist_scalar(xr, qp, len, lane, CUDART_INF_F);
+        if (lane == 0) s_buf[filled + i] = ((unsigned long long)__float_as_uint(F) << 32) | row;
+      }
+      filled += m;
+    }
+    __syncthreads();
   }
+  int P2 = 1;
+  while (P2 < filled) P2 <<= 1;
+  for (int i = filled + t; i < P2; i += blockDim.x) s_buf[i] = ~0ull;
   __syncthreads();
   // bitonic sort of (F, row) pairs, ascending
   for (int size = 2; size <= P2; size <<= 1) {
@@ -283,12 +303,10 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
   if (t == 0) {
     uint64_t kth = s_buf[k - 1];
     float Fk = __uint_as_float((uint32_t)(kth >> 32));
-    leaf_out[2 * q] = lo;
-    leaf_out[2 * q + 1] = hi;
     seed_out[q] = Fk;
     thr[q] = up_scaled_bits(Fk, cg);
     bsf[q] = s_buf[0];
-    atomicAdd(&counters[3], (unsigned long long)m);
+    atomicAdd(&counters[3], (unsigned long long)filled);
   }
 }
 
@@ -860,18 +878,21 @@ static bool vec_ok(const paris_index* idx, const float* q) {
 paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st) {
   if (qs.nq <= 0) return PARIS_OK;
   const int Lp = max(idx->leaf_cap, qs.k);
+  const int nk = qs.keys ? qs.nk : 1;
   int P2 = 1;
-  while (P2 < Lp) P2 <<= 1;
-  size_t smem = (size_t)max(2 * Lp + 1, P2) * sizeof(uint64_t);
+  while (P2 < nk * Lp) P2 <<= 1;
+  size_t smem = (size_t)(2 * Lp + 2 + P2) * sizeof(uint64_t);
+  if (smem > 220 * 1024) return fail(PARIS_EINVAL, "too many leaves per query for the approximate search");
   int vec = vec_ok(idx, qs.queries) ? 1 : 0;
   int it = vec ? iters_for(idx->len) : 1;
+  const uint64_t* qk = qs.keys ? qs.keys : qs.qkey;
 #define DESC(IT)                                                                                 \
   do {                                                                                           \
     PARIS_CUDA(cudaFuncSetAttribute(descent_kernel<IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)smem));                                                 \
     descent_kernel<IT><<<(unsigned)qs.nq, kDescentThreads, smem, st>>>(                          \
         idx->series, idx->n, idx->len, vec, idx->keys_sorted, idx->rows_sorted, idx->leaf_cap, qs.k, \
-        qs.queries, qs.qkey, qs.leaf, qs.seed, qs.thr, qs.bsf, qs.cg, qs.counters);              \
+        qs.queries, qk, nk, qs.leaf, qs.seed, qs.thr, qs.bsf, qs.cg, qs.counters);               \
   } while (0)
   switch (it) {
     case 1: DESC(1); break;

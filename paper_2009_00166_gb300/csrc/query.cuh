@@ -23,6 +23,8 @@ struct QueryState {
   uint32_t* status = nullptr;      // [1]
   unsigned long long* counters = nullptr;  // [4]: candidates, refined, contenders, leaf rows
   float cg = 1.f;                  // (1+gamma)/(1-gamma), rounded up, gamma = gamma_{len+2}
+  const uint64_t* keys = nullptr;  // [nq][nk] approximate-search keys (NULL: qkey only)
+  int nk = 1;
 };
 
 // Candidate lists of a chunk of queries [q0, q0 + qc).
@@ -62,6 +64,12 @@ extern const int kQueryTiles[kNumQueryTiles];
 bool query_tile_fits(int qt, int card);
 paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,
                                    int stop_on_overflow, uint32_t* status, cudaStream_t st);
+
+// Learned approximate-search keys (mlp.cu): [nq][r+1], own key first.
+paris_status learned_keys(const paris_index* idx, const paris_seed_model* md, int r, const QueryState& qs,
+                          uint64_t* keys, cudaStream_t st);
+paris_status launch_row_buckets(const paris_index* idx, const int64_t* rows, int64_t m, int32_t* out,
+                                uint32_t* status, cudaStream_t st);
 
 // Mixed-precision screening (dense.cu).
 bool dense_supported(const paris_index* idx, int k);
