@@ -35,8 +35,13 @@ def parse():
     p.add_argument("--len", type=int, default=256)
     p.add_argument("--per-sigma", type=int, default=1000)
     p.add_argument("--k", type=int, default=1)
-    p.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    p.add_argument("--mode", default="batched", choices=["plain", "batched"])
     p.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
+    p.add_argument("--seed", default="descent", choices=["descent", "learned"])
+    p.add_argument("--no-learned-comparison", action="store_true",
+                   help="skip training the seed model and the learned-seed comparison runs")
+    p.add_argument("--train-queries", type=int, default=20000, help="(query, true-NN bucket) pairs for the seed model")
+    p.add_argument("--train-epochs", type=int, default=10)
     p.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain fp32 method shown beside")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
@@ -223,6 +228,7 @@ def main():
     n, length, k = args.n, args.len, args.k
     mode = P.PARIS_MODE_BATCHED if args.mode == "batched" else P.PARIS_MODE_PLAIN
     precision = P.PARIS_REFINE_MIXED if args.precision == "mixed" else P.PARIS_REFINE_FP32
+    seed_mode = P.PARIS_SEED_LEARNED if args.seed == "learned" else P.PARIS_SEED_DESCENT
     host, qhost, sig, _ = make_workload(n, length, args.per_sigma, rank)
     X = host.to(dev)
     Q = qhost.to(dev)
@@ -230,14 +236,42 @@ def main():
     nq = Q.shape[0]
     stream = torch.cuda.current_stream()
 
-    def step(collect=None, md=mode, prec=precision, answers=None):
+    # ---- learned best-so-far proposal: trained before the timed region on (query PAA, bucket of
+    # its exact nearest neighbour) pairs that the exact method itself labels
+    model, training = None, None
+    want_model = seed_mode == P.PARIS_SEED_LEARNED or (not args.no_learned_comparison and args.plain_steps > 0)
+    if want_model:
+        import synth
+        t0 = time.perf_counter()
+        tq_np, _, _ = synth.mixed_sigma_queries(host.numpy(), n, length, args.train_queries, 0.1, 1.0, seed=20)
+        tq = torch.from_numpy(tq_np).to(dev)
+        idx = P.paris_build(X, 16, 256)
+        nn_rows, _ = P.paris_exact_knn_ex(idx, tq, 1, mode=mode, precision=precision)
+        labels = P.paris_row_buckets(idx, nn_rows.cpu().numpy()[:, 0])
+        idx.free()
+        _, _, tpaa = P.paris_encode(tq, 16, 256, want_paa=True)
+        t1 = time.perf_counter()
+        model = P.SeedModel(1)
+        losses = model.train(tpaa, torch.from_numpy(labels).to(dev), batch=512, epochs=args.train_epochs, lr=2e-3,
+                             order_seed=2)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        training = {"pairs": args.train_queries, "label_s": t1 - t0, "train_s": t2 - t1,
+                    "epochs": args.train_epochs, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                    "top_r": 3}
+        del tq, tpaa
+
+    def step(collect=None, md=mode, prec=precision, sd=seed_mode, answers=None, split=False):
+        """Build, then answer every query: one call for the whole batch, or one per sigma group."""
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         idx = P.paris_build(X, 16, 256)
         e1.record(stream)
+        if sd == P.PARIS_SEED_LEARNED:
+            P.paris_attach_seed_model(idx, model, 3)
         per_sigma_stats = []
-        for g in groups:
-            out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, want_stats=collect is not None)
+        for g in (groups if split else [Q]):
+            out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, seed=sd, want_stats=collect is not None)
             if collect is not None:
                 per_sigma_stats.append(out[2])
             if answers is not None:
@@ -276,18 +310,46 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
 
-    # ---- the plain method (one query per lower-bound pass, fp32 refinement) beside it
-    plain = None
-    if args.plain_steps > 0 and (args.mode != "plain" or args.precision != "fp32"):
-        ans_fast, ans_plain = [], []
-        step(answers=ans_fast)
-        step(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32, answers=ans_plain)
-        same = all(bool(torch.equal(a, b)) for a, b in zip(ans_fast, ans_plain))
-        torch.cuda.synchronize()
-        ts = [step(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32) for _ in range(args.plain_steps)]
-        plain = {"value": nq * args.plain_steps / (sum(ts) * 1e-3), "unit": "queries/s",
-                 "ms_per_step": sum(ts) / args.plain_steps, "mode": "plain", "precision": "fp32",
-                 "identical_answers": same}
+    # ---- beside it: the plain method (one query per lower-bound pass, fp32 refinement) with the
+    # descent seed and with the learned seed, and the headline form per sigma group; answers of
+    # every form are compared with the headline's
+    def summarize(rs, label):
+        ms = [r["build_ms"] + r["query_ms"] for r in rs]
+        by = []
+        for i, s_ in enumerate(SIGMAS):
+            tq = sum(st_["ms_prep"] + st_["ms_descent"] + st_["ms_lbscan"] + st_["ms_refine"] + st_["ms_select"] +
+                     st_["ms_dense"] for r in rs for st_ in [r["stats"][i]])
+            c = sum(r["stats"][i]["candidates"] for r in rs) / (len(rs) * args.per_sigma)
+            by.append({"sigma": s_, "queries_per_s": args.per_sigma * len(rs) / (tq * 1e-3),
+                       "candidates_per_query": c, "pruning_ratio": 1.0 - c / n,
+                       "dense_queries": sum(r["stats"][i]["dense_queries"] for r in rs) / len(rs),
+                       "lbscan_ms": sum(r["stats"][i]["ms_lbscan"] for r in rs) / len(rs)})
+        return {"form": label, "value": nq * len(rs) / (sum(ms) * 1e-3), "unit": "queries/s",
+                "ms_per_step": sum(ms) / len(rs), "by_sigma": by}
+
+    beside, plain_recs, per_sigma = {}, [], None
+    if args.plain_steps > 0:
+        ans_ref = []
+        step(answers=ans_ref)
+        forms = [("plain_descent", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32, sd=P.PARIS_SEED_DESCENT))]
+        if model is not None:
+            forms.append(("plain_learned", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32,
+                                                sd=P.PARIS_SEED_LEARNED)))
+            forms.append(("headline_learned", dict(sd=P.PARIS_SEED_LEARNED)))
+        forms.append(("headline_by_sigma", dict()))
+        for name, kw in forms:
+            ans = []
+            step(answers=ans, split=True, **kw)
+            same = bool(torch.equal(torch.cat(ans), ans_ref[0]))
+            rs = []
+            for _ in range(args.plain_steps):
+                step(collect=rs, split=True, **kw)
+            beside[name] = summarize(rs, name)
+            beside[name]["identical_answers"] = same
+            if name == "plain_descent":
+                plain_recs = rs
+            if name == "headline_by_sigma":
+                per_sigma = beside[name]["by_sigma"]
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -300,10 +362,12 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             idx = P.paris_build(host, 16, 256)                      # host series: copied in by the library
+            if seed_mode == P.PARIS_SEED_LEARNED:
+                P.paris_attach_seed_model(idx, model, 3)
             for i in range(len(SIGMAS)):
                 sl = slice(i * args.per_sigma, (i + 1) * args.per_sigma)
                 P.paris_exact_knn_ex(idx, qhost[sl], k, out_idx=out_i[sl], out_dist=out_d[sl], mode=mode,
-                                     precision=precision)
+                                     precision=precision, seed=seed_mode)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             idx.free()
@@ -333,24 +397,19 @@ def main():
             dense_q += s["dense_queries"]
     build_ms = sum(r["build_ms"] for r in recs) / steps
     query_ms = sum(r["query_ms"] for r in recs) / steps
-    # LB-scan roofline from the scans that run to completion: the sigma = 0.01 group (in MIXED
-    # precision the scans of queries sent to the tensor-core path stop early)
-    launches_lb = args.per_sigma * steps
-    lb_ms0 = sum(r["stats"][0]["ms_lbscan"] for r in recs)
-    cands0 = sum(r["stats"][0]["candidates"] for r in recs)
-    lb_bytes = 16.0 * n + 8.0 * cands0 / launches_lb
-    lb_launch_ms = lb_ms0 / launches_lb
-    lb_gbs = lb_bytes / (lb_launch_ms * 1e-3) / 1e9
+    # LB-scan roofline (the paper's scan: one query per pass over the summaries) from complete
+    # single-query scans: the sigma = 0.01 group of the plain-method steps
+    lb_src = plain_recs
+    lb_gbs = lb_launch_ms = lb_bytes = None
+    if lb_src:
+        launches_lb = args.per_sigma * len(lb_src)
+        lb_ms0 = sum(r["stats"][0]["ms_lbscan"] for r in lb_src)
+        cands0 = sum(r["stats"][0]["candidates"] for r in lb_src)
+        lb_bytes = 16.0 * n + 8.0 * cands0 / launches_lb
+        lb_launch_ms = lb_ms0 / launches_lb
+        lb_gbs = lb_bytes / (lb_launch_ms * 1e-3) / 1e9
     refine_bytes_total = refined * (length * 4.0) + cands * 12.0
     refine_gbs = refine_bytes_total / (ph["refine"] * 1e-3) / 1e9 if ph["refine"] > 0 else 0.0
-    per_sigma = []
-    for i, s in enumerate(SIGMAS):
-        tot = sum(r["stats"][i]["ms_prep"] + r["stats"][i]["ms_descent"] + r["stats"][i]["ms_lbscan"] +
-                  r["stats"][i]["ms_refine"] + r["stats"][i]["ms_select"] + r["stats"][i]["ms_dense"] for r in recs)
-        c = sum(r["stats"][i]["candidates"] for r in recs) / (steps * args.per_sigma)
-        dq = sum(r["stats"][i]["dense_queries"] for r in recs) / steps
-        per_sigma.append({"sigma": s, "queries_per_s": args.per_sigma * steps / (tot * 1e-3),
-                          "candidates_per_query": c, "pruning_ratio": 1.0 - c / n, "dense_queries": dq})
     dominant = max(ph, key=ph.get)
     if dominant == "dense":
         # algorithmic work of the BF16 screening: two passes (threshold, emission) of 2*len flops
@@ -363,9 +422,21 @@ def main():
     elif dominant == "refine":
         roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel")}
+    elif args.mode == "batched":
+        # the batched scan is bound by shared-memory table lookups: 8 32-bit lookups (FP16 pairs)
+        # per (row, query); peak = 32 banks x 152 SMs x the median SM clock under load
+        qscan = nq * steps
+        lookups = 8.0 * n * qscan
+        ach = lookups / (ph["lbscan"] * 1e-3) / 1e9
+        clk_mhz = clk.get("sm_mhz") or 2070.0
+        peak_l = 32.0 * 152 * clk_mhz * 1e6 / 1e9
+        roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
+                "unit": "G shared-memory lookups/s", "frac": ach / peak_l, "traffic": traffic_for("lbscan_batched_kernel"),
+                "note": "upper estimate: counts every (row, query) lookup although scans of queries sent to the "
+                        "tensor-core path stop early"}
     else:
         roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": lb_gbs / hbm_peak, "traffic": traffic_for("lbscan_kernel")}
+                "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel")}
     roof["peak_kind"] = peak_kind
     value = nq * steps * world / (total_ms * 1e-3)
     line = {
@@ -378,14 +449,18 @@ def main():
                    "l2": "inputs larger than L2 (20.5 GB series; 320 MB summaries read per query)",
                    "parallelism": f"replicas x{world} (independent collections per GPU)"},
         "roofline": roof,
-        "lb_scan": {"achieved_gbs": lb_gbs, "frac_of_hbm": lb_gbs / hbm_peak, "peak_kind": peak_kind,
-                    "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes,
-                    "launches": "the sigma=0.01 group's complete scans"},
+        "lb_scan": None if lb_gbs is None else {
+            "achieved_gbs": lb_gbs, "frac_of_hbm": lb_gbs / hbm_peak, "peak_kind": peak_kind,
+            "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes,
+            "launches": "complete one-query scans (sigma=0.01 group of the plain-method steps)"},
         "build": {"ms": build_ms, "gb_per_s": n * length * 4 / (build_ms * 1e-3) / 1e9,
                   "series_per_s": n / (build_ms * 1e-3)},
         "query_ms_per_step": query_ms,
         "precision": args.precision,
-        "plain_method": plain,
+        "seed": args.seed,
+        "seed_training": training,
+        "plain_method": beside.get("plain_descent"),
+        "beside": beside,
         "dense_queries_per_step": dense_q / steps,
         "phase_ms_per_step": {kk: v / steps for kk, v in ph.items()},
         "per_sigma": per_sigma,

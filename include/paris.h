@@ -142,6 +142,11 @@ const char* paris_last_error(void);
  * caching allocator). alloc returns NULL on failure. Passing NULL functions restores the
  * default. Not thread-safe with respect to concurrent library calls.
  * ---------------------------------------------------------------------------------------- */
+/* By default the library allocates from its own stream-ordered pool per device, which keeps
+ * freed blocks cached for later calls; paris_trim_memory returns the cached blocks of the
+ * current device to the driver (it synchronises the device first). */
+paris_status paris_trim_memory(void);
+
 typedef void* (*paris_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*paris_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 paris_status paris_set_allocator(paris_alloc_fn alloc, paris_free_fn free_fn, void* ctx);

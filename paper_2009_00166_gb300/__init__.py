@@ -37,5 +37,6 @@ from .binding import (  # noqa: F401
     paris_row_buckets,
     paris_last_error,
     paris_set_allocator,
+    paris_trim_memory,
     use_torch_allocator,
 )

@@ -77,6 +77,7 @@ def lib():
             "paris_last_error": ([], C.c_char_p),
             "paris_kernel_launches": ([], C.c_uint64),
             "paris_set_allocator": ([ALLOC_FN, FREE_FN, VP], I32),
+            "paris_trim_memory": ([], I32),
             "paris_index_describe": ([VP, C.POINTER(IndexView)], I32),
             "paris_breakpoints": ([I32, P], I32),
             "paris_export_sax": ([VP, P, VP], I32),
@@ -106,6 +107,10 @@ def lib():
 
 def paris_kernel_launches() -> int:
     return int(lib().paris_kernel_launches())
+
+
+def paris_trim_memory():
+    _check(lib().paris_trim_memory())
 
 
 def paris_last_error() -> str:

@@ -45,10 +45,41 @@ std::atomic<uint64_t> g_launches{0};
 void note_launches(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+namespace {
+// The library's own stream-ordered pool per device: freed blocks stay cached for the next call
+// (release threshold = unlimited) instead of going back to the driver at every synchronisation.
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t library_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t threshold = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
 void* dev_alloc(size_t bytes, cudaStream_t st) {
   if (g_alloc) return g_alloc(bytes, st, g_ctx);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+  cudaMemPool_t pool = library_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -260,6 +291,18 @@ extern "C" {
 const char* paris_last_error(void) { return g_err.c_str(); }
 
 uint64_t paris_kernel_launches(void) { return launch_count(); }
+
+paris_status paris_trim_memory(void) {
+  clear_error();
+  int dev = 0;
+  PARIS_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool = library_pool();
+  if (pool) {
+    PARIS_CUDA(cudaDeviceSynchronize());
+    PARIS_CUDA(cudaMemPoolTrimTo(pool, 0));
+  }
+  return PARIS_OK;
+}
 
 paris_status paris_set_allocator(paris_alloc_fn alloc, paris_free_fn free_fn, void* ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr))
@@ -513,9 +556,10 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   if (qc <= 0) {
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
-    double budget = std::min((double)freeb * 0.25, 8.0e9);
-    qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0));
-    qc = std::max<int64_t>(1, std::min<int64_t>(qc, 1024));
+    double budget = std::min((double)freeb * 0.3, 24.0e9);
+    qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0 +
+                             (double)idx->card * 32.0));
+    qc = std::max<int64_t>(1, std::min<int64_t>(qc, 4096));
   }
   qc = std::min(qc, nq);
   DevBuf cblock;
@@ -531,7 +575,8 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
            o_F = take((size_t)qc * cap * 4), o_pre = take((size_t)(qc + 1) * 4), o_kth = take((size_t)qc * 4),
            o_hist = take((size_t)qc * 2048 * 4), o_sel = take((size_t)qc * 8), o_cc = take((size_t)qc * 4),
            o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4),
-           o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4);
+           o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4),
+           o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
     char* b = cblock.as<char>();
     cs.cap = cap;
@@ -549,6 +594,7 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     cs.rows2 = (uint32_t*)(b + o_r2);
     cs.lb2 = (float*)(b + o_l2);
     cs.bucket = (uint32_t*)(b + o_bk);
+    cs.packed = (uint32_t*)(b + o_pk);
   }
   int qt = 0;
   if (o.mode == PARIS_MODE_BATCHED && o.query_tile) {

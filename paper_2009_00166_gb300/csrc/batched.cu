@@ -19,7 +19,7 @@ namespace paris {
 namespace {
 
 constexpr int kBThreads = 512;
-constexpr int kBUnroll = 2;
+constexpr int kBUnroll = 4;
 constexpr float kHalfKeep = 1.0f - 1.0f / 64.0f;
 constexpr float kHalfCap = 4000.0f;
 
@@ -49,9 +49,22 @@ __device__ __forceinline__ void append_kept(bool keep, int64_t row, float lb, in
   if ((int64_t)base + __popc(mk) > cap) overflowed = true;
 }
 
+// FP16 pair tables of a chunk, packed once: word (pair p, entry e) = {T[2p][e], T[2p+1][e]}.
+__global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int64_t entries, uint32_t* __restrict__ out) {
+  const int64_t npairs = (qc + 1) / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs * entries;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / entries, e = i - p * entries;
+    const int64_t qa = 2 * p, qb = qa + 1;
+    const float va = qtable[qa * entries + e];
+    const float vb = qb < qc ? qtable[qb * entries + e] : 0.f;
+    out[i] = pack_half2_rd(va, vb);
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
-    const uint4* __restrict__ sax, int64_t n, int card, const float* __restrict__ qtable,
+    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
     const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, uint32_t* __restrict__ count,
     uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap, int stop_on_overflow,
     uint32_t* __restrict__ status) {
@@ -74,17 +87,18 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
   for (int tile = 0; tile < ntiles; ++tile) {
     const int qb = tile * QT;
     __syncthreads();  // the previous tile's tables are no longer read
-    for (int64_t e = threadIdx.x; e < entries * NP; e += blockDim.x) {
+    const int npairs_chunk = (qc + 1) / 2;
+    for (int64_t e4 = threadIdx.x; e4 < entries * NP / 4; e4 += blockDim.x) {  // 4 entries per thread step
+      const int64_t e = 4 * e4;
       const int p = (int)(e / entries);
       const int64_t rem = e - (int64_t)p * entries;
       const int c = (int)(rem >> 4), i = (int)(rem & 15);
-      const int qa = qb + 2 * p, qbb = qa + 1;
-      const float va = qa < qc ? qtable[(int64_t)qa * entries + rem] : 0.f;
-      const float vb = qbb < qc ? qtable[(int64_t)qbb * entries + rem] : 0.f;
-      const uint32_t word = pack_half2_rd(va, vb);
+      const int pg = qb / 2 + p;  // pair index within the chunk
+      const uint4 word = pg < npairs_chunk ? *reinterpret_cast<const uint4*>(packed + (int64_t)pg * entries + rem)
+                                           : make_uint4(0u, 0u, 0u, 0u);
       const int w0 = (p >> 1) * 16384 + c * 64 + (p & 1) * 32 + i;
-      s_tab[w0] = word;
-      s_tab[w0 + 16] = word;
+      *reinterpret_cast<uint4*>(&s_tab[w0]) = word;
+      *reinterpret_cast<uint4*>(&s_tab[w0 + 16]) = word;
     }
     if (threadIdx.x < QT) {
       const int q = qb + threadIdx.x;
@@ -171,10 +185,13 @@ paris_status launch_np(const paris_index* idx, const QueryState& qs, const Chunk
   const int ntiles = (cs.qc + 2 * NP - 1) / (2 * NP);
   const int64_t groups = (idx->n + 31) / 32;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count_b(), (groups + 63) / 64));
-  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(
-      reinterpret_cast<const uint4*>(idx->sax), idx->n, idx->card, qs.qtable + cs.q0 * (int64_t)idx->card * 16,
-      qs.thr, cs.q0, cs.qc, ntiles, cs.count, cs.rows, cs.lb, cs.cap, stop, status);
-  note_launches(1);
+  const int64_t entries = (int64_t)idx->card * 16;
+  pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
+      qs.qtable + cs.q0 * entries, cs.qc, entries, cs.packed);
+  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax), idx->n,
+                                                            idx->card, cs.packed, qs.thr, cs.q0, cs.qc, ntiles,
+                                                            cs.count, cs.rows, cs.lb, cs.cap, stop, status);
+  note_launches(2);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }

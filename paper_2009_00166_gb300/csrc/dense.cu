@@ -34,7 +34,9 @@ constexpr int BM = 128;             // queries per tile (MMA M)
 constexpr int BN = 64;              // series rows per tile (MMA N)
 constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
 constexpr int STAGES = 4;           // shared-memory ring depth for row tiles
-constexpr int DENSE_THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr int DENSE_THREADS = 320;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
+constexpr int EPI_WARPS = 8;        // two per TMEM lane quadrant, one per 32-column half of a tile
+constexpr int SAMPLE = 16;          // pass 1 visits one row tile in SAMPLE
 constexpr int KMAX = 16;            // largest k the screening supports
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr int MAX_KB = 4;           // len <= 256
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(b_accf + 8 * a, 1);
-      mbar_init(b_acce + 8 * a, 4);
+      mbar_init(b_acce + 8 * a, EPI_WARPS);
     }
     mbar_init(b_afull, 1);
     *abort_flag = 0;
@@ -183,6 +185,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   const int64_t ntiles = (P.n + BN - 1) / BN;
+  // pass 1 needs the upper ends of any k rows: it visits every SAMPLE-th tile; pass 2 visits all
+  const int64_t tstep = (PHASE == 1 ? SAMPLE : 1);
+  const int64_t tfirst = (int64_t)blockIdx.x * tstep, tstride = (int64_t)gridDim.x * tstep;
   const uint64_t deadline = globaltimer() + kWaitNs;
   const int nkb = P.nkb;
 
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       for (int kb = 0; kb < nkb; ++kb)
         tma_load_2d(smem_u32(smA + (size_t)kb * BM * 128), &tmA, kb * BKE, P.qtile * BM, b_afull);
       int i = 0;
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)((i / STAGES) & 1);
         if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
       bool ok = mbar_wait(b_afull, 0u, abort_flag, deadline);
       int i = 0;
-      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+      for (int64_t t = tfirst; ok && t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)((i / STAGES) & 1);
         const int ab = i & 1;
@@ -243,8 +248,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       if (i > 0) mbar_wait(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag,
                            deadline + 100000000ull);
     }
-  } else {  // ---- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+  } else {  // ---- epilogue: warps 2..9, TMEM lane quadrant = warp % 4, column half = (warp - 2) / 4
     const int qd = warp & 3;
+    const int c = (warp - 2) >> 2;
     const int m = qd * 32 + lane;
     const int d = P.qtile * BM + m;
     const bool valid = d < P.nd;
@@ -264,23 +270,17 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) best[j] = CUDART_INF_F;
     float kth = CUDART_INF_F;
-    // row norms of a tile: lane l holds rows 32c + l (c = 0, 1), prefetched one tile ahead and
-    // broadcast with shuffles
-    auto load_norms = [&](int64_t t, float2 (&xr)[BN / 32]) {
-#pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        const int64_t row = t * BN + c * 32 + lane;
-        xr[c] = (t < ntiles && row < P.n) ? P.xnorm[row] : make_float2(0.f, 0.f);
-      }
+    // row norms of this warp's half of a tile: lane l holds row 32c + l, prefetched one tile
+    // ahead and broadcast with shuffles
+    auto load_norms = [&](int64_t t) {
+      const int64_t row = t * BN + c * 32 + lane;
+      return (t < ntiles && row < P.n) ? P.xnorm[row] : make_float2(0.f, 0.f);
     };
-    float2 xnext[BN / 32];
-    load_norms(blockIdx.x, xnext);
+    float2 xnext = load_norms(tfirst);
     int i = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-      float2 xcur[BN / 32];
-#pragma unroll
-      for (int c = 0; c < BN / 32; ++c) xcur[c] = xnext[c];
-      load_norms(t + gridDim.x, xnext);
+    for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
+      const float2 xcur = xnext;
+      xnext = load_norms(t + tstride);
       const int ab = i & 1;
       const uint32_t aph = (uint32_t)((i >> 1) & 1);
       if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
@@ -288,8 +288,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
         break;
       }
       tc_fence_after();
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      {
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);
         const int64_t row0 = t * BN + c * 32;
@@ -300,8 +299,8 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
         uint32_t hit = 0u;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
-          const float xn = __shfl_sync(PARIS_FULL_MASK, xcur[c].x, jj);
-          const float xrt = __shfl_sync(PARIS_FULL_MASK, xcur[c].y, jj);
+          const float xn = __shfl_sync(PARIS_FULL_MASK, xcur.x, jj);
+          const float xrt = __shfl_sync(PARIS_FULL_MASK, xcur.y, jj);
           const float d2 = fmaf(-2.0f, __uint_as_float(v[jj]), qn + xn);
           const float M = __fmaf_ru(c1q, xrt, __fmul_ru(P.c2, __fadd_ru(qn, xn)));
           if (PHASE == 1) {

@@ -39,6 +39,7 @@ struct ChunkState {
   uint32_t* rows2 = nullptr;       // [qc][cap] candidates reordered by lower-bound bucket
   float* lb2 = nullptr;            // [qc][cap]
   uint32_t* bucket = nullptr;      // [qc][32] bucket counts, then cursors
+  uint32_t* packed = nullptr;      // [(qc+1)/2][card][16] FP16 pair tables of the batched scan
   uint32_t* prefix = nullptr;      // [qc + 1]
   uint32_t* kth = nullptr;         // [qc] fp32 bits of the k-th smallest F
   uint32_t* sel_hist = nullptr;    // [qc][2048]
