@@ -18,7 +18,7 @@ namespace paris {
 
 namespace {
 
-constexpr int kBThreads = 512;
+constexpr int kBThreads = 768;
 constexpr int kBUnroll = 4;
 constexpr float kHalfKeep = 1.0f - 1.0f / 64.0f;
 constexpr float kHalfCap = 4000.0f;
@@ -105,9 +105,17 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
       s_thr[threadIdx.x] = q < qc ? __uint_as_float(thr[q0 + q]) : -1.0f;  // -1: nothing kept
     }
     __syncthreads();
-    float th[QT];
+    // FP16 thresholds per pair: keep iff sum <= thr / (1 - 2^-6), the bound rounded up so the
+    // kept set is a superset of the FP32 test's
+    __half2 thh[NP];
 #pragma unroll
-    for (int q = 0; q < QT; ++q) th[q] = s_thr[q];
+    for (int p = 0; p < NP; ++p) {
+      const float ta = s_thr[2 * p], tb = s_thr[2 * p + 1];
+      thh[p] = __halves2half2(ta < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(ta / kHalfKeep, 65504.f)),
+                              tb < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(tb / kHalfKeep, 65504.f)));
+      if (ta >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__float2half(65504.f), __high2half(thh[p]));
+      if (tb >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__low2half(thh[p]), __float2half(65504.f));
+    }
     bool ovf[QT];
 #pragma unroll
     for (int q = 0; q < QT; ++q) ovf[q] = false;
@@ -129,6 +137,8 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
           const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
           addr[kk] = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
         }
+        __half2 sum[NP];
+        uint32_t keepmask = 0u;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           const uint32_t off = (uint32_t)((p >> 1) * 65536 + (p & 1) * 128);
@@ -141,19 +151,30 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
             acc0 = __hadd2(acc0, *reinterpret_cast<__half2*>(&v0));
             acc1 = __hadd2(acc1, *reinterpret_cast<__half2*>(&v1));
           }
-          const __half2 acc = __hadd2(acc0, acc1);
-          const float la = __low2float(acc) * kHalfKeep, lbq = __high2float(acc) * kHalfKeep;
-          const int qa = qb + 2 * p;
-          append_kept(rv && la <= th[2 * p], row, la, lane, count + qa, out_rows + (int64_t)qa * cap,
-                      out_lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
-          append_kept(rv && lbq <= th[2 * p + 1], row, lbq, lane, count + qa + 1, out_rows + (int64_t)(qa + 1) * cap,
-                      out_lb + (int64_t)(qa + 1) * cap, cap, ovf[2 * p + 1], status);
+          sum[p] = __hadd2(acc0, acc1);
+          const uint32_t m = __hle2_mask(sum[p], thh[p]);
+          keepmask |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
+        }
+        keepmask = rv ? keepmask : 0u;
+        const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
+        if (any) {  // rare: some lane keeps this row for some query of the tile
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            if (!((any >> (2 * p)) & 3u)) continue;
+            const int qa = qb + 2 * p;
+            const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
+            append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa, out_rows + (int64_t)qa * cap,
+                        out_lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
+            append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qa + 1,
+                        out_rows + (int64_t)(qa + 1) * cap, out_lb + (int64_t)(qa + 1) * cap, cap, ovf[2 * p + 1],
+                        status);
+          }
         }
       }
       if (stop_on_overflow) {
         bool all = true;
 #pragma unroll
-        for (int q = 0; q < QT; ++q) all = all && (ovf[q] || th[q] < 0.f);
+        for (int q = 0; q < QT; ++q) all = all && (ovf[q] || s_thr[q] < 0.f);
         if (all) break;
       }
     }

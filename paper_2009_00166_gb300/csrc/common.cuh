@@ -185,9 +185,28 @@ __device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
   return (int64_t)__shfl_sync(PARIS_FULL_MASK, (long long)v, src);
 }
 
-// Number of breakpoints <= v (upper region on ties): binary search over order keys.
+// Number of breakpoints <= v (upper region on ties). An FP32 estimate floor(card * Phi(v)) is
+// moved to the exact answer by comparing order keys of the FP64 values (a few steps at most);
+// the binary search below is the fallback.
+__device__ __forceinline__ int symbol_search(uint64_t key, const uint64_t* beta_keys, int card);
 __device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, int card) {
-  uint64_t key = double_order_key(v);
+  const uint64_t key = double_order_key(v);
+  int sym = (int)(normcdff(__double2float_rn(v)) * (float)card);
+  sym = sym < 0 ? 0 : (sym > card - 1 ? card - 1 : sym);
+  // answer: beta_keys[sym-1] <= key < beta_keys[sym] (missing ends are -inf / +inf)
+  for (int it = 0; it < 8; ++it) {
+    if (sym > 0 && beta_keys[sym - 1] > key) {
+      --sym;
+    } else if (sym < card - 1 && beta_keys[sym] <= key) {
+      ++sym;
+    } else {
+      return sym;
+    }
+  }
+  return symbol_search(key, beta_keys, card);
+}
+
+__device__ __forceinline__ int symbol_search(uint64_t key, const uint64_t* beta_keys, int card) {
   int lo = 0, cnt = card - 1;  // upper_bound over beta_keys[0, card-1)
   while (cnt > 0) {
     int half = cnt >> 1;
@@ -227,42 +246,45 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
     const float4* p = reinterpret_cast<const float4*>(row + (active ? (int64_t)seg * s : 0));
     constexpr bool kCache = SEGV <= 4;
     float4 cache[kCache ? SEGV : 1];
-    uint32_t emax = 1u, emin = 255u, anysub = 0u;
+    // pass 1: the largest magnitude as bits (NaN and infinity sort above every finite value)
+    uint32_t mb = 0u;
 #pragma unroll
     for (int v = 0; v < SEGV; ++v) {
       float4 x = active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (kCache) cache[kCache ? v : 0] = x;
-      const uint32_t u[4] = {__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), __float_as_uint(x.w)};
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t be = (u[c] >> 23) & 0xffu;
-        const bool nz = (u[c] & 0x7fffffffu) != 0u;
-        emax = max(emax, be);
-        emin = nz ? min(emin, be) : emin;
-        anysub |= (uint32_t)(nz && be == 0u);
-      }
+      mb = max(mb, max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu),
+                       max(__float_as_uint(x.z) & 0x7fffffffu, __float_as_uint(x.w) & 0x7fffffffu)));
     }
-    if (emax == 255u) {
+    if (mb >= 0x7f800000u) {
       finite = false;
       done = true;
-    } else {
-      const int lambda = (int)emax - 126 + sh.log2s - 63;
-      // every nonzero value has its least significant bit at 2^(be-150) >= 2^lambda
-      if (!anysub && (emin == 255u || (int)emin - 150 >= lambda)) {
-        int64_t S = 0;
+    } else if (mb == 0u) {
+      paa_out = 0.0;
+      done = true;
+    } else if ((mb >> 23) != 0u) {
+      // values are integer multiples of 2^lambda when no nonzero magnitude is below 2^(lambda+23);
+      // the sum of s values below 2^(emax-126) then stays below 2^63 * 2^lambda
+      const int emax = (int)(mb >> 23);
+      const int lambda = emax - 126 + sh.log2s - 63;
+      const int te = lambda + 23 + 127;                      // biased exponent of 2^(lambda+23)
+      const uint32_t tbits = te >= 1 ? (uint32_t)te << 23 : 0u;  // 0: every fp32 value qualifies
+      const int na = -lambda;                                // scale by 2^na = 2^a * 2^b
+      const int a = na >> 1, b2 = na - a;
+      const float sa = __int_as_float((a + 127) << 23), sb = __int_as_float((b2 + 127) << 23);
+      bool tiny = false;
+      int64_t S = 0;
 #pragma unroll
-        for (int v = 0; v < SEGV; ++v) {
-          float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
-          const uint32_t u[4] = {__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), __float_as_uint(x.w)};
+      for (int v = 0; v < SEGV; ++v) {
+        float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
+        const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint32_t be = (u[c] >> 23) & 0xffu;
-            const uint64_t mant = (uint64_t)((u[c] & 0x7fffffu) | 0x800000u);
-            const int sh_ = max((int)be - 150 - lambda, 0);
-            const int64_t mag = (u[c] & 0x7fffffffu) ? (int64_t)(mant << sh_) : 0;
-            S += (u[c] >> 31) ? -mag : mag;
-          }
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t ub = __float_as_uint(xs[c]) & 0x7fffffffu;
+          tiny |= (ub - 1u) < (tbits - 1u) && tbits != 0u;  // nonzero and below 2^(lambda+23)
+          S += __float2ll_rz((xs[c] * sa) * sb);             // exact: an integer below 2^62
         }
+      }
+      if (!tiny) {
         paa_out = fixed_to_double(S, lambda - sh.log2s);  // s is a power of two on this path
         done = true;
       }
