@@ -305,10 +305,8 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     launches = P.paris_kernel_launches() - launches0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2009_00166_gb300 import shards
+    job_rate, total_ms = shards.job_throughput(total_ms, float(nq * args.steps))
 
     # ---- beside it: the plain method (one query per lower-bound pass, fp32 refinement) with the
     # descent seed and with the learned seed, and the headline form per sigma group; answers of
@@ -438,7 +436,7 @@ def main():
         roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel")}
     roof["peak_kind"] = peak_kind
-    value = nq * steps * world / (total_ms * 1e-3)
+    value = job_rate
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
