@@ -122,7 +122,9 @@ typedef struct paris_query_stats {
   double ms_prep, ms_descent, ms_lbscan, ms_refine, ms_select; /* device time per phase */
   double ms_dense;     /* device time of the BF16 screening (MIXED) */
   int32_t query_tile;  /* queries per summary pass used by BATCHED mode (0 in PLAIN) */
-  int32_t reserved_stats;
+  int32_t rescreens;   /* MIXED: repeated BF16 screenings of queries whose screened candidate list
+                          overflowed (each repeat first lowers the query's threshold to the k-th
+                          best candidate found; the call fails with EINTERNAL after 4 repeats) */
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */

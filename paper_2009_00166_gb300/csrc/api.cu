@@ -248,8 +248,24 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
       return PARIS_OK;
     }
   }
-  ChunkState sub = cs;
-  sub.qc = (int)std::min<int64_t>(cs.qc, 24);
+  // Trial launches on up to three spread samples of 12 queries (start, middle and end of the
+  // chunk), so the choice sees the chunk's mix of tight and loose thresholds.
+  int offs[3] = {0, 0, 0}, nsub = 1, m = (int)std::min<int64_t>(cs.qc, 24);
+  if (cs.qc >= 36) {
+    m = 12;
+    nsub = 3;
+    offs[1] = cs.qc / 2 - 6;
+    offs[2] = cs.qc - 12;
+  }
+  auto sub_of = [&](int j) {
+    ChunkState sub = cs;
+    sub.q0 = cs.q0 + offs[j];
+    sub.qc = m;
+    sub.count = cs.count + offs[j];
+    sub.rows = cs.rows + (int64_t)offs[j] * cs.cap;
+    sub.lb = cs.lb + (int64_t)offs[j] * cs.cap;
+    return sub;
+  };
   DevBuf scratch_status;
   if (!scratch_status.alloc(4, st)) return fail(PARIS_ENOMEM, "tuning scratch");
   cudaEvent_t e0, e1;
@@ -260,16 +276,20 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
   for (int i = 0; i < kNumQueryTiles; ++i) {
     const int qt = kQueryTiles[i];
     if (!query_tile_fits(qt, idx->card)) continue;
-    PARIS_CUDA(cudaMemsetAsync(sub.count, 0, (size_t)sub.qc * 4, st));
-    cudaEventRecord(e0, st);
-    paris_status s = launch_lbscan_batched(idx, qs, sub, qt, 1, scratch_status.as<uint32_t>(), st);
-    cudaEventRecord(e1, st);
-    if (s != PARIS_OK) return s;
-    PARIS_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const int covered = (sub.qc + qt - 1) / qt * qt;  // queries the launch had room for
-    const float per_query = ms / (float)std::max(sub.qc, std::min(covered, sub.qc));
+    float total = 0.f;
+    for (int j = 0; j < nsub; ++j) {
+      const ChunkState sub = sub_of(j);
+      PARIS_CUDA(cudaMemsetAsync(sub.count, 0, (size_t)sub.qc * 4, st));
+      cudaEventRecord(e0, st);
+      paris_status s = launch_lbscan_batched(idx, qs, sub, qt, 1, scratch_status.as<uint32_t>(), st);
+      cudaEventRecord(e1, st);
+      if (s != PARIS_OK) return s;
+      PARIS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      total += ms;
+    }
+    const float per_query = total / (float)(m * nsub);
     if (per_query < best_t) {
       best_t = per_query;
       best = qt;
@@ -277,7 +297,7 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  PARIS_CUDA(cudaMemsetAsync(sub.count, 0, (size_t)sub.qc * 4, st));
+  for (int j = 0; j < nsub; ++j) PARIS_CUDA(cudaMemsetAsync(cs.count + offs[j], 0, (size_t)m * 4, st));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tuned[key] = best;
   *out = best;
@@ -552,6 +572,7 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   if (!lbstatus.alloc(4, st)) return fail(PARIS_ENOMEM, "status word");
   uint32_t* lb_status = mixed ? lbstatus.as<uint32_t>() : qs.status;  // overflow is the signal in MIXED
   int64_t dense_total = 0;
+  int rescreens = 0;
   int64_t qc = o.chunk;
   if (qc <= 0) {
     size_t freeb = 0, totalb = 0;
@@ -621,7 +642,7 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     if (mixed) {
       int nd = 0;
       timer.begin(5);
-      PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, &nd, st));
+      PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, lb_status, &nd, st));
       timer.end(5);
       dense_total += nd;
     }
@@ -631,6 +652,25 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     timer.begin(4);
     PARIS_TRY(launch_select(idx, qs, cs, (int64_t*)si.dev, (float*)sd.dev, st));
     timer.end(4);
+    // a screened list that overflowed: lower the query's threshold to the k-th best candidate it
+    // stored and screen it again (rare; the other queries' lists are unchanged by the repeat)
+    for (int retry = 0; mixed; ++retry) {
+      int nover = 0;
+      PARIS_TRY(tighten_overflowed(qs, cs, &nover, st));
+      if (nover == 0) break;
+      if (retry == kDenseRetries) return fail(PARIS_EINTERNAL, "paris_exact_knn: candidate list overflow");
+      rescreens += nover;
+      int nd = 0;
+      timer.begin(5);
+      PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, lb_status, &nd, st));
+      timer.end(5);
+      timer.begin(3);
+      PARIS_TRY(launch_refine(idx, qs, cs, st));
+      timer.end(3);
+      timer.begin(4);
+      PARIS_TRY(launch_select(idx, qs, cs, (int64_t*)si.dev, (float*)sd.dev, st));
+      timer.end(4);
+    }
   }
   PARIS_TRY(si.finish(st));
   PARIS_TRY(sd.finish(st));
@@ -640,6 +680,7 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     timer.collect(ms);
     stats->ms_dense = ms[5];
     stats->query_tile = qt;
+    stats->rescreens = rescreens;
     stats->dense_queries = dense_total;
     stats->ms_prep = ms[0];
     stats->ms_descent = ms[1];

@@ -8,9 +8,20 @@
 // Entries are rounded down to FP16 (and capped at 4000) so each stays below the exact
 // contribution; the 16-term FP16 sum has relative error below 16 * 2^-11, so a row is kept when
 // (sum * (1 - 2^-6)) <= threshold, and that scaled value is what is stored as its lower bound.
+//
+// Work order: each CTA owns a contiguous row range and every query tile passes over it (the
+// range may be cut into blocks that all tiles visit in turn). Within a tile a warp checks its
+// 32 rows after 4 and after 8 of the 16 slots and drops them as soon as no (row, query) partial
+// sum is within its threshold; partial sums of non-negative terms never decrease, so the kept
+// set and the stored bounds are unchanged.
+//
+// A pilot pass over every 64th row group first counts each query's kept rows; a query whose
+// scaled count reaches 3/4 of its list capacity would overflow anyway and is handed to the
+// tensor-core screening before the scan (only when overflow is allowed, i.e. MIXED refinement).
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "query.cuh"
 
@@ -22,6 +33,8 @@ constexpr int kBThreads = 768;
 constexpr int kBUnroll = 4;
 constexpr float kHalfKeep = 1.0f - 1.0f / 64.0f;
 constexpr float kHalfCap = 4000.0f;
+constexpr int64_t kPilotStride = 64;  // the pilot pass reads every 64th group of 32 rows
+constexpr double kPilotRoute = 0.75;  // routed when the scaled pilot count reaches 0.75 * capacity
 
 __device__ __forceinline__ uint32_t pack_half2_rd(float a, float b) {
   __half ha = __float2half_rd(fminf(a, kHalfCap)), hb = __float2half_rd(fminf(b, kHalfCap));
@@ -62,129 +75,273 @@ __global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int6
   }
 }
 
+// Copies the FP16 pair tables of query tile `qb` into shared memory (two copies per symbol row,
+// one per half-warp) and returns the tile's FP32 thresholds in s_thr (-1: nothing kept).
 template <int NP>
-__global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
-    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
-    const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, uint32_t* __restrict__ count,
-    uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap, int stop_on_overflow,
-    uint32_t* __restrict__ status) {
+__device__ __forceinline__ void load_tile(const uint32_t* __restrict__ packed, int64_t entries, int qb, int qc,
+                                          const uint32_t* __restrict__ thr, int64_t q0, const bool* active,
+                                          uint32_t* s_tab, float* s_thr) {
   constexpr int QT = 2 * NP;
-  extern __shared__ __align__(16) uint32_t s_tab[];  // region r (64 KB): pairs 2r, 2r+1
-  __shared__ float s_thr[QT];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t offp[8];
+  const int npairs_chunk = (qc + 1) / 2;
+  for (int64_t e4 = threadIdx.x; e4 < entries * NP / 4; e4 += blockDim.x) {  // 4 entries per thread step
+    const int64_t e = 4 * e4;
+    const int p = (int)(e / entries);
+    const int64_t rem = e - (int64_t)p * entries;
+    const int c = (int)(rem >> 4), i = (int)(rem & 15);
+    const int pg = qb / 2 + p;  // pair index within the chunk
+    const uint4 word = pg < npairs_chunk ? *reinterpret_cast<const uint4*>(packed + (int64_t)pg * entries + rem)
+                                         : make_uint4(0u, 0u, 0u, 0u);
+    const int w0 = (p >> 1) * 16384 + c * 64 + (p & 1) * 32 + i;
+    *reinterpret_cast<uint4*>(&s_tab[w0]) = word;
+    *reinterpret_cast<uint4*>(&s_tab[w0 + 16]) = word;
+  }
+  if (threadIdx.x < QT) {
+    const int q = qb + threadIdx.x;
+    s_thr[threadIdx.x] = (q < qc && active[threadIdx.x]) ? __uint_as_float(thr[q0 + q]) : -1.0f;
+  }
+}
+
+// FP16 thresholds per pair: keep iff sum <= thr / (1 - 2^-6), the bound rounded up so the kept
+// set is a superset of the FP32 test's.
+template <int NP>
+__device__ __forceinline__ void tile_thresholds(const float* s_thr, __half2 (&thh)[NP]) {
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const float ta = s_thr[2 * p], tb = s_thr[2 * p + 1];
+    thh[p] = __halves2half2(ta < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(ta / kHalfKeep, 65504.f)),
+                            tb < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(tb / kHalfKeep, 65504.f)));
+    if (ta >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__float2half(65504.f), __high2half(thh[p]));
+    if (tb >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__low2half(thh[p]), __float2half(65504.f));
+  }
+}
+
+// Adds the FP16 pair entries of slots [K0, K1) of one row to the two summation chains of every
+// pair (even slots to a0, odd slots to a1).
+template <int NP, int K0, int K1>
+__device__ __forceinline__ void add_slots(const uint32_t (&wv)[4], const uint32_t (&offp)[8], uint32_t tab,
+                                          __half2 (&a0)[NP], __half2 (&a1)[NP]) {
+#pragma unroll
+  for (int kk = K0; kk < K1; kk += 2) {
+    const uint32_t sel0 = (4u + 0u) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
+    const uint32_t sel1 = (4u + 2u) | ((uint32_t)((kk + 1) & 3) << 4) | (5u << 8) | (5u << 12);
+    const uint32_t ad0 = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel0);
+    const uint32_t ad1 = tab + __byte_perm(wv[(kk + 1) >> 2], offp[kk >> 1], sel1);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const uint32_t off = (uint32_t)((p >> 1) * 65536 + (p & 1) * 128);
+      uint32_t v0, v1;
+      asm("ld.shared.b32 %0, [%1];" : "=r"(v0) : "r"(ad0 + off));
+      asm("ld.shared.b32 %0, [%1];" : "=r"(v1) : "r"(ad1 + off));
+      a0[p] = __hadd2(a0[p], *reinterpret_cast<__half2*>(&v0));
+      a1[p] = __hadd2(a1[p], *reinterpret_cast<__half2*>(&v1));
+    }
+  }
+}
+
+// True when some lane's row may still be kept for some query of the tile. The partial sums only
+// grow with further non-negative terms (round-to-nearest addition is monotone), so a partial sum
+// above a threshold already decides the full sum's test.
+template <int NP>
+__device__ __forceinline__ bool warp_alive(bool rv, const __half2 (&a0)[NP], const __half2 (&a1)[NP],
+                                           const __half2 (&thh)[NP]) {
+  uint32_t m = 0u;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) m |= __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
+  return __any_sync(PARIS_FULL_MASK, rv && m != 0u);
+}
+
+// Keep bits of one row: bit 2p (query 2p of the tile) and 2p + 1, sums left in `sum`. The warp
+// gives up on its 32 rows after 4 and after 8 of the 16 slots once no (row, query) partial sum
+// is within its threshold (returns 0 for every lane then).
+template <int NP>
+__device__ __forceinline__ uint32_t row_keep_bits(const uint4& word, bool rv, const uint32_t (&offp)[8], uint32_t tab,
+                                                  const __half2 (&thh)[NP], __half2 (&sum)[NP]) {
+  const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
+  __half2 a0[NP], a1[NP];  // two chains per pair: shorter latency
+#pragma unroll
+  for (int p = 0; p < NP; ++p) a0[p] = a1[p] = __floats2half2_rn(0.f, 0.f);
+  add_slots<NP, 0, 4>(wv, offp, tab, a0, a1);
+  if (!warp_alive<NP>(rv, a0, a1, thh)) return 0u;
+  add_slots<NP, 4, 8>(wv, offp, tab, a0, a1);
+  if (!warp_alive<NP>(rv, a0, a1, thh)) return 0u;
+  add_slots<NP, 8, 16>(wv, offp, tab, a0, a1);
+  uint32_t keepmask = 0u;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    sum[p] = __hadd2(a0[p], a1[p]);
+    const uint32_t m = __hle2_mask(sum[p], thh[p]);
+    keepmask |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
+  }
+  return rv ? keepmask : 0u;
+}
+
+__device__ __forceinline__ void lane_offsets(int lane, uint32_t (&offp)[8]) {
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     uint32_t o0 = 4u * (16u * (lane >> 4) + ((2 * m + lane) & 15));
     uint32_t o1 = 4u * (16u * (lane >> 4) + ((2 * m + 1 + lane) & 15));
     offp[m] = o0 | (o1 << 16);
   }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
+    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
+    const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, uint32_t* __restrict__ count,
+    uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap, int stop_on_overflow,
+    int64_t block_groups, uint32_t* __restrict__ status) {
+  constexpr int QT = 2 * NP;
+  extern __shared__ __align__(16) uint32_t s_tab[];  // region r (64 KB): pairs 2r, 2r+1
+  __shared__ float s_thr[QT];
+  __shared__ bool s_active[QT];
+  __shared__ int s_skip;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t offp[8];
+  lane_offsets(lane, offp);
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
   const int64_t groups = (n + 31) >> 5;
   const int64_t per = (groups + gridDim.x - 1) / gridDim.x;
   const int64_t g0 = (int64_t)blockIdx.x * per, g1 = min(groups, g0 + per);
   const int64_t entries = (int64_t)card * 16;
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int qb = tile * QT;
-    __syncthreads();  // the previous tile's tables are no longer read
-    const int npairs_chunk = (qc + 1) / 2;
-    for (int64_t e4 = threadIdx.x; e4 < entries * NP / 4; e4 += blockDim.x) {  // 4 entries per thread step
-      const int64_t e = 4 * e4;
-      const int p = (int)(e / entries);
-      const int64_t rem = e - (int64_t)p * entries;
-      const int c = (int)(rem >> 4), i = (int)(rem & 15);
-      const int pg = qb / 2 + p;  // pair index within the chunk
-      const uint4 word = pg < npairs_chunk ? *reinterpret_cast<const uint4*>(packed + (int64_t)pg * entries + rem)
-                                           : make_uint4(0u, 0u, 0u, 0u);
-      const int w0 = (p >> 1) * 16384 + c * 64 + (p & 1) * 32 + i;
-      *reinterpret_cast<uint4*>(&s_tab[w0]) = word;
-      *reinterpret_cast<uint4*>(&s_tab[w0 + 16]) = word;
-    }
-    if (threadIdx.x < QT) {
-      const int q = qb + threadIdx.x;
-      s_thr[threadIdx.x] = q < qc ? __uint_as_float(thr[q0 + q]) : -1.0f;  // -1: nothing kept
-    }
-    __syncthreads();
-    // FP16 thresholds per pair: keep iff sum <= thr / (1 - 2^-6), the bound rounded up so the
-    // kept set is a superset of the FP32 test's
-    __half2 thh[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float ta = s_thr[2 * p], tb = s_thr[2 * p + 1];
-      thh[p] = __halves2half2(ta < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(ta / kHalfKeep, 65504.f)),
-                              tb < 0.f ? __float2half(-65504.f) : __float2half_ru(fminf(tb / kHalfKeep, 65504.f)));
-      if (ta >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__float2half(65504.f), __high2half(thh[p]));
-      if (tb >= 65504.f * kHalfKeep) thh[p] = __halves2half2(__low2half(thh[p]), __float2half(65504.f));
-    }
-    bool ovf[QT];
-#pragma unroll
-    for (int q = 0; q < QT; ++q) ovf[q] = false;
-    for (int64_t it = g0 + (int64_t)wib * kBUnroll; it < g1; it += (int64_t)nw * kBUnroll) {
-      uint4 word[kBUnroll];
-#pragma unroll
-      for (int u = 0; u < kBUnroll; ++u) {
-        const int64_t row = (it + u) * 32 + lane;
-        word[u] = (it + u < g1 && row < n) ? __ldcs(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+  // The CTA's row range may be cut into blocks that every query tile passes over in turn.
+  for (int64_t b0 = g0; b0 < g1; b0 += block_groups) {
+    const int64_t b1 = min(g1, b0 + block_groups);
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const int qb = tile * QT;
+      __syncthreads();  // the previous tile's tables and flags are no longer read
+      if (threadIdx.x == 0) {
+        int skip = 1;
+        for (int q = 0; q < QT; ++q) {
+          const int qq = qb + q;
+          // a list whose count passed its capacity has flagged its overflow (or was handed to the
+          // tensor-core screening beforehand): the query takes no further part in the scan
+          const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qq) > cap);
+          s_active[q] = act;
+          if (act) skip = 0;
+        }
+        s_skip = skip;
       }
+      __syncthreads();
+      if (s_skip) continue;
+      load_tile<NP>(packed, entries, qb, qc, thr, q0, s_active, s_tab, s_thr);
+      __syncthreads();
+      __half2 thh[NP];
+      tile_thresholds<NP>(s_thr, thh);
+      bool ovf[QT];
 #pragma unroll
-      for (int u = 0; u < kBUnroll; ++u) {
-        const int64_t row = (it + u) * 32 + lane;
-        const bool rv = it + u < g1 && row < n;
-        const uint32_t wv[4] = {word[u].x, word[u].y, word[u].z, word[u].w};
-        uint32_t addr[16];
+      for (int q = 0; q < QT; ++q) ovf[q] = false;
+      for (int64_t it = b0 + (int64_t)wib * kBUnroll; it < b1; it += (int64_t)nw * kBUnroll) {
+        uint4 word[kBUnroll];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-          const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
-          addr[kk] = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
+        for (int u = 0; u < kBUnroll; ++u) {
+          const int64_t row = (it + u) * 32 + lane;
+          word[u] = (it + u < b1 && row < n) ? __ldcg(sax + row) : make_uint4(0u, 0u, 0u, 0u);
         }
-        __half2 sum[NP];
-        uint32_t keepmask = 0u;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          const uint32_t off = (uint32_t)((p >> 1) * 65536 + (p & 1) * 128);
-          __half2 acc0 = __floats2half2_rn(0.f, 0.f), acc1 = acc0;  // two chains: shorter latency
+        for (int u = 0; u < kBUnroll; ++u) {
+          const int64_t row = (it + u) * 32 + lane;
+          const bool rv = it + u < b1 && row < n;
+          __half2 sum[NP];
+          const uint32_t keepmask = row_keep_bits<NP>(word[u], rv, offp, tab, thh, sum);
+          const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
+          if (any) {  // rare: some lane keeps this row for some query of the tile
 #pragma unroll
-          for (int kk = 0; kk < 16; kk += 2) {
-            uint32_t v0, v1;
-            asm("ld.shared.b32 %0, [%1];" : "=r"(v0) : "r"(addr[kk] + off));
-            asm("ld.shared.b32 %0, [%1];" : "=r"(v1) : "r"(addr[kk + 1] + off));
-            acc0 = __hadd2(acc0, *reinterpret_cast<__half2*>(&v0));
-            acc1 = __hadd2(acc1, *reinterpret_cast<__half2*>(&v1));
-          }
-          sum[p] = __hadd2(acc0, acc1);
-          const uint32_t m = __hle2_mask(sum[p], thh[p]);
-          keepmask |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
-        }
-        keepmask = rv ? keepmask : 0u;
-        const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
-        if (any) {  // rare: some lane keeps this row for some query of the tile
-#pragma unroll
-          for (int p = 0; p < NP; ++p) {
-            if (!((any >> (2 * p)) & 3u)) continue;
-            const int qa = qb + 2 * p;
-            const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
-            append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa, out_rows + (int64_t)qa * cap,
-                        out_lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
-            append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qa + 1,
-                        out_rows + (int64_t)(qa + 1) * cap, out_lb + (int64_t)(qa + 1) * cap, cap, ovf[2 * p + 1],
-                        status);
+            for (int p = 0; p < NP; ++p) {
+              if (!((any >> (2 * p)) & 3u)) continue;
+              const int qa = qb + 2 * p;
+              const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
+              append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa,
+                          out_rows + (int64_t)qa * cap, out_lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
+              append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qa + 1,
+                          out_rows + (int64_t)(qa + 1) * cap, out_lb + (int64_t)(qa + 1) * cap, cap,
+                          ovf[2 * p + 1], status);
+            }
           }
         }
-      }
-      if (stop_on_overflow) {
-        bool all = true;
+        if (stop_on_overflow) {
+          bool all = true;
 #pragma unroll
-        for (int q = 0; q < QT; ++q) all = all && (ovf[q] || s_thr[q] < 0.f);
-        if (all) break;
+          for (int q = 0; q < QT; ++q) all = all && (ovf[q] || s_thr[q] < 0.f);
+          if (all) break;
+        }
       }
     }
   }
+}
+
+// Pilot pass: counts, per query, the kept rows among every `stride`-th group of 32 rows (same
+// test as the scan). Queries whose scaled count says the list would overflow go straight to the
+// tensor-core screening instead of appending rows that would be discarded.
+template <int NP>
+__global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(
+    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
+    const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, int64_t stride, uint32_t* __restrict__ pilot) {
+  constexpr int QT = 2 * NP;
+  extern __shared__ __align__(16) uint32_t s_tab[];
+  __shared__ float s_thr[QT];
+  __shared__ bool s_active[QT];
+  __shared__ uint32_t s_cnt[QT];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t offp[8];
+  lane_offsets(lane, offp);
+  const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
+  const int64_t samples = (((n + 31) >> 5) + stride - 1) / stride;
+  const int64_t per = (samples + gridDim.x - 1) / gridDim.x;
+  const int64_t s0 = (int64_t)blockIdx.x * per, s1 = min(samples, s0 + per);
+  const int64_t entries = (int64_t)card * 16;
+  if (threadIdx.x < QT) s_active[threadIdx.x] = true;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int qb = tile * QT;
+    __syncthreads();
+    load_tile<NP>(packed, entries, qb, qc, thr, q0, s_active, s_tab, s_thr);
+    if (threadIdx.x < QT) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    __half2 thh[NP];
+    tile_thresholds<NP>(s_thr, thh);
+    uint32_t cnt[QT];
+#pragma unroll
+    for (int q = 0; q < QT; ++q) cnt[q] = 0u;
+    for (int64_t it = s0 + wib; it < s1; it += nw) {
+      const int64_t row = it * stride * 32 + lane;
+      const bool rv = row < n;
+      const uint4 word = rv ? __ldcg(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+      __half2 sum[NP];
+      const uint32_t keepmask = row_keep_bits<NP>(word, rv, offp, tab, thh, sum);
+#pragma unroll
+      for (int q = 0; q < QT; ++q) cnt[q] += __popc(__ballot_sync(PARIS_FULL_MASK, (keepmask >> q) & 1u));
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < QT; ++q)
+        if (cnt[q]) atomicAdd(&s_cnt[q], cnt[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < QT && qb + (int)threadIdx.x < qc && s_cnt[threadIdx.x])
+      atomicAdd(pilot + qb + threadIdx.x, s_cnt[threadIdx.x]);
+  }
+}
+
+// Marks the queries whose scaled pilot count reaches `limit` as overflowed (count = cap + 1).
+__global__ void pilot_route_kernel(const uint32_t* __restrict__ pilot, int qc, int64_t stride, double limit,
+                                   int64_t cap, uint32_t* __restrict__ count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < qc && (double)pilot[q] * (double)stride >= limit) count[q] = (uint32_t)(cap + 1);
 }
 
 size_t batched_smem(int np, int card) {
   const int regions = (np + 1) / 2;
   // region r spans 64 KB of 256-byte symbol rows; the last region only needs card rows
   return (size_t)(regions - 1) * 65536 + (size_t)card * 256;
+}
+
+// Row groups (32 rows) per CTA row block. By default a CTA's whole row range is one block: every
+// query tile streams the summaries from HBM (measured faster at 20M rows than L2-sized blocks,
+// whose tile tables must be reloaded per block). PARIS_BATCHED_BLOCK_ROWS sets rows per block.
+int64_t block_groups() {
+  int64_t rows = 0;
+  if (const char* env = std::getenv("PARIS_BATCHED_BLOCK_ROWS")) rows = std::atoll(env);
+  if (rows <= 0) return INT64_MAX / 64;
+  return std::max<int64_t>(1, (rows + 31) / 32);
 }
 
 int sm_count_b() {
@@ -201,18 +358,35 @@ paris_status launch_np(const paris_index* idx, const QueryState& qs, const Chunk
   static int configured = 0;
   if ((int)smem > configured) {
     PARIS_CUDA(cudaFuncSetAttribute(lbscan_batched_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PARIS_CUDA(cudaFuncSetAttribute(pilot_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = (int)smem;
   }
   const int ntiles = (cs.qc + 2 * NP - 1) / (2 * NP);
   const int64_t groups = (idx->n + 31) / 32;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count_b(), (groups + 63) / 64));
   const int64_t entries = (int64_t)idx->card * 16;
+  const uint4* sax = reinterpret_cast<const uint4*>(idx->sax);
   pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
       qs.qtable + cs.q0 * entries, cs.qc, entries, cs.packed);
-  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax), idx->n,
-                                                            idx->card, cs.packed, qs.thr, cs.q0, cs.qc, ntiles,
-                                                            cs.count, cs.rows, cs.lb, cs.cap, stop, status);
-  note_launches(2);
+  note_launches(1);
+  if (stop && cs.cap < idx->n && groups >= 64 * kPilotStride) {
+    // lists that would overflow anyway are handed to the tensor-core screening up front
+    DevBuf pilot;
+    if (!pilot.alloc((size_t)cs.qc * 4, st)) return fail(PARIS_ENOMEM, "pilot counts");
+    PARIS_CUDA(cudaMemsetAsync(pilot.p, 0, (size_t)cs.qc * 4, st));
+    const int64_t samples = (groups + kPilotStride - 1) / kPilotStride;
+    const int pgrid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count_b(), samples / 64));
+    pilot_kernel<NP><<<pgrid, kBThreads, smem, st>>>(sax, idx->n, idx->card, cs.packed, qs.thr, cs.q0, cs.qc, ntiles,
+                                                    kPilotStride, pilot.as<uint32_t>());
+    pilot_route_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(pilot.as<uint32_t>(), cs.qc, kPilotStride,
+                                                           kPilotRoute * (double)cs.cap, cs.cap, cs.count);
+    note_launches(2);
+    PARIS_CUDA(cudaGetLastError());
+  }
+  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(sax, idx->n, idx->card, cs.packed, qs.thr, cs.q0, cs.qc,
+                                                            ntiles, cs.count, cs.rows, cs.lb, cs.cap, stop,
+                                                            block_groups(), status);
+  note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }

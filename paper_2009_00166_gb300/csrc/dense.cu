@@ -60,7 +60,8 @@ struct DenseParams {
   uint32_t* rows;
   float* lb;
   int64_t cap;
-  uint32_t* status;
+  uint32_t* status;    // device errors (timeouts)
+  uint32_t* overflow;  // set when a list passed its capacity (the per-query count says which)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
               P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
               P.lb[(int64_t)slot * P.cap + p] = x;
             } else {
-              atomicOr(P.status, DEV_CAND_OVERFLOW);
+              atomicOr(P.overflow, DEV_CAND_OVERFLOW);
             }
           }
         }
@@ -394,6 +395,18 @@ __global__ void dense_select_kernel(const uint32_t* __restrict__ count, int qc, 
 __global__ void dense_reset_kernel(uint32_t* __restrict__ count, const int* __restrict__ slots, int nd) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nd) count[slots[i]] = 0u;
+}
+
+// A query whose screened list overflowed keeps the k-th best exact candidate it did store: that
+// distance, rounded up by the fp32 error factor, bounds the true k-th distance, so the query's
+// threshold drops to it before the screening is repeated. Counts such queries in *nover.
+__global__ void tighten_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap, const uint32_t* __restrict__ kth,
+                               float cg, uint32_t* __restrict__ thr, int64_t q0, int* __restrict__ nover) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= qc || (int64_t)count[j] <= cap) return;
+  const float t = __fmul_ru(__uint_as_float(kth[j]), cg);
+  atomicMin(thr + q0 + j, __float_as_uint(t));  // non-negative floats order like their bits
+  atomicAdd(nover, 1);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -483,6 +496,20 @@ paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
   return PARIS_OK;
 }
 
+paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int* nover, cudaStream_t st) {
+  *nover = 0;
+  DevBuf nb;
+  if (!nb.alloc(4, st)) return fail(PARIS_ENOMEM, "overflow counter");
+  PARIS_CUDA(cudaMemsetAsync(nb.p, 0, 4, st));
+  tighten_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.count, cs.qc, cs.cap, cs.kth, qs.cg, qs.thr, cs.q0,
+                                                      nb.as<int>());
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  PARIS_CUDA(cudaMemcpyAsync(nover, nb.p, 4, cudaMemcpyDeviceToHost, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  return PARIS_OK;
+}
+
 void release_shadow(paris_index* idx) {
   if (idx->shadow) dev_free(idx->shadow, (size_t)idx->n * idx->len * 2, nullptr);
   if (idx->xnorm) dev_free(idx->xnorm, (size_t)idx->n * sizeof(float2), nullptr);
@@ -494,7 +521,8 @@ void release_shadow(paris_index* idx) {
 
 // Screens the chunk's queries whose candidate lists overflowed `cap`: their lists are rebuilt
 // from the BF16 pass. Returns the number of such queries in *nd_out.
-paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, int* nd_out, cudaStream_t st) {
+paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, uint32_t* overflow, int* nd_out,
+                          cudaStream_t st) {
   *nd_out = 0;
   DevBuf slots, ndbuf;
   if (!slots.alloc((size_t)cs.qc * 4, st) || !ndbuf.alloc(4, st)) return fail(PARIS_ENOMEM, "dense scratch");
@@ -541,6 +569,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   P.lb = cs.lb;
   P.cap = cs.cap;
   P.status = qs.status;
+  P.overflow = overflow;
   const int64_t ntiles = (idx->n + BN - 1) / BN;
   const int grid = (int)std::min<int64_t>(ntiles, sm_count_dense());
   const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;

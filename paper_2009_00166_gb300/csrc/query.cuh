@@ -7,6 +7,7 @@ namespace paris {
 constexpr int kContCap = 512;   // exact re-rank contenders per query
 constexpr int kLimbs = 20;      // 640-bit exact squared distances, least significant bit 2^-298
 constexpr int kMaxLeaf = 4096;  // leaf capacity limit
+constexpr int kDenseRetries = 4;  // repeated screenings of an overflowed list before giving up
 
 // Per-call query state, all device pointers.
 struct QueryState {
@@ -77,8 +78,9 @@ bool dense_supported(const paris_index* idx, int k);
 void dense_margins(int len, float* c1, float* c2);
 paris_status ensure_shadow(paris_index* idx, cudaStream_t st);
 void release_shadow(paris_index* idx);
-paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, int* nd_out,
+paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, uint32_t* overflow, int* nd_out,
                           cudaStream_t st);
+paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int* nover, cudaStream_t st);
 
 paris_status launch_select(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            int64_t* out_idx, float* out_dist, cudaStream_t st);

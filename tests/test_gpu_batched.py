@@ -52,3 +52,28 @@ def test_bad_query_tile(setup):
     P, idx, q, _ = setup
     with pytest.raises(P.ParisError):
         run(P, idx, q, 1, mode=P.PARIS_MODE_BATCHED, query_tile=6)
+
+
+def test_pilot_routing_keeps_answers_exact():
+    """A collection large enough for the pilot pass (every 64th group of 32 rows): queries whose
+    lists would overflow go to the tensor-core screening up front, tight ones are scanned, and
+    every answer still equals the oracle's; a tile mixing both kinds is covered by the order."""
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    n = 300_007
+    x = synth.random_walk(n, 256, seed=9)
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    src = np.random.default_rng(4).choice(n, 13, replace=False)
+    sig = np.array([1.0, 0.01, 1.5, 1.0, 0.1, 2.0, 0.01, 1.0, 1.0, 0.05, 1.2, 1.0, 0.01])
+    q = np.stack([synth.noisy_queries(x[src[j:j + 1]], sig[j], [5, j])[0] for j in range(13)])
+    for k in (1, 10):
+        wi, wd = oknn.knn(x, q, k)
+        for qt in (0, 4, 12):
+            gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=P.PARIS_REFINE_MIXED)
+            assert np.array_equal(gi, wi)
+            assert np.allclose(gd, wd, rtol=1e-5, atol=0)
+            assert st["dense_queries"] >= 1
+        fi, fd, _ = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, precision=P.PARIS_REFINE_FP32)
+        assert np.array_equal(fi, wi) and np.allclose(fd, wd, rtol=1e-5, atol=0)
+    idx.free()
