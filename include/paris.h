@@ -133,6 +133,25 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
                                 const paris_query_opts* opts, paris_query_stats* stats,
                                 void* stream);
 
+/* Exact k-NN over several collections in one call (the paper's search, Sec. 3.3 and Alg. 7-9,
+ * applied per collection): queries[c] ([nq[c]][len of idx[c]], row-major fp32, device or host)
+ * are answered against idx[c] only, into out_idx[c] / out_dist[c] ([nq[c]][k], laid out and
+ * ordered as in paris_exact_knn; out_dist may be NULL, or out_dist[c] NULL for a collection).
+ * In BATCHED mode the lower-bound scans of all collections run as ONE launch per chunk round:
+ * the collections' CTAs split the GPU in proportion to rows x query tiles, and each CTA streams
+ * its collection's summaries (16 B per series whatever the series length). Lengths may differ
+ * (e.g. 128, 256 and 1024); cardinalities must be equal. The query tile of the launch is
+ * opts->query_tile, or the tuned tile of the collection with the most work. Other phases run
+ * per collection on the same stream. 1 <= nidx <= 4. stats (NULL = none) points to nidx
+ * records; the shared scan's device time is reported in each record's ms_lbscan.
+ * Errors: EINVAL for a bad argument of any collection (nothing is run), otherwise as
+ * paris_exact_knn_ex; the first failing collection's status is returned. */
+paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx,
+                                   const float* const* queries, const int64_t* nq, int32_t k,
+                                   int64_t* const* out_idx, float* const* out_dist,
+                                   const paris_query_opts* opts, paris_query_stats* stats,
+                                   void* stream);
+
 /* Number of GPU kernels the library has launched since it was loaded (all threads). */
 uint64_t paris_kernel_launches(void);
 

@@ -28,6 +28,7 @@ from .binding import (  # noqa: F401
     paris_encode,
     paris_exact_knn,
     paris_exact_knn_ex,
+    paris_exact_knn_multi,
     paris_export_order,
     paris_export_sax,
     paris_free,

@@ -74,6 +74,8 @@ def lib():
             "paris_free": ([VP], None),
             "paris_exact_knn": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_exact_knn_ex": ([VP, P, I64, I32, P, P, C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
+            "paris_exact_knn_multi": ([C.POINTER(VP), I32, C.POINTER(VP), C.POINTER(C.c_int64), I32, C.POINTER(VP),
+                                       C.POINTER(VP), C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
             "paris_last_error": ([], C.c_char_p),
             "paris_kernel_launches": ([], C.c_uint64),
             "paris_set_allocator": ([ALLOC_FN, FREE_FN, VP], I32),
@@ -204,6 +206,35 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
     if want_stats:
         return out_idx, out_dist, stats.as_dict()
     return out_idx, out_dist
+
+
+def paris_exact_knn_multi(indexes, queries, k: int, mode: int = PARIS_MODE_BATCHED, query_tile: int = 0,
+                          chunk: int = 0, precision: int = PARIS_REFINE_FP32, seed: int = PARIS_SEED_DESCENT,
+                          want_stats: bool = False, stream=None):
+    """paris_exact_knn_multi: one (idx [nq][k], dist [nq][k]) pair per collection[, stats dicts]."""
+    import torch
+    m = len(indexes)
+    if len(queries) != m:
+        raise ValueError("one query block per index")
+    outs = []
+    for q in queries:
+        nq = int(q.shape[0])
+        dev = q.device if hasattr(q, "device") else torch.device("cpu")
+        outs.append((torch.empty((nq, k), dtype=torch.int64, device=dev),
+                     torch.empty((nq, k), dtype=torch.float32, device=dev)))
+    VPA = C.c_void_p * m
+    hs = VPA(*[ix.handle for ix in indexes])
+    qp = VPA(*[_ptr(q) for q in queries])
+    nqs = (C.c_int64 * m)(*[int(q.shape[0]) for q in queries])
+    oi = VPA(*[_ptr(o[0]) for o in outs])
+    od = VPA(*[_ptr(o[1]) for o in outs])
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed)
+    stats = (QueryStats * m)()
+    _check(lib().paris_exact_knn_multi(hs, m, qp, nqs, k, oi, od, C.byref(opts), stats if want_stats else None,
+                                       _stream(stream)))
+    if want_stats:
+        return outs, [st.as_dict() for st in stats]
+    return outs
 
 
 def paris_exact_knn(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, stream=None):

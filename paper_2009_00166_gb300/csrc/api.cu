@@ -522,14 +522,7 @@ static paris_status check_query_args(const paris_index* idx, const float* querie
   return PARIS_OK;
 }
 
-paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
-                                int64_t* out_idx, float* out_dist, const paris_query_opts* opts,
-                                paris_query_stats* stats, void* stream) {
-  clear_error();
-  PARIS_TRY(check_query_args(idx, queries, nq, k));
-  if (nq > 0 && !out_idx) return fail(PARIS_EINVAL, "out_idx is NULL");
-  paris_query_opts o{};
-  if (opts) o = *opts;
+static paris_status check_query_opts(const paris_index* idx, const paris_query_opts& o) {
   for (int i = 0; i < 3; ++i)
     if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
   if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
@@ -539,53 +532,88 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     return fail(PARIS_EINVAL, "unknown precision %d", o.precision);
   if (o.mode != PARIS_MODE_PLAIN && o.mode != PARIS_MODE_BATCHED)
     return fail(PARIS_EINVAL, "unknown mode %d", o.mode);
-  if (stats) std::memset(stats, 0, sizeof *stats);
-  if (nq == 0) return PARIS_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t qbytes = (size_t)nq * idx->len * sizeof(float);
-  Staged sq, si, sd;
-  PARIS_TRY(sq.in(queries, qbytes, st));
-  PARIS_TRY(si.out(out_idx, (size_t)nq * k * sizeof(int64_t), st));
-  PARIS_TRY(sd.out(out_dist, (size_t)nq * k * sizeof(float), st));
-  QueryState qs;
-  DevBuf qblock;
-  PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
-  PhaseTimer timer(stats != nullptr, st);
-  timer.begin(0);
-  PARIS_TRY(launch_query_prep(idx, qs, st));
-  timer.end(0);
-  timer.begin(1);
-  DevBuf lkeys;
-  if (o.seed == PARIS_SEED_LEARNED) {
-    if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
-    PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
-    qs.keys = lkeys.as<uint64_t>();
-    qs.nk = idx->seed_r + 1;
+  if (o.mode == PARIS_MODE_BATCHED && o.query_tile) {
+    bool known = false;
+    for (int i = 0; i < kNumQueryTiles; ++i) known = known || kQueryTiles[i] == o.query_tile;
+    if (!known || !query_tile_fits(o.query_tile, idx->card))
+      return fail(PARIS_EINVAL, "query_tile %d is not one of 2, 4, 8, 12 or does not fit", o.query_tile);
   }
-  PARIS_TRY(launch_descent(idx, qs, st));
-  timer.end(1);
-  // chunks of queries whose candidate lists are resident together; in MIXED precision the lists
-  // are short and a query whose list overflows is screened by the BF16 tensor-core pass instead
-  const bool mixed = o.precision == PARIS_REFINE_MIXED && dense_supported(idx, k);
-  const int64_t cap = mixed ? std::min<int64_t>(idx->n, std::max<int64_t>(idx->n / 128, 8192)) : idx->n;
-  DevBuf lbstatus;
-  if (!lbstatus.alloc(4, st)) return fail(PARIS_ENOMEM, "status word");
-  uint32_t* lb_status = mixed ? lbstatus.as<uint32_t>() : qs.status;  // overflow is the signal in MIXED
+  return PARIS_OK;
+}
+
+namespace {
+
+// One collection's exact k-NN call: staged queries and outputs, query state, the candidate
+// lists of the current chunk of queries and the per-phase timers. The phases are split so that
+// several collections can share one batched lower-bound scan launch per chunk round.
+struct KnnJob {
+  const paris_index* idx = nullptr;
+  int64_t nq = 0;
+  int k = 1;
+  paris_query_opts o{};
+  paris_query_stats* stats = nullptr;
+  cudaStream_t st = nullptr;
+  Staged sq, si, sd;
+  QueryState qs;
+  DevBuf qblock, lkeys, lbstatus, cblock;
+  ChunkState cs;
+  PhaseTimer timer{false, nullptr};
+  bool mixed = false;
+  uint32_t* lb_status = nullptr;  // MIXED: overflow is the signal, not an error
+  int64_t qc = 0;
+  int qt = 0;
   int64_t dense_total = 0;
   int rescreens = 0;
-  int64_t qc = o.chunk;
-  if (qc <= 0) {
-    size_t freeb = 0, totalb = 0;
-    cudaMemGetInfo(&freeb, &totalb);
-    double budget = std::min((double)freeb * 0.3, 24.0e9);
-    qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0 +
-                             (double)idx->card * 32.0));
-    qc = std::max<int64_t>(1, std::min<int64_t>(qc, 4096));
-  }
-  qc = std::min(qc, nq);
-  DevBuf cblock;
-  ChunkState cs;
-  {
+
+  int64_t chunks() const { return qc > 0 ? (nq + qc - 1) / qc : 0; }
+
+  // Staging, query preparation, approximate search and the candidate-list buffers.
+  paris_status setup(const paris_index* index, const float* queries, int64_t n_q, int32_t kk, int64_t* out_idx,
+                     float* out_dist, const paris_query_opts& opts, paris_query_stats* st_out, cudaStream_t stream,
+                     double budget_share) {
+    idx = index;
+    nq = n_q;
+    k = kk;
+    o = opts;
+    stats = st_out;
+    st = stream;
+    timer.on = stats != nullptr;
+    timer.st = st;
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    if (nq == 0) return PARIS_OK;
+    const size_t qbytes = (size_t)nq * idx->len * sizeof(float);
+    PARIS_TRY(sq.in(queries, qbytes, st));
+    PARIS_TRY(si.out(out_idx, (size_t)nq * k * sizeof(int64_t), st));
+    PARIS_TRY(sd.out(out_dist, (size_t)nq * k * sizeof(float), st));
+    PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
+    timer.begin(0);
+    PARIS_TRY(launch_query_prep(idx, qs, st));
+    timer.end(0);
+    timer.begin(1);
+    if (o.seed == PARIS_SEED_LEARNED) {
+      if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
+      PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
+      qs.keys = lkeys.as<uint64_t>();
+      qs.nk = idx->seed_r + 1;
+    }
+    PARIS_TRY(launch_descent(idx, qs, st));
+    timer.end(1);
+    // chunks of queries whose candidate lists are resident together; in MIXED precision the lists
+    // are short and a query whose list overflows is screened by the BF16 tensor-core pass instead
+    mixed = o.precision == PARIS_REFINE_MIXED && dense_supported(idx, k);
+    const int64_t cap = mixed ? std::min<int64_t>(idx->n, std::max<int64_t>(idx->n / 128, 8192)) : idx->n;
+    if (!lbstatus.alloc(4, st)) return fail(PARIS_ENOMEM, "status word");
+    lb_status = mixed ? lbstatus.as<uint32_t>() : qs.status;
+    qc = o.chunk;
+    if (qc <= 0) {
+      size_t freeb = 0, totalb = 0;
+      cudaMemGetInfo(&freeb, &totalb);
+      double budget = std::min((double)freeb * 0.3, 24.0e9) * budget_share;
+      qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0 +
+                               (double)idx->card * 32.0));
+      qc = std::max<int64_t>(1, std::min<int64_t>(qc, 4096));
+    }
+    qc = std::min(qc, nq);
     size_t off = 0;
     auto take = [&](size_t b) {
       size_t o2 = off;
@@ -616,29 +644,35 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
     cs.lb2 = (float*)(b + o_l2);
     cs.bucket = (uint32_t*)(b + o_bk);
     cs.packed = (uint32_t*)(b + o_pk);
+    qt = o.mode == PARIS_MODE_BATCHED ? o.query_tile : 0;
+    return PARIS_OK;
   }
-  int qt = 0;
-  if (o.mode == PARIS_MODE_BATCHED && o.query_tile) {
-    qt = o.query_tile;
-    bool known = false;
-    for (int i = 0; i < kNumQueryTiles; ++i) known = known || kQueryTiles[i] == qt;
-    if (!known || !query_tile_fits(qt, idx->card))
-      return fail(PARIS_EINVAL, "query_tile %d is not one of 2, 4, 8, 12 or does not fit", qt);
-  }
-  for (int64_t q0 = 0; q0 < nq; q0 += qc) {
-    cs.q0 = q0;
-    cs.qc = (int)std::min<int64_t>(qc, nq - q0);
+
+  // Selects chunk `c` and clears its candidate counts; tunes the query tile on first use.
+  paris_status begin_chunk(int64_t c) {
+    cs.q0 = c * qc;
+    cs.qc = (int)std::min<int64_t>(qc, nq - cs.q0);
     PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
     if (o.mode == PARIS_MODE_BATCHED && qt == 0) PARIS_TRY(tuned_query_tile(idx, qs, cs, st, &qt));
+    return PARIS_OK;
+  }
+
+  // This collection's own lower-bound scan of the current chunk.
+  paris_status scan_chunk() {
     timer.begin(2);
     if (o.mode == PARIS_MODE_BATCHED) {
       PARIS_TRY(launch_lbscan_batched(idx, qs, cs, qt, mixed ? 1 : 0, lb_status, st));
     } else {
       for (int j = 0; j < cs.qc; ++j)
-        PARIS_TRY(launch_lbscan(idx, qs, q0 + j, cs.count + j, cs.rows + (int64_t)j * cap,
-                                cs.lb + (int64_t)j * cap, cap, lb_status, mixed ? 1 : 0, st));
+        PARIS_TRY(launch_lbscan(idx, qs, cs.q0 + j, cs.count + j, cs.rows + (int64_t)j * cs.cap,
+                                cs.lb + (int64_t)j * cs.cap, cs.cap, lb_status, mixed ? 1 : 0, st));
     }
     timer.end(2);
+    return PARIS_OK;
+  }
+
+  // Tensor-core screening (MIXED), refinement and selection of the current chunk.
+  paris_status finish_chunk() {
     if (mixed) {
       int nd = 0;
       timer.begin(5);
@@ -671,33 +705,119 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
       PARIS_TRY(launch_select(idx, qs, cs, (int64_t*)si.dev, (float*)sd.dev, st));
       timer.end(4);
     }
+    return PARIS_OK;
   }
-  PARIS_TRY(si.finish(st));
-  PARIS_TRY(sd.finish(st));
-  PARIS_TRY(check_status_word(qs.status, st, "paris_exact_knn"));
-  if (stats) {
-    double ms[6] = {0, 0, 0, 0, 0, 0};
-    timer.collect(ms);
-    stats->ms_dense = ms[5];
-    stats->query_tile = qt;
-    stats->rescreens = rescreens;
-    stats->dense_queries = dense_total;
-    stats->ms_prep = ms[0];
-    stats->ms_descent = ms[1];
-    stats->ms_lbscan = ms[2];
-    stats->ms_refine = ms[3];
-    stats->ms_select = ms[4];
-    unsigned long long c[4];
-    PARIS_CUDA(cudaMemcpyAsync(c, qs.counters, sizeof c, cudaMemcpyDeviceToHost, st));
-    PARIS_CUDA(cudaStreamSynchronize(st));
-    stats->candidates = (int64_t)c[0];
-    stats->refined = (int64_t)c[1];
-    stats->contenders = (int64_t)c[2];
-    stats->leaf_rows = (int64_t)c[3];
+
+  // Outputs back to host buffers, device status and statistics.
+  paris_status finish(const char* what) {
+    if (nq == 0) return PARIS_OK;
+    PARIS_TRY(si.finish(st));
+    PARIS_TRY(sd.finish(st));
+    PARIS_TRY(check_status_word(qs.status, st, what));
+    if (stats) {
+      double ms[6] = {0, 0, 0, 0, 0, 0};
+      timer.collect(ms);
+      stats->ms_dense = ms[5];
+      stats->query_tile = qt;
+      stats->rescreens = rescreens;
+      stats->dense_queries = dense_total;
+      stats->ms_prep = ms[0];
+      stats->ms_descent = ms[1];
+      stats->ms_lbscan = ms[2];
+      stats->ms_refine = ms[3];
+      stats->ms_select = ms[4];
+      unsigned long long c[4];
+      PARIS_CUDA(cudaMemcpyAsync(c, qs.counters, sizeof c, cudaMemcpyDeviceToHost, st));
+      PARIS_CUDA(cudaStreamSynchronize(st));
+      stats->candidates = (int64_t)c[0];
+      stats->refined = (int64_t)c[1];
+      stats->contenders = (int64_t)c[2];
+      stats->leaf_rows = (int64_t)c[3];
+    }
+    return PARIS_OK;
   }
-  return PARIS_OK;
+};
+
+}  // namespace
+
+paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
+                                int64_t* out_idx, float* out_dist, const paris_query_opts* opts,
+                                paris_query_stats* stats, void* stream) {
+  clear_error();
+  PARIS_TRY(check_query_args(idx, queries, nq, k));
+  if (nq > 0 && !out_idx) return fail(PARIS_EINVAL, "out_idx is NULL");
+  paris_query_opts o{};
+  if (opts) o = *opts;
+  PARIS_TRY(check_query_opts(idx, o));
+  KnnJob job;
+  PARIS_TRY(job.setup(idx, queries, nq, k, out_idx, out_dist, o, stats, (cudaStream_t)stream, 1.0));
+  for (int64_t c = 0; c < job.chunks(); ++c) {
+    PARIS_TRY(job.begin_chunk(c));
+    PARIS_TRY(job.scan_chunk());
+    PARIS_TRY(job.finish_chunk());
+  }
+  return job.finish("paris_exact_knn");
 }
 
+paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx, const float* const* queries,
+                                   const int64_t* nq, int32_t k, int64_t* const* out_idx, float* const* out_dist,
+                                   const paris_query_opts* opts, paris_query_stats* stats, void* stream) {
+  clear_error();
+  if (nidx < 1 || nidx > kMaxScanJobs) return fail(PARIS_EINVAL, "nidx must be in [1, %d]", kMaxScanJobs);
+  if (!idx || !queries || !nq || !out_idx) return fail(PARIS_EINVAL, "NULL argument array");
+  paris_query_opts o{};
+  if (opts) o = *opts;
+  for (int c = 0; c < nidx; ++c) {
+    PARIS_TRY(check_query_args(idx[c], queries[c], nq[c], k));
+    if (nq[c] > 0 && !out_idx[c]) return fail(PARIS_EINVAL, "out_idx[%d] is NULL", c);
+    PARIS_TRY(check_query_opts(idx[c], o));
+    if (idx[c]->card != idx[0]->card) return fail(PARIS_EINVAL, "the collections must share the cardinality");
+    for (int d = 0; d < c; ++d)
+      if (out_idx[d] && out_idx[d] == out_idx[c]) return fail(PARIS_EINVAL, "out_idx[%d] aliases out_idx[%d]", c, d);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  KnnJob jobs[kMaxScanJobs];
+  int64_t rounds = 0;
+  double total = 0.0;
+  for (int c = 0; c < nidx; ++c) total += (double)idx[c]->n;
+  for (int c = 0; c < nidx; ++c) {
+    // candidate-list memory is shared in proportion to collection size
+    PARIS_TRY(jobs[c].setup(idx[c], queries[c], nq[c], k, out_idx[c], out_dist ? out_dist[c] : nullptr, o,
+                            stats ? &stats[c] : nullptr, st, (double)idx[c]->n / total));
+    rounds = std::max(rounds, jobs[c].chunks());
+  }
+  for (int64_t r = 0; r < rounds; ++r) {
+    ScanJob sj[kMaxScanJobs];
+    int m = 0, qt = 0;
+    double most = -1.0;
+    for (int c = 0; c < nidx; ++c) {
+      if (r >= jobs[c].chunks()) continue;
+      PARIS_TRY(jobs[c].begin_chunk(r));
+      if (o.mode == PARIS_MODE_BATCHED) {
+        sj[m++] = ScanJob{idx[c], &jobs[c].qs, &jobs[c].cs, jobs[c].mixed ? 1 : 0, jobs[c].lb_status};
+        const double work = (double)idx[c]->n * jobs[c].cs.qc;
+        if (work > most) {  // one query tile per launch: the tuned tile of the largest share
+          most = work;
+          qt = jobs[c].qt;
+        }
+      } else {
+        PARIS_TRY(jobs[c].scan_chunk());
+      }
+    }
+    if (m > 0) {
+      // one launch scans every collection's chunk; its time is charged to each collection
+      for (int c = 0; c < nidx; ++c)
+        if (r < jobs[c].chunks()) jobs[c].timer.begin(2);
+      PARIS_TRY(launch_lbscan_batched_multi(sj, m, qt, st));
+      for (int c = 0; c < nidx; ++c)
+        if (r < jobs[c].chunks()) jobs[c].timer.end(2);
+    }
+    for (int c = 0; c < nidx; ++c)
+      if (r < jobs[c].chunks()) PARIS_TRY(jobs[c].finish_chunk());
+  }
+  for (int c = 0; c < nidx; ++c) PARIS_TRY(jobs[c].finish("paris_exact_knn_multi"));
+  return PARIS_OK;
+}
 paris_status paris_exact_knn(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
                              int64_t* out_idx, float* out_dist, void* stream) {
   return paris_exact_knn_ex(idx, queries, nq, k, out_idx, out_dist, nullptr, nullptr, stream);

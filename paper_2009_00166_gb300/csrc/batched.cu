@@ -184,29 +184,67 @@ __device__ __forceinline__ void lane_offsets(int lane, uint32_t (&offp)[8]) {
   }
 }
 
+// One collection's share of a batched scan launch: its summaries, the chunk's packed tables,
+// thresholds and candidate lists, and the CTAs [cta0, cta0 + ncta) that split its rows.
+struct ScanColl {
+  const uint4* sax;
+  int64_t n;
+  const uint32_t* packed;
+  const uint32_t* thr;
+  int64_t q0;
+  int qc, ntiles;
+  uint32_t* count;
+  uint32_t* rows;
+  float* lb;
+  int64_t cap;
+  uint32_t* pilot;  // pilot counts [qc] (pilot launch only)
+  int stop;         // lists may overflow (MIXED): overflowed queries leave the scan
+  uint32_t* status;  // device status word of the collection's call
+  int cta0, ncta;
+};
+
+constexpr int kMaxColl = 4;
+static_assert(kMaxColl == kMaxScanJobs, "one scan descriptor per collection of a multi-collection call");
+
+struct ScanWork {
+  int ncoll;
+  int card;
+  int64_t block_groups;  // row groups per block of a CTA's range
+  int64_t stride;        // pilot: every stride-th row group
+  ScanColl c[kMaxColl];
+};
+
+__device__ __forceinline__ int coll_of_block(const ScanWork& W) {
+  int ci = 0;
+  while (ci + 1 < W.ncoll && (int)blockIdx.x >= W.c[ci + 1].cta0) ++ci;
+  return ci;
+}
+
 template <int NP>
-__global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
-    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
-    const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, uint32_t* __restrict__ count,
-    uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap, int stop_on_overflow,
-    int64_t block_groups, uint32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __grid_constant__ ScanWork W) {
   constexpr int QT = 2 * NP;
   extern __shared__ __align__(16) uint32_t s_tab[];  // region r (64 KB): pairs 2r, 2r+1
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
   __shared__ int s_skip;
+  const ScanColl& C = W.c[coll_of_block(W)];
+  const uint4* __restrict__ sax = C.sax;
+  const int64_t n = C.n, cap = C.cap;
+  const int qc = C.qc, stop_on_overflow = C.stop;
+  uint32_t* __restrict__ count = C.count;
+  uint32_t* __restrict__ status = C.status;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t offp[8];
   lane_offsets(lane, offp);
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
   const int64_t groups = (n + 31) >> 5;
-  const int64_t per = (groups + gridDim.x - 1) / gridDim.x;
-  const int64_t g0 = (int64_t)blockIdx.x * per, g1 = min(groups, g0 + per);
-  const int64_t entries = (int64_t)card * 16;
+  const int64_t per = (groups + C.ncta - 1) / C.ncta;
+  const int64_t g0 = (int64_t)(blockIdx.x - C.cta0) * per, g1 = min(groups, g0 + per);
+  const int64_t entries = (int64_t)W.card * 16;
   // The CTA's row range may be cut into blocks that every query tile passes over in turn.
-  for (int64_t b0 = g0; b0 < g1; b0 += block_groups) {
-    const int64_t b1 = min(g1, b0 + block_groups);
-    for (int tile = 0; tile < ntiles; ++tile) {
+  for (int64_t b0 = g0; b0 < g1; b0 += W.block_groups) {
+    const int64_t b1 = min(g1, b0 + W.block_groups);
+    for (int tile = 0; tile < C.ntiles; ++tile) {
       const int qb = tile * QT;
       __syncthreads();  // the previous tile's tables and flags are no longer read
       if (threadIdx.x == 0) {
@@ -223,7 +261,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
       }
       __syncthreads();
       if (s_skip) continue;
-      load_tile<NP>(packed, entries, qb, qc, thr, q0, s_active, s_tab, s_thr);
+      load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, s_active, s_tab, s_thr);
       __syncthreads();
       __half2 thh[NP];
       tile_thresholds<NP>(s_thr, thh);
@@ -251,9 +289,9 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
               const int qa = qb + 2 * p;
               const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
               append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa,
-                          out_rows + (int64_t)qa * cap, out_lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
+                          C.rows + (int64_t)qa * cap, C.lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
               append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qa + 1,
-                          out_rows + (int64_t)(qa + 1) * cap, out_lb + (int64_t)(qa + 1) * cap, cap,
+                          C.rows + (int64_t)(qa + 1) * cap, C.lb + (int64_t)(qa + 1) * cap, cap,
                           ovf[2 * p + 1], status);
             }
           }
@@ -273,27 +311,28 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(
 // test as the scan). Queries whose scaled count says the list would overflow go straight to the
 // tensor-core screening instead of appending rows that would be discarded.
 template <int NP>
-__global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(
-    const uint4* __restrict__ sax, int64_t n, int card, const uint32_t* __restrict__ packed,
-    const uint32_t* __restrict__ thr, int64_t q0, int qc, int ntiles, int64_t stride, uint32_t* __restrict__ pilot) {
+__global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(const __grid_constant__ ScanWork W) {
   constexpr int QT = 2 * NP;
   extern __shared__ __align__(16) uint32_t s_tab[];
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
   __shared__ uint32_t s_cnt[QT];
+  const ScanColl& C = W.c[coll_of_block(W)];
+  const int64_t n = C.n, stride = W.stride;
+  const int qc = C.qc;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t offp[8];
   lane_offsets(lane, offp);
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
   const int64_t samples = (((n + 31) >> 5) + stride - 1) / stride;
-  const int64_t per = (samples + gridDim.x - 1) / gridDim.x;
-  const int64_t s0 = (int64_t)blockIdx.x * per, s1 = min(samples, s0 + per);
-  const int64_t entries = (int64_t)card * 16;
+  const int64_t per = (samples + C.ncta - 1) / C.ncta;
+  const int64_t s0 = (int64_t)(blockIdx.x - C.cta0) * per, s1 = min(samples, s0 + per);
+  const int64_t entries = (int64_t)W.card * 16;
   if (threadIdx.x < QT) s_active[threadIdx.x] = true;
-  for (int tile = 0; tile < ntiles; ++tile) {
+  for (int tile = 0; tile < C.ntiles; ++tile) {
     const int qb = tile * QT;
     __syncthreads();
-    load_tile<NP>(packed, entries, qb, qc, thr, q0, s_active, s_tab, s_thr);
+    load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, s_active, s_tab, s_thr);
     if (threadIdx.x < QT) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     __half2 thh[NP];
@@ -304,7 +343,7 @@ __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(
     for (int64_t it = s0 + wib; it < s1; it += nw) {
       const int64_t row = it * stride * 32 + lane;
       const bool rv = row < n;
-      const uint4 word = rv ? __ldcg(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+      const uint4 word = rv ? __ldcg(C.sax + row) : make_uint4(0u, 0u, 0u, 0u);
       __half2 sum[NP];
       const uint32_t keepmask = row_keep_bits<NP>(word, rv, offp, tab, thh, sum);
 #pragma unroll
@@ -317,7 +356,7 @@ __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(
     }
     __syncthreads();
     if (threadIdx.x < QT && qb + (int)threadIdx.x < qc && s_cnt[threadIdx.x])
-      atomicAdd(pilot + qb + threadIdx.x, s_cnt[threadIdx.x]);
+      atomicAdd(C.pilot + qb + threadIdx.x, s_cnt[threadIdx.x]);
   }
 }
 
@@ -351,41 +390,114 @@ int sm_count_b() {
   return sms;
 }
 
+// Splits `grid` CTAs (grid >= ncoll) among the collections in proportion to their work, at
+// least one each.
+void split_ctas(ScanWork& W, const double* work, int grid) {
+  double total = 0.0;
+  for (int c = 0; c < W.ncoll; ++c) total += work[c];
+  int given = 0;
+  for (int c = 0; c < W.ncoll; ++c) {
+    W.c[c].ncta = std::max(1, total > 0.0 ? (int)(grid * work[c] / total) : grid / W.ncoll);
+    given += W.c[c].ncta;
+  }
+  while (given > grid) {  // take from the collection holding the most CTAs
+    int best = 0;
+    for (int c = 1; c < W.ncoll; ++c)
+      if (W.c[c].ncta > W.c[best].ncta) best = c;
+    --W.c[best].ncta;
+    --given;
+  }
+  while (given < grid) {  // give to the collection with the most work per CTA
+    int best = 0;
+    for (int c = 1; c < W.ncoll; ++c)
+      if (work[c] / W.c[c].ncta > work[best] / W.c[best].ncta) best = c;
+    ++W.c[best].ncta;
+    ++given;
+  }
+  int off = 0;
+  for (int c = 0; c < W.ncoll; ++c) {
+    W.c[c].cta0 = off;
+    off += W.c[c].ncta;
+  }
+}
+
 template <int NP>
-paris_status launch_np(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int stop, uint32_t* status,
-                       cudaStream_t st) {
-  const size_t smem = batched_smem(NP, idx->card);
+paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
+  const int card = jobs[0].idx->card;
+  const size_t smem = batched_smem(NP, card);
   static int configured = 0;
   if ((int)smem > configured) {
     PARIS_CUDA(cudaFuncSetAttribute(lbscan_batched_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PARIS_CUDA(cudaFuncSetAttribute(pilot_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = (int)smem;
   }
-  const int ntiles = (cs.qc + 2 * NP - 1) / (2 * NP);
-  const int64_t groups = (idx->n + 31) / 32;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count_b(), (groups + 63) / 64));
-  const int64_t entries = (int64_t)idx->card * 16;
-  const uint4* sax = reinterpret_cast<const uint4*>(idx->sax);
-  pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
-      qs.qtable + cs.q0 * entries, cs.qc, entries, cs.packed);
-  note_launches(1);
-  if (stop && cs.cap < idx->n && groups >= 64 * kPilotStride) {
-    // lists that would overflow anyway are handed to the tensor-core screening up front
-    DevBuf pilot;
-    if (!pilot.alloc((size_t)cs.qc * 4, st)) return fail(PARIS_ENOMEM, "pilot counts");
-    PARIS_CUDA(cudaMemsetAsync(pilot.p, 0, (size_t)cs.qc * 4, st));
-    const int64_t samples = (groups + kPilotStride - 1) / kPilotStride;
-    const int pgrid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count_b(), samples / 64));
-    pilot_kernel<NP><<<pgrid, kBThreads, smem, st>>>(sax, idx->n, idx->card, cs.packed, qs.thr, cs.q0, cs.qc, ntiles,
-                                                    kPilotStride, pilot.as<uint32_t>());
-    pilot_route_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(pilot.as<uint32_t>(), cs.qc, kPilotStride,
-                                                           kPilotRoute * (double)cs.cap, cs.cap, cs.count);
-    note_launches(2);
+  const int64_t entries = (int64_t)card * 16;
+  const int sms = sm_count_b();
+  ScanWork W{}, PW{};
+  W.card = PW.card = card;
+  W.block_groups = block_groups();
+  W.stride = PW.stride = kPilotStride;
+  double work[kMaxColl], pwork[kMaxColl];
+  int64_t groups_total = 0, pilot_samples = 0;
+  DevBuf pilot;
+  int64_t pilot_q = 0;
+  for (int j = 0; j < m; ++j) pilot_q += jobs[j].cs->qc;
+  if (!pilot.alloc((size_t)pilot_q * 4, st)) return fail(PARIS_ENOMEM, "pilot counts");
+  int64_t pilot_off = 0;
+  bool any_pilot = false;
+  for (int j = 0; j < m; ++j) {
+    const paris_index* idx = jobs[j].idx;
+    const QueryState& qs = *jobs[j].qs;
+    const ChunkState& cs = *jobs[j].cs;
+    const int64_t groups = (idx->n + 31) / 32;
+    ScanColl C{};
+    C.sax = reinterpret_cast<const uint4*>(idx->sax);
+    C.n = idx->n;
+    C.packed = cs.packed;
+    C.thr = qs.thr;
+    C.q0 = cs.q0;
+    C.qc = cs.qc;
+    C.ntiles = (cs.qc + 2 * NP - 1) / (2 * NP);
+    C.count = cs.count;
+    C.rows = cs.rows;
+    C.lb = cs.lb;
+    C.cap = cs.cap;
+    C.stop = jobs[j].stop;
+    C.status = jobs[j].status;
+    pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
+        qs.qtable + cs.q0 * entries, cs.qc, entries, cs.packed);
+    note_launches(1);
+    W.c[W.ncoll] = C;
+    work[W.ncoll++] = (double)groups * C.ntiles;
+    groups_total += groups;
+    if (C.stop && cs.cap < idx->n && groups >= 64 * kPilotStride) {
+      // lists that would overflow anyway are handed to the tensor-core screening up front
+      C.pilot = pilot.as<uint32_t>() + pilot_off;
+      pilot_off += cs.qc;
+      const int64_t samples = (groups + kPilotStride - 1) / kPilotStride;
+      PW.c[PW.ncoll] = C;
+      pwork[PW.ncoll++] = (double)samples * C.ntiles;
+      pilot_samples += samples;
+      any_pilot = true;
+    }
+  }
+  if (any_pilot) {
+    PARIS_CUDA(cudaMemsetAsync(pilot.p, 0, (size_t)pilot_off * 4, st));
+    const int pgrid = (int)std::max<int64_t>(PW.ncoll, std::min<int64_t>(sms, pilot_samples / 64));
+    split_ctas(PW, pwork, pgrid);
+    pilot_kernel<NP><<<pgrid, kBThreads, smem, st>>>(PW);
+    note_launches(1);
+    for (int c = 0; c < PW.ncoll; ++c) {
+      const ScanColl& C = PW.c[c];
+      pilot_route_kernel<<<(C.qc + 255) / 256, 256, 0, st>>>(C.pilot, C.qc, kPilotStride, kPilotRoute * (double)C.cap,
+                                                             C.cap, C.count);
+      note_launches(1);
+    }
     PARIS_CUDA(cudaGetLastError());
   }
-  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(sax, idx->n, idx->card, cs.packed, qs.thr, cs.q0, cs.qc,
-                                                            ntiles, cs.count, cs.rows, cs.lb, cs.cap, stop,
-                                                            block_groups(), status);
+  const int grid = (int)std::max<int64_t>(W.ncoll, std::min<int64_t>(sms, (groups_total + 63) / 64));
+  split_ctas(W, work, grid);
+  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(W);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
@@ -397,15 +509,24 @@ const int kQueryTiles[kNumQueryTiles] = {2, 4, 8, 12};
 
 bool query_tile_fits(int qt, int card) { return batched_smem(qt / 2, card) <= 200 * 1024; }
 
-paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,
-                                   int stop_on_overflow, uint32_t* status, cudaStream_t st) {
+paris_status launch_lbscan_batched_multi(const ScanJob* jobs, int m, int qt, cudaStream_t st) {
+  if (m < 1 || m > kMaxScanJobs) return fail(PARIS_EINVAL, "between 1 and %d collections per batched scan", kMaxScanJobs);
+  for (int j = 1; j < m; ++j)
+    if (jobs[j].idx->card != jobs[0].idx->card)
+      return fail(PARIS_EINVAL, "collections of one batched scan share the cardinality");
   switch (qt) {
-    case 2: return launch_np<1>(idx, qs, cs, stop_on_overflow, status, st);
-    case 4: return launch_np<2>(idx, qs, cs, stop_on_overflow, status, st);
-    case 8: return launch_np<4>(idx, qs, cs, stop_on_overflow, status, st);
-    case 12: return launch_np<6>(idx, qs, cs, stop_on_overflow, status, st);
+    case 2: return launch_np<1>(jobs, m, st);
+    case 4: return launch_np<2>(jobs, m, st);
+    case 8: return launch_np<4>(jobs, m, st);
+    case 12: return launch_np<6>(jobs, m, st);
     default: return fail(PARIS_EINVAL, "query_tile must be one of 2, 4, 8, 12 (got %d)", qt);
   }
+}
+
+paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,
+                                   int stop_on_overflow, uint32_t* status, cudaStream_t st) {
+  ScanJob job{idx, &qs, &cs, stop_on_overflow, status};
+  return launch_lbscan_batched_multi(&job, 1, qt, st);
 }
 
 }  // namespace paris

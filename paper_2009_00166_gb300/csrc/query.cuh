@@ -66,6 +66,16 @@ extern const int kQueryTiles[kNumQueryTiles];
 bool query_tile_fits(int qt, int card);
 paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,
                                    int stop_on_overflow, uint32_t* status, cudaStream_t st);
+// Several collections (same cardinality) in one scan launch; their CTAs split the grid by work.
+struct ScanJob {
+  const paris_index* idx;
+  const QueryState* qs;
+  const ChunkState* cs;
+  int stop;          // lists may overflow (MIXED refinement)
+  uint32_t* status;  // the collection's device status word
+};
+constexpr int kMaxScanJobs = 4;
+paris_status launch_lbscan_batched_multi(const ScanJob* jobs, int m, int qt, cudaStream_t st);
 
 // Learned approximate-search keys (mlp.cu): [nq][r+1], own key first.
 paris_status learned_keys(const paris_index* idx, const paris_seed_model* md, int r, const QueryState& qs,
