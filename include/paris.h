@@ -152,6 +152,39 @@ paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx,
                                    const paris_query_opts* opts, paris_query_stats* stats,
                                    void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Captured batches: the batched search of Sec. 3.3 recorded ONCE as a CUDA graph for batches of
+ * exactly nq queries against one index, then replayed per batch (no per-kernel launch cost and
+ * no host round trip inside the batch). The plan owns device buffers for nq queries and
+ * [nq][k] outputs; idx stays borrowed and must outlive the plan. The first run executes eagerly
+ * (it also picks the query tile when opts->query_tile is 0) and records the graph; later runs
+ * copy the queries in, replay the graph and copy the outputs out. Results are those of
+ * paris_exact_knn_ex with the same options. A run whose tensor-core screening overflowed a
+ * candidate list (MIXED) is redone eagerly, with the repeated screenings, before returning.
+ * Descent seed only (PARIS_SEED_LEARNED: EINVAL). One thread at a time per plan.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct paris_knn_plan paris_knn_plan;
+
+typedef struct paris_knn_plan_stats {
+  int64_t graph_kernels; /* kernels in the recorded graph (0 before the first run) */
+  int64_t replays;       /* runs served by the graph */
+  int64_t eager_runs;    /* runs executed eagerly (the first, and any that overflowed) */
+  int32_t captured;      /* 1 once the graph exists */
+  int32_t query_tile;    /* query tile of the batched scan */
+} paris_knn_plan_stats;
+
+/* nq >= 1; k, opts as paris_exact_knn_ex. Allocates the plan's buffers (and the BF16 shadow in
+ * MIXED). Errors: EINVAL, ENOMEM, ECUDA. */
+paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k,
+                                   const paris_query_opts* opts, paris_knn_plan** out);
+/* queries: [nq][len] fp32, device or host; out_idx [nq][k] int64 and out_dist [nq][k] fp32
+ * (NULL allowed), device or host. The call is ordered after earlier work on `stream` and later
+ * work on `stream` waits for it; it returns once the outputs are written. */
+paris_status paris_knn_plan_run(paris_knn_plan* plan, const float* queries, int64_t* out_idx,
+                                float* out_dist, void* stream);
+paris_status paris_knn_plan_info(const paris_knn_plan* plan, paris_knn_plan_stats* out);
+void paris_knn_plan_free(paris_knn_plan* plan); /* NULL-safe */
+
 /* Number of GPU kernels the library has launched since it was loaded (all threads). */
 uint64_t paris_kernel_launches(void);
 

@@ -29,6 +29,7 @@ from .binding import (  # noqa: F401
     paris_exact_knn,
     paris_exact_knn_ex,
     paris_exact_knn_multi,
+    KnnPlan,
     paris_export_order,
     paris_export_sax,
     paris_free,

@@ -48,6 +48,14 @@ class QueryStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PlanStats(C.Structure):
+    _fields_ = [("graph_kernels", C.c_int64), ("replays", C.c_int64), ("eager_runs", C.c_int64),
+                ("captured", C.c_int32), ("query_tile", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class IndexView(C.Structure):
     _fields_ = [("n", C.c_int64), ("len", C.c_int32), ("w", C.c_int32), ("card", C.c_int32),
                 ("leaf_capacity", C.c_int32), ("series", C.c_void_p), ("keys_sorted", C.c_void_p),
@@ -74,6 +82,10 @@ def lib():
             "paris_free": ([VP], None),
             "paris_exact_knn": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_exact_knn_ex": ([VP, P, I64, I32, P, P, C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
+            "paris_knn_plan_create": ([VP, I64, I32, C.POINTER(QueryOpts), C.POINTER(VP)], I32),
+            "paris_knn_plan_run": ([VP, P, P, P, VP], I32),
+            "paris_knn_plan_info": ([VP, C.POINTER(PlanStats)], I32),
+            "paris_knn_plan_free": ([VP], None),
             "paris_exact_knn_multi": ([C.POINTER(VP), I32, C.POINTER(VP), C.POINTER(C.c_int64), I32, C.POINTER(VP),
                                        C.POINTER(VP), C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
             "paris_last_error": ([], C.c_char_p),
@@ -235,6 +247,44 @@ def paris_exact_knn_multi(indexes, queries, k: int, mode: int = PARIS_MODE_BATCH
     if want_stats:
         return outs, [st.as_dict() for st in stats]
     return outs
+
+
+class KnnPlan:
+    """paris_knn_plan_*: a batch of exactly ``nq`` queries recorded once as a CUDA graph."""
+
+    def __init__(self, index: ParisIndex, nq: int, k: int, mode: int = PARIS_MODE_BATCHED, query_tile: int = 0,
+                 chunk: int = 0, precision: int = PARIS_REFINE_FP32):
+        self.index, self.nq, self.k = index, int(nq), int(k)
+        opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision)
+        h = C.c_void_p()
+        _check(lib().paris_knn_plan_create(index.handle, self.nq, self.k, C.byref(opts), C.byref(h)))
+        self.handle = h
+
+    def run(self, queries, out_idx=None, out_dist=None, stream=None):
+        import torch
+        dev = queries.device if hasattr(queries, "device") else torch.device("cpu")
+        if out_idx is None:
+            out_idx = torch.empty((self.nq, self.k), dtype=torch.int64, device=dev)
+        if out_dist is None:
+            out_dist = torch.empty((self.nq, self.k), dtype=torch.float32, device=dev)
+        _check(lib().paris_knn_plan_run(self.handle, _ptr(queries), _ptr(out_idx), _ptr(out_dist), _stream(stream)))
+        return out_idx, out_dist
+
+    def info(self) -> dict:
+        st = PlanStats()
+        _check(lib().paris_knn_plan_info(self.handle, C.byref(st)))
+        return st.as_dict()
+
+    def free(self):
+        if self.handle:
+            lib().paris_knn_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def paris_exact_knn(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, stream=None):

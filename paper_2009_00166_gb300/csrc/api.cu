@@ -586,18 +586,11 @@ struct KnnJob {
     PARIS_TRY(si.out(out_idx, (size_t)nq * k * sizeof(int64_t), st));
     PARIS_TRY(sd.out(out_dist, (size_t)nq * k * sizeof(float), st));
     PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
-    timer.begin(0);
-    PARIS_TRY(launch_query_prep(idx, qs, st));
-    timer.end(0);
-    timer.begin(1);
     if (o.seed == PARIS_SEED_LEARNED) {
       if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
-      PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
       qs.keys = lkeys.as<uint64_t>();
       qs.nk = idx->seed_r + 1;
     }
-    PARIS_TRY(launch_descent(idx, qs, st));
-    timer.end(1);
     // chunks of queries whose candidate lists are resident together; in MIXED precision the lists
     // are short and a query whose list overflows is screened by the BF16 tensor-core pass instead
     mixed = o.precision == PARIS_REFINE_MIXED && dense_supported(idx, k);
@@ -625,7 +618,9 @@ struct KnnJob {
            o_hist = take((size_t)qc * 2048 * 4), o_sel = take((size_t)qc * 8), o_cc = take((size_t)qc * 4),
            o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4),
            o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4),
-           o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4);
+           o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4), o_pl = take((size_t)qc * 4),
+           o_ds = take((size_t)qc * 4), o_dn = take(8), o_no = take(8),
+           o_dq = take(dense_query_rows(qc) * idx->len * 2), o_dm = take(dense_query_rows(qc) * 8);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
     char* b = cblock.as<char>();
     cs.cap = cap;
@@ -644,8 +639,67 @@ struct KnnJob {
     cs.lb2 = (float*)(b + o_l2);
     cs.bucket = (uint32_t*)(b + o_bk);
     cs.packed = (uint32_t*)(b + o_pk);
+    cs.pilot = (uint32_t*)(b + o_pl);
+    cs.dslots = (int*)(b + o_ds);
+    cs.dnd = (int*)(b + o_dn);
+    cs.nover = (int*)(b + o_no);
+    cs.dqbf = (void*)(b + o_dq);
+    cs.dqnm = (float2*)(b + o_dm);
+    cs.dq_rows = (int64_t)dense_query_rows(qc);
     qt = o.mode == PARIS_MODE_BATCHED ? o.query_tile : 0;
     return PARIS_OK;
+  }
+
+  // Query preparation and approximate search (the seeds of every query).
+  paris_status front() {
+    if (nq == 0) return PARIS_OK;
+    timer.begin(0);
+    PARIS_TRY(launch_query_prep(idx, qs, st));
+    timer.end(0);
+    timer.begin(1);
+    if (o.seed == PARIS_SEED_LEARNED)
+      PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
+    PARIS_TRY(launch_descent(idx, qs, st));
+    timer.end(1);
+    return PARIS_OK;
+  }
+
+  // The whole call as one stream of launches with no host synchronisation (for graph capture):
+  // the query tile must be known; screened lists that overflow are only counted (cs.nover).
+  paris_status record_all() {
+    if (nq == 0) return PARIS_OK;
+    if (o.mode == PARIS_MODE_BATCHED && qt == 0) return fail(PARIS_EINTERNAL, "query tile unknown at capture");
+    PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+    PARIS_CUDA(cudaMemsetAsync(cs.nover, 0, 4, st));
+    PARIS_TRY(front());
+    for (int64_t c = 0; c < chunks(); ++c) {
+      cs.q0 = c * qc;
+      cs.qc = (int)std::min<int64_t>(qc, nq - cs.q0);
+      PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
+      PARIS_TRY(scan_chunk());
+      if (mixed) PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, lb_status, nullptr, st));
+      PARIS_TRY(launch_refine(idx, qs, cs, st));
+      PARIS_TRY(launch_select(idx, qs, cs, (int64_t*)si.dev, (float*)sd.dev, st));
+      if (mixed) PARIS_TRY(launch_tighten(qs, cs, st));
+    }
+    return PARIS_OK;
+  }
+
+  // The whole call with host decisions (tuning, screening tile counts, repeated screenings).
+  paris_status run_eager(const char* what) {
+    if (nq == 0) return PARIS_OK;
+    PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+    dense_total = 0;
+    rescreens = 0;
+    PARIS_TRY(front());
+    for (int64_t c = 0; c < chunks(); ++c) {
+      PARIS_TRY(begin_chunk(c));
+      PARIS_TRY(scan_chunk());
+      PARIS_TRY(finish_chunk());
+    }
+    return finish(what);
   }
 
   // Selects chunk `c` and clears its candidate counts; tunes the query tile on first use.
@@ -751,12 +805,166 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   PARIS_TRY(check_query_opts(idx, o));
   KnnJob job;
   PARIS_TRY(job.setup(idx, queries, nq, k, out_idx, out_dist, o, stats, (cudaStream_t)stream, 1.0));
-  for (int64_t c = 0; c < job.chunks(); ++c) {
-    PARIS_TRY(job.begin_chunk(c));
-    PARIS_TRY(job.scan_chunk());
-    PARIS_TRY(job.finish_chunk());
+  return job.run_eager("paris_exact_knn");
+}
+
+// A captured query pipeline: the plan owns its query and output buffers and one KnnJob; the
+// first run executes eagerly (choosing the query tile) and then records the whole call as one
+// CUDA graph that later runs replay.
+struct paris_knn_plan {
+  const paris_index* idx = nullptr;
+  int64_t nq = 0;
+  int k = 1;
+  paris_query_opts o{};
+  cudaStream_t pst = nullptr;
+  cudaEvent_t ev = nullptr;
+  DevBuf qbuf, obi, obd;
+  KnnJob* job = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0, replays = 0, eager_runs = 0;
+  bool capture_failed = false;
+};
+
+paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k, const paris_query_opts* opts,
+                                   paris_knn_plan** out) {
+  clear_error();
+  if (!out) return fail(PARIS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nq < 1) return fail(PARIS_EINVAL, "a plan needs nq >= 1");
+  PARIS_TRY(check_query_args(idx, (const float*)1, nq, k));
+  paris_query_opts o{};
+  if (opts) o = *opts;
+  PARIS_TRY(check_query_opts(idx, o));
+  if (o.seed == PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "captured plans use the descent seed only");
+  auto* pl = new (std::nothrow) paris_knn_plan;
+  if (!pl) return fail(PARIS_ENOMEM, "plan");
+  pl->idx = idx;
+  pl->nq = nq;
+  pl->k = k;
+  pl->o = o;
+  auto bail = [&](paris_status s) {
+    paris_knn_plan_free(pl);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&pl->pst, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(PARIS_ECUDA, "plan stream"));
   }
-  return job.finish("paris_exact_knn");
+  if (!pl->qbuf.alloc((size_t)nq * idx->len * 4, pl->pst) || !pl->obi.alloc((size_t)nq * k * 8, pl->pst) ||
+      !pl->obd.alloc((size_t)nq * k * 4, pl->pst))
+    return bail(fail(PARIS_ENOMEM, "plan buffers"));
+  pl->job = new (std::nothrow) KnnJob;
+  if (!pl->job) return bail(fail(PARIS_ENOMEM, "plan"));
+  paris_status st = pl->job->setup(idx, pl->qbuf.as<float>(), nq, k, pl->obi.as<int64_t>(), pl->obd.as<float>(), o,
+                                   nullptr, pl->pst, 1.0);
+  if (st != PARIS_OK) return bail(st);
+  if (pl->job->mixed) {
+    st = ensure_shadow(const_cast<paris_index*>(idx), pl->pst);
+    if (st != PARIS_OK) return bail(st);
+  }
+  if (cudaStreamSynchronize(pl->pst) != cudaSuccess) return bail(fail(PARIS_ECUDA, "plan setup"));
+  *out = pl;
+  return PARIS_OK;
+}
+
+void paris_knn_plan_free(paris_knn_plan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  delete pl->job;
+  pl->qbuf.release();
+  pl->obi.release();
+  pl->obd.release();
+  if (pl->pst) {
+    cudaStreamSynchronize(pl->pst);
+    cudaStreamDestroy(pl->pst);
+  }
+  if (pl->ev) cudaEventDestroy(pl->ev);
+  delete pl;
+}
+
+namespace {
+paris_status plan_capture(paris_knn_plan* pl) {
+  const uint64_t before = launch_count();
+  if (cudaStreamBeginCapture(pl->pst, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PARIS_ECUDA, "stream capture could not start");
+  }
+  paris_status s = pl->job->record_all();
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(pl->pst, &g);
+  if (s != PARIS_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return s != PARIS_OK ? s : fail(PARIS_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  }
+  if (cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(PARIS_ECUDA, "graph instantiation failed");
+  }
+  pl->graph = g;
+  pl->kernels = (int64_t)(launch_count() - before);
+  // the recording counted kernels it did not run; replays count them when they run
+  note_launches(-(int)pl->kernels);
+  return PARIS_OK;
+}
+}  // namespace
+
+paris_status paris_knn_plan_run(paris_knn_plan* pl, const float* queries, int64_t* out_idx, float* out_dist,
+                                void* stream) {
+  clear_error();
+  if (!pl || !queries || !out_idx) return fail(PARIS_EINVAL, "NULL argument");
+  cudaStream_t cst = (cudaStream_t)stream;
+  KnnJob& job = *pl->job;
+  PARIS_CUDA(cudaEventRecord(pl->ev, cst));
+  PARIS_CUDA(cudaStreamWaitEvent(pl->pst, pl->ev, 0));
+  PARIS_CUDA(cudaMemcpyAsync(pl->qbuf.p, queries, (size_t)pl->nq * pl->idx->len * 4, cudaMemcpyDefault, pl->pst));
+  bool eager = true;
+  if (pl->exec) {
+    PARIS_CUDA(cudaGraphLaunch(pl->exec, pl->pst));
+    note_launches((int)pl->kernels);
+    ++pl->replays;
+    uint32_t word[2] = {0u, 0u};
+    PARIS_CUDA(cudaMemcpyAsync(&word[0], job.qs.status, 4, cudaMemcpyDeviceToHost, pl->pst));
+    PARIS_CUDA(cudaMemcpyAsync(&word[1], job.cs.nover, 4, cudaMemcpyDeviceToHost, pl->pst));
+    PARIS_CUDA(cudaStreamSynchronize(pl->pst));
+    // a screened list that overflowed needs the host-driven repeats: run the batch eagerly
+    eager = word[1] != 0u;
+    if (!eager) PARIS_TRY(check_status_word(job.qs.status, pl->pst, "paris_knn_plan_run"));
+  }
+  if (eager) {
+    PARIS_TRY(job.run_eager("paris_knn_plan_run"));
+    ++pl->eager_runs;
+    if (!pl->exec && !pl->capture_failed) {
+      // the query tile is settled now; later runs replay the recorded call
+      if (plan_capture(pl) != PARIS_OK) {
+        pl->capture_failed = true;  // keep running eagerly
+        clear_error();
+      }
+    }
+  }
+  PARIS_CUDA(cudaMemcpyAsync(out_idx, pl->obi.p, (size_t)pl->nq * pl->k * 8, cudaMemcpyDefault, pl->pst));
+  if (out_dist)
+    PARIS_CUDA(cudaMemcpyAsync(out_dist, pl->obd.p, (size_t)pl->nq * pl->k * 4, cudaMemcpyDefault, pl->pst));
+  PARIS_CUDA(cudaEventRecord(pl->ev, pl->pst));
+  PARIS_CUDA(cudaStreamWaitEvent(cst, pl->ev, 0));
+  PARIS_CUDA(cudaStreamSynchronize(pl->pst));
+  return PARIS_OK;
+}
+
+paris_status paris_knn_plan_info(const paris_knn_plan* pl, paris_knn_plan_stats* out) {
+  clear_error();
+  if (!pl || !out) return fail(PARIS_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof *out);
+  out->graph_kernels = pl->kernels;
+  out->replays = pl->replays;
+  out->eager_runs = pl->eager_runs;
+  out->captured = pl->exec != nullptr;
+  out->query_tile = pl->job ? pl->job->qt : 0;
+  return PARIS_OK;
 }
 
 paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx, const float* const* queries,
@@ -784,6 +992,7 @@ paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx, 
     // candidate-list memory is shared in proportion to collection size
     PARIS_TRY(jobs[c].setup(idx[c], queries[c], nq[c], k, out_idx[c], out_dist ? out_dist[c] : nullptr, o,
                             stats ? &stats[c] : nullptr, st, (double)idx[c]->n / total));
+    PARIS_TRY(jobs[c].front());
     rounds = std::max(rounds, jobs[c].chunks());
   }
   for (int64_t r = 0; r < rounds; ++r) {

@@ -439,12 +439,6 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   W.stride = PW.stride = kPilotStride;
   double work[kMaxColl], pwork[kMaxColl];
   int64_t groups_total = 0, pilot_samples = 0;
-  DevBuf pilot;
-  int64_t pilot_q = 0;
-  for (int j = 0; j < m; ++j) pilot_q += jobs[j].cs->qc;
-  if (!pilot.alloc((size_t)pilot_q * 4, st)) return fail(PARIS_ENOMEM, "pilot counts");
-  int64_t pilot_off = 0;
-  bool any_pilot = false;
   for (int j = 0; j < m; ++j) {
     const paris_index* idx = jobs[j].idx;
     const QueryState& qs = *jobs[j].qs;
@@ -472,17 +466,15 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     groups_total += groups;
     if (C.stop && cs.cap < idx->n && groups >= 64 * kPilotStride) {
       // lists that would overflow anyway are handed to the tensor-core screening up front
-      C.pilot = pilot.as<uint32_t>() + pilot_off;
-      pilot_off += cs.qc;
+      C.pilot = cs.pilot;
+      PARIS_CUDA(cudaMemsetAsync(cs.pilot, 0, (size_t)cs.qc * 4, st));
       const int64_t samples = (groups + kPilotStride - 1) / kPilotStride;
       PW.c[PW.ncoll] = C;
       pwork[PW.ncoll++] = (double)samples * C.ntiles;
       pilot_samples += samples;
-      any_pilot = true;
     }
   }
-  if (any_pilot) {
-    PARIS_CUDA(cudaMemsetAsync(pilot.p, 0, (size_t)pilot_off * 4, st));
+  if (PW.ncoll > 0) {
     const int pgrid = (int)std::max<int64_t>(PW.ncoll, std::min<int64_t>(sms, pilot_samples / 64));
     split_ctas(PW, pwork, pgrid);
     pilot_kernel<NP><<<pgrid, kBThreads, smem, st>>>(PW);

@@ -48,7 +48,8 @@ constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
 struct DenseParams {
   int64_t n;
   int len, nkb;
-  int qtile, nd;
+  int qtile, nd;         // nd < 0: the count of screened queries is read from nd_dev
+  const int* nd_dev;
   const float2* xnorm;  // [n]: (|x|^2, |x|)
   const float2* qnorm;  // [nd_pad]
   const int* qslot;     // [nd]: chunk-local slot of dense query d
@@ -152,6 +153,9 @@ template <int PHASE>
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
     dense_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DenseParams P) {
   extern __shared__ uint8_t dsm_raw[];
+  // a launch for a query tile past the screened queries has nothing to do (uniform per grid)
+  const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
+  if (P.qtile * BM >= nd) return;
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* smA = base;
   uint8_t* smB = base + A_BYTES;
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     const int c = (warp - 2) >> 2;
     const int m = qd * 32 + lane;
     const int d = P.qtile * BM + m;
-    const bool valid = d < P.nd;
+    const bool valid = d < nd;
     float qn = 0.f, qrt = 0.f, thr_q = 0.f;
     int slot = 0;
     uint32_t* thr_ptr = nullptr;
@@ -362,8 +366,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 
 // BF16 shadow of the series and fp32 (|x|^2, |x|) per row; one warp per row.
 __global__ void shadow_kernel(const float* __restrict__ x, int64_t n, int len, __nv_bfloat16* __restrict__ out,
-                              float2* __restrict__ norms, const int* __restrict__ gather, int64_t q0, int64_t rows_pad) {
+                              float2* __restrict__ norms, const int* __restrict__ gather, int64_t q0, int64_t rows_pad,
+                              const int* __restrict__ n_dev = nullptr) {
   const int lane = threadIdx.x & 31;
+  if (n_dev) n = *n_dev;  // rows to convert counted on the device (the rest of rows_pad is zero)
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows_pad; r += warps) {
     const bool real = r < n;
@@ -392,9 +398,9 @@ __global__ void dense_select_kernel(const uint32_t* __restrict__ count, int qc, 
   *nd = m;
 }
 
-__global__ void dense_reset_kernel(uint32_t* __restrict__ count, const int* __restrict__ slots, int nd) {
+__global__ void dense_reset_kernel(uint32_t* __restrict__ count, const int* __restrict__ slots, const int* nd) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nd) count[slots[i]] = 0u;
+  if (i < *nd) count[slots[i]] = 0u;
 }
 
 // A query whose screened list overflowed keeps the k-th best exact candidate it did store: that
@@ -496,16 +502,19 @@ paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
   return PARIS_OK;
 }
 
-paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int* nover, cudaStream_t st) {
-  *nover = 0;
-  DevBuf nb;
-  if (!nb.alloc(4, st)) return fail(PARIS_ENOMEM, "overflow counter");
-  PARIS_CUDA(cudaMemsetAsync(nb.p, 0, 4, st));
+paris_status launch_tighten(const QueryState& qs, const ChunkState& cs, cudaStream_t st) {
   tighten_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.count, cs.qc, cs.cap, cs.kth, qs.cg, qs.thr, cs.q0,
-                                                      nb.as<int>());
+                                                      cs.nover);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
-  PARIS_CUDA(cudaMemcpyAsync(nover, nb.p, 4, cudaMemcpyDeviceToHost, st));
+  return PARIS_OK;
+}
+
+paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int* nover, cudaStream_t st) {
+  *nover = 0;
+  PARIS_CUDA(cudaMemsetAsync(cs.nover, 0, 4, st));
+  PARIS_TRY(launch_tighten(qs, cs, st));
+  PARIS_CUDA(cudaMemcpyAsync(nover, cs.nover, 4, cudaMemcpyDeviceToHost, st));
   PARIS_CUDA(cudaStreamSynchronize(st));
   return PARIS_OK;
 }
@@ -520,31 +529,37 @@ void release_shadow(paris_index* idx) {
 }
 
 // Screens the chunk's queries whose candidate lists overflowed `cap`: their lists are rebuilt
-// from the BF16 pass. Returns the number of such queries in *nd_out.
+// from the BF16 pass. Eager form: the number of such queries is read back (*nd_out) and exactly
+// that many query tiles are launched. Graph form (nd_out == NULL): nothing is read back; one
+// launch per possible query tile, each leaving at once when its tile is past the count.
 paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, uint32_t* overflow, int* nd_out,
                           cudaStream_t st) {
-  *nd_out = 0;
-  DevBuf slots, ndbuf;
-  if (!slots.alloc((size_t)cs.qc * 4, st) || !ndbuf.alloc(4, st)) return fail(PARIS_ENOMEM, "dense scratch");
-  dense_select_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, slots.as<int>(), ndbuf.as<int>());
+  if (nd_out) *nd_out = 0;
+  int* slots = cs.dslots;
+  int* ndev = cs.dnd;
+  dense_select_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, slots, ndev);
   note_launches(1);
-  int nd = 0;
-  PARIS_CUDA(cudaMemcpyAsync(&nd, ndbuf.p, 4, cudaMemcpyDeviceToHost, st));
-  PARIS_CUDA(cudaStreamSynchronize(st));
-  *nd_out = nd;
-  if (nd == 0) return PARIS_OK;
-  PARIS_TRY(ensure_shadow(idx, st));
-  const int64_t nd_pad = ((int64_t)nd + BM - 1) / BM * BM;
-  DevBuf qbf, qnm;
-  if (!qbf.alloc((size_t)nd_pad * idx->len * 2, st) || !qnm.alloc((size_t)nd_pad * sizeof(float2), st))
-    return fail(PARIS_ENOMEM, "dense query tiles");
-  shadow_kernel<<<(unsigned)std::max<int64_t>(1, (nd_pad + 7) / 8), 256, 0, st>>>(
-      qs.queries, nd, idx->len, qbf.as<__nv_bfloat16>(), qnm.as<float2>(), slots.as<int>(), cs.q0, nd_pad);
-  dense_reset_kernel<<<(nd + 255) / 256, 256, 0, st>>>(cs.count, slots.as<int>(), nd);
+  int nd = -1;
+  int64_t tiles = ((int64_t)cs.qc + BM - 1) / BM;
+  if (nd_out) {
+    PARIS_CUDA(cudaMemcpyAsync(&nd, ndev, 4, cudaMemcpyDeviceToHost, st));
+    PARIS_CUDA(cudaStreamSynchronize(st));
+    *nd_out = nd;
+    if (nd == 0) return PARIS_OK;
+    tiles = ((int64_t)nd + BM - 1) / BM;
+  }
+  if (!idx->shadow) {
+    if (!nd_out) return fail(PARIS_EINTERNAL, "BF16 shadow must exist before a captured screening");
+    PARIS_TRY(ensure_shadow(idx, st));
+  }
+  const int64_t rows_pad = tiles * BM;
+  shadow_kernel<<<(unsigned)std::max<int64_t>(1, (rows_pad + 7) / 8), 256, 0, st>>>(
+      qs.queries, nd, idx->len, (__nv_bfloat16*)cs.dqbf, cs.dqnm, slots, cs.q0, rows_pad, nd_out ? nullptr : ndev);
+  dense_reset_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.count, slots, ndev);
   note_launches(2);
   PARIS_CUDA(cudaGetLastError());
   CUtensorMap mapA;
-  PARIS_TRY(make_bf16_map(&mapA, qbf.p, nd_pad, idx->len, BM));
+  PARIS_TRY(make_bf16_map(&mapA, cs.dqbf, cs.dq_rows, idx->len, BM));
   static bool attr = false;
   if (!attr) {
     PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
@@ -556,9 +571,10 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   P.len = idx->len;
   P.nkb = idx->len / BKE;
   P.nd = nd;
+  P.nd_dev = ndev;
   P.xnorm = idx->xnorm;
-  P.qnorm = qnm.as<float2>();
-  P.qslot = slots.as<int>();
+  P.qnorm = cs.dqnm;
+  P.qslot = slots;
   P.q0 = cs.q0;
   P.thr = qs.thr;
   P.k = qs.k;
@@ -574,7 +590,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   const int grid = (int)std::min<int64_t>(ntiles, sm_count_dense());
   const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;
   for (int phase = 1; phase <= 2; ++phase) {
-    for (int t = 0; t < (int)(nd_pad / BM); ++t) {
+    for (int t = 0; t < (int)tiles; ++t) {
       P.qtile = t;
       if (phase == 1)
         dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);
@@ -586,5 +602,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   }
   return PARIS_OK;
 }
+
+size_t dense_query_rows(int64_t qc) { return (size_t)((qc + BM - 1) / BM * BM); }
 
 }  // namespace paris

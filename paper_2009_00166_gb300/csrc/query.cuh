@@ -48,6 +48,13 @@ struct ChunkState {
   uint32_t* cont_count = nullptr;  // [qc]
   uint32_t* cont_rows = nullptr;   // [qc][kContCap]
   uint32_t* cont_limbs = nullptr;  // [qc][kContCap][kLimbs]
+  uint32_t* pilot = nullptr;       // [qc] pilot-pass kept counts (batched scan)
+  int* dslots = nullptr;           // [qc] chunk slots of the queries screened by the tensor cores
+  int* dnd = nullptr;              // [1] number of such queries
+  int* nover = nullptr;            // [1] screened lists that overflowed
+  void* dqbf = nullptr;            // [dq_rows][len] BF16 query tiles of the screening
+  float2* dqnm = nullptr;          // [dq_rows] (|q|^2, |q|) of those queries
+  int64_t dq_rows = 0;             // qc rounded up to whole query tiles
 };
 
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
@@ -91,6 +98,9 @@ void release_shadow(paris_index* idx);
 paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, uint32_t* overflow, int* nd_out,
                           cudaStream_t st);
 paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int* nover, cudaStream_t st);
+// Graph form of the above: adds the count of overflowed lists to cs.nover without reading it.
+paris_status launch_tighten(const QueryState& qs, const ChunkState& cs, cudaStream_t st);
+size_t dense_query_rows(int64_t qc);
 
 paris_status launch_select(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            int64_t* out_idx, float* out_dist, cudaStream_t st);
