@@ -11,10 +11,20 @@
 //          candidate (with d~ - M as its lower bound) for the exact fp32 re-check (Alg. 9).
 // Rows are only discarded when provably farther than the k-th neighbour, so answers stay exact.
 //
-// Kernel shape: one persistent CTA per SM; warp 0 streams 64-row tiles of the BF16 shadow of
-// the series into a 4-stage shared-memory ring with TMA (128-byte swizzle), warp 1 issues the
-// tensor-core MMAs (one thread) into two TMEM accumulators of 128 x 64 fp32, and warps 2-5 read
-// the accumulators back (tcgen05.ld) and run the screening epilogue, one query per thread.
+// Per pair the epilogue first applies a cheaper test with the row tile's norm range (smallest
+// and largest |x|^2, largest |x|): pass 2 drops a pair when rd(xn_min - 2 q~.x~) exceeds
+// ru(thr + M_max - |q|^2), which implies d~ - M > thr for the pair's own norms; only the pairs
+// that survive get the exact interval above. Pass 1 ranks the looser upper ends
+// ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max), which still bound the distance from above.
+//
+// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries; warp 0 streams
+// 64-row tiles of the BF16 shadow of the series, with the rows' fp32 norms, into a 3-stage
+// shared-memory ring with TMA (128-byte swizzle; the norms by a bulk copy), warp 1 issues the
+// tensor-core MMAs (one thread) of both query tiles against each row tile into double-buffered
+// TMEM accumulators (2 x 2 x 128 x 64 fp32), and warps 2-17 read the accumulators back
+// (tcgen05.ld) and run the screening epilogue: one query per thread and 32 rows of the tile per
+// warp. A stage is refilled once the MMAs have read it and the epilogue has read its norms.
+// Each row tile read from HBM serves 256 queries.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,16 +43,20 @@ namespace {
 constexpr int BM = 128;             // queries per tile (MMA M)
 constexpr int BN = 64;              // series rows per tile (MMA N)
 constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
-constexpr int STAGES = 4;           // shared-memory ring depth for row tiles
-constexpr int DENSE_THREADS = 320;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
-constexpr int EPI_WARPS = 8;        // two per TMEM lane quadrant, one per 32-column half of a tile
+constexpr int QTILES = 2;           // query tiles sharing each row tile
+constexpr int STAGES = 3;           // shared-memory ring depth for row tiles
+constexpr int DENSE_THREADS = 576;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-17: epilogue
+constexpr int EPI_WARPS = 16;       // per TMEM lane quadrant: one per (query tile, 32-row half)
 constexpr int SAMPLE = 16;          // pass 1 visits one row tile in SAMPLE
 constexpr int KMAX = 16;            // largest k the screening supports
-constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr uint32_t TMEM_COLS = 2 * QTILES * BN;  // double-buffered accumulators of both query tiles
 constexpr int MAX_KB = 4;           // len <= 256
-constexpr size_t A_BYTES = (size_t)MAX_KB * BM * 128;
+constexpr size_t A_TILE_BYTES = (size_t)MAX_KB * BM * 128;
+constexpr size_t A_BYTES = QTILES * A_TILE_BYTES;
 constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
-constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * B_STAGE_BYTES + 256;
+constexpr size_t NORM_STAGE_BYTES = (size_t)BN * 8 + 16;  // (|x|^2, |x|) of a row tile, then its range
+constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * (B_STAGE_BYTES + NORM_STAGE_BYTES) + 256;
+static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
 constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
 
 struct DenseParams {
@@ -51,6 +65,7 @@ struct DenseParams {
   int qtile, nd;         // nd < 0: the count of screened queries is read from nd_dev
   const int* nd_dev;
   const float2* xnorm;  // [n]: (|x|^2, |x|)
+  const float4* xtile;  // [row tiles]: (min |x|^2, max |x|^2, max |x|, 0) of the tile's rows
   const float2* qnorm;  // [nd_pad]
   const int* qslot;     // [nd]: chunk-local slot of dense query d
   int64_t q0;           // thresholds of slot j live at thr[q0 + j]
@@ -100,6 +115,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if (globaltimer() > deadline) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"((uint64_t)src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -156,20 +177,24 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   // a launch for a query tile past the screened queries has nothing to do (uniform per grid)
   const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
   if (P.qtile * BM >= nd) return;
+  const int nq_tiles = (P.qtile + 1) * BM < nd ? 2 : 1;  // query tiles of this launch that hold queries
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* smA = base;
   uint8_t* smB = base + A_BYTES;
-  uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
-  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full
-  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+  const uint8_t* smN = smB + STAGES * B_STAGE_BYTES;
+  uint64_t* bars = (uint64_t*)(smB + STAGES * (B_STAGE_BYTES + NORM_STAGE_BYTES));
+  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full | norms_empty[STAGES]
+  uint32_t* tmem_holder = (uint32_t*)(bars + 3 * STAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + STAGES), b_accf = smem_u32(bars + 2 * STAGES),
-                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4);
+                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4),
+                 b_nempty = smem_u32(bars + 2 * STAGES + 5);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_full + 8 * s, 1);
       mbar_init(b_empty + 8 * s, 1);
+      mbar_init(b_nempty + 8 * s, EPI_WARPS);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(b_accf + 8 * a, 1);
@@ -198,21 +223,27 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer
-      mbar_expect_tx(b_afull, (uint32_t)(nkb * BM * 128));
-      for (int kb = 0; kb < nkb; ++kb)
-        tma_load_2d(smem_u32(smA + (size_t)kb * BM * 128), &tmA, kb * BKE, P.qtile * BM, b_afull);
+      mbar_expect_tx(b_afull, (uint32_t)(nq_tiles * nkb * BM * 128));
+      for (int qt = 0; qt < nq_tiles; ++qt)
+        for (int kb = 0; kb < nkb; ++kb)
+          tma_load_2d(smem_u32(smA + qt * A_TILE_BYTES + (size_t)kb * BM * 128), &tmA, kb * BKE,
+                      (P.qtile + qt) * BM, b_afull);
       int i = 0;
       for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
+        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline) ||
+            !mbar_wait(b_nempty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
           *abort_flag = 1;
           break;
         }
-        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128));
+        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128 + NORM_STAGE_BYTES));
         for (int kb = 0; kb < nkb; ++kb)
           tma_load_2d(smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128), &tmB, kb * BKE,
                       (int)(t * BN), b_full + 8 * s);
+        // the norm array is padded to whole row tiles, so the copy stays inside it
+        bulk_load(smem_u32(smN + (size_t)s * NORM_STAGE_BYTES), P.xnorm + t * BN, (uint32_t)(BN * 8), b_full + 8 * s);
+        bulk_load(smem_u32(smN + (size_t)s * NORM_STAGE_BYTES + BN * 8), P.xtile + t, 16u, b_full + 8 * s);
       }
       // drain: the last loads must land before the CTA may exit
       const int issued = i;
@@ -236,14 +267,16 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * BN);
-        for (int kb = 0; kb < nkb; ++kb) {
-          const uint32_t a0 = smem_u32(smA + (size_t)kb * BM * 128);
-          const uint32_t b0 = smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128);
+        for (int qt = 0; qt < nq_tiles; ++qt) {
+          const uint32_t d_tmem = tmem_base + (uint32_t)((ab * QTILES + qt) * BN);
+          for (int kb = 0; kb < nkb; ++kb) {
+            const uint32_t a0 = smem_u32(smA + qt * A_TILE_BYTES + (size_t)kb * BM * 128);
+            const uint32_t b0 = smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)  // 16 BF16 = 32 bytes per MMA step along K
-            umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
-                      (kb | ks) ? 1u : 0u);
+            for (int ks = 0; ks < 4; ++ks)  // 16 BF16 = 32 bytes per MMA step along K
+              umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
+                        (kb | ks) ? 1u : 0u);
+          }
         }
         umma_commit(b_empty + 8 * s);
         umma_commit(b_accf + 8 * ab);
@@ -253,11 +286,13 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       if (i > 0) mbar_wait(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag,
                            deadline + 100000000ull);
     }
-  } else {  // ---- epilogue: warps 2..9, TMEM lane quadrant = warp % 4, column half = (warp - 2) / 4
+  } else {  // ---- epilogue: warps 2..17, TMEM lane quadrant = warp % 4
     const int qd = warp & 3;
-    const int c = (warp - 2) >> 2;
+    const int c = ((warp - 2) >> 2) & 1;  // query tile
+    const int h = (warp - 2) >> 3;        // 32-row half of each row tile
+    const bool tile_on = c < nq_tiles;  // warp-uniform: this warp's query tile holds queries
     const int m = qd * 32 + lane;
-    const int d = P.qtile * BM + m;
+    const int d = (P.qtile + c) * BM + m;
     const bool valid = d < nd;
     float qn = 0.f, qrt = 0.f, thr_q = 0.f;
     int slot = 0;
@@ -275,57 +310,48 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) best[j] = CUDART_INF_F;
     float kth = CUDART_INF_F;
-    // row norms of this warp's half of a tile: lane l holds row 32c + l, prefetched one tile
-    // ahead and broadcast with shuffles
-    auto load_norms = [&](int64_t t) {
-      const int64_t row = t * BN + c * 32 + lane;
-      return (t < ntiles && row < P.n) ? P.xnorm[row] : make_float2(0.f, 0.f);
-    };
-    float2 xnext = load_norms(tfirst);
     int i = 0;
     for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
-      const float2 xcur = xnext;
-      xnext = load_norms(t + tstride);
+      const int s = i % STAGES;
+      const uint32_t ph = (uint32_t)((i / STAGES) & 1);
       const int ab = i & 1;
       const uint32_t aph = (uint32_t)((i >> 1) & 1);
-      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
+      // the stage's norms cannot be overwritten before this warp releases them, so the wait on
+      // its (already completed) load phase is exact; it makes the bulk copy's data visible
+      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline) ||
+          !mbar_wait(b_full + 8 * s, ph, abort_flag, deadline)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      {
+      if (tile_on) {
+        const float2* nrm = (const float2*)(smN + (size_t)s * NORM_STAGE_BYTES) + h * 32;
+        const float4 rng = *(const float4*)(smN + (size_t)s * NORM_STAGE_BYTES + BN * 8);  // broadcast
+        // largest margin over the tile's rows, rounded up
+        const float Mmax = __fmaf_ru(c1q, rng.z, __fmul_ru(P.c2, __fadd_ru(qn, rng.y)));
         uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * BN + c * 32), v);
-        const int64_t row0 = t * BN + c * 32;
+        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)((ab * QTILES + c) * BN + h * 32), v);
+        const int64_t row0 = t * BN + h * 32;
         const int64_t left = P.n - row0;
         const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);  // rows of this chunk inside the series
-        // common path, unrolled: the per-pair interval end and a mask of the pairs that need work
-        float val[32];
-        uint32_t hit = 0u;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const float xn = __shfl_sync(PARIS_FULL_MASK, xcur.x, jj);
-          const float xrt = __shfl_sync(PARIS_FULL_MASK, xcur.y, jj);
-          const float d2 = fmaf(-2.0f, __uint_as_float(v[jj]), qn + xn);
-          const float M = __fmaf_ru(c1q, xrt, __fmul_ru(P.c2, __fadd_ru(qn, xn)));
-          if (PHASE == 1) {
-            val[jj] = __fadd_ru(d2, M);  // upper end: the exact squared distance is below it
-            hit |= (val[jj] < kth ? 1u : 0u) << jj;
-          } else {
-            val[jj] = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
-            hit |= (val[jj] <= thr_q ? 1u : 0u) << jj;
-          }
-        }
         const uint32_t row_mask = nrow >= 32 ? 0xffffffffu : (nrow <= 0 ? 0u : ((1u << nrow) - 1u));
-        hit = valid ? (hit & row_mask) : 0u;
-        // rare path, not unrolled: insert into the top-k (pass 1) or emit a candidate (pass 2)
-        while (hit) {
-          const int jj = __ffs(hit) - 1;
-          hit &= hit - 1u;
-          float x = 0.f;
+        uint32_t hit = 0u;
+        if (PHASE == 1) {
+          // upper ends from the tile's norm range: ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max))
+          const float Cq = __fadd_ru(qn, Mmax);
+          float val[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) x = (j == jj) ? val[j] : x;
-          if (PHASE == 1) {
+          for (int jj = 0; jj < 32; ++jj) {
+            val[jj] = __fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(v[jj]), rng.y), Cq);
+            hit |= (val[jj] < kth ? 1u : 0u) << jj;
+          }
+          hit = valid ? (hit & row_mask) : 0u;
+          while (hit) {  // rare: insert into the top-k
+            const int jj = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            float x = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x = (j == jj) ? val[j] : x;
             if (x < kth) {
 #pragma unroll
               for (int j = 0; j < KMAX; ++j) {
@@ -339,20 +365,42 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
               for (int j = 0; j < KMAX; ++j)
                 if (j == P.k - 1) kth = best[j];
             }
-          } else {
-            const uint32_t p = atomicAdd(P.count + slot, 1u);
-            if ((int64_t)p < P.cap) {
-              P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
-              P.lb[(int64_t)slot * P.cap + p] = x;
-            } else {
-              atomicOr(P.overflow, DEV_CAND_OVERFLOW);
+          }
+        } else {
+          // drop unless rd(xn_min - 2 dot) <= ru(thr + M_max - |q|^2)
+          const float R = __fsub_ru(__fadd_ru(thr_q, Mmax), qn);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
+          hit = valid ? (hit & row_mask) : 0u;
+          while (hit) {  // rare: the row's own interval, then emit
+            const int jj = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            uint32_t dv = 0u;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dv = (j == jj) ? v[j] : dv;
+            const float2 xx = nrm[jj];
+            const float d2 = fmaf(-2.0f, __uint_as_float(dv), qn + xx.x);
+            const float M = __fmaf_ru(c1q, xx.y, __fmul_ru(P.c2, __fadd_ru(qn, xx.x)));
+            const float x = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
+            if (x <= thr_q) {
+              const uint32_t p = atomicAdd(P.count + slot, 1u);
+              if ((int64_t)p < P.cap) {
+                P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
+                P.lb[(int64_t)slot * P.cap + p] = x;
+              } else {
+                atomicOr(P.overflow, DEV_CAND_OVERFLOW);
+              }
             }
           }
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+      if (lane == 0) {
+        mbar_arrive(b_acce + 8 * ab);
+        mbar_arrive(b_nempty + 8 * s);
+      }
     }
     if (PHASE == 1 && valid && kth < CUDART_INF_F) atomicMin(thr_ptr, __float_as_uint(__fmul_ru(kth, P.cg)));
   }
@@ -475,29 +523,74 @@ void dense_margins(int len, float* c1, float* c2) {
   *c2 = std::nextafter((float)(b * (1.0 + std::ldexp(1.0, -10))), INFINITY);
 }
 
+// Norm range of each 64-row tile over its rows inside the series; one warp per tile.
+__global__ void tile_range_kernel(const float2* __restrict__ nm, int64_t n, float4* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tiles = (n + BN - 1) / BN;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += warps) {
+    float lo = CUDART_INF_F, hi = -CUDART_INF_F, rt = -CUDART_INF_F;
+    for (int j = lane; j < BN; j += 32) {
+      const int64_t r = t * BN + j;
+      if (r < n) {
+        const float2 v = nm[r];
+        lo = fminf(lo, v.x);
+        hi = fmaxf(hi, v.x);
+        rt = fmaxf(rt, v.y);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(PARIS_FULL_MASK, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(PARIS_FULL_MASK, hi, o));
+      rt = fmaxf(rt, __shfl_xor_sync(PARIS_FULL_MASK, rt, o));
+    }
+    if (lane == 0) out[t] = make_float4(lo, hi, rt, 0.f);
+  }
+}
+
+// Row norms are stored for whole row tiles, so a tile's norms are one bulk copy.
+size_t norm_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN * BN) * sizeof(float2); }
+size_t range_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN) * sizeof(float4); }
+
 paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
   std::lock_guard<std::mutex> lock(g_shadow_mutex);
   if (idx->shadow) return PARIS_OK;
   const size_t bytes = (size_t)idx->n * idx->len * 2;
   void* sh = dev_alloc(bytes, st);
-  float2* nm = (float2*)dev_alloc((size_t)idx->n * sizeof(float2), st);
+  float2* nm = (float2*)dev_alloc(norm_bytes(idx->n), st);
   if (!sh || !nm) {
     dev_free(sh, bytes, st);
-    dev_free(nm, (size_t)idx->n * sizeof(float2), st);
+    dev_free(nm, norm_bytes(idx->n), st);
     return fail(PARIS_ENOMEM, "BF16 shadow of the series (%zu bytes)", bytes);
   }
   int grid = sm_count_dense() * 8;
   shadow_kernel<<<grid, 256, 0, st>>>(idx->series, idx->n, idx->len, (__nv_bfloat16*)sh, nm, nullptr, 0, idx->n);
+  note_launches(1);
+  // norms of the rows past the series in the last row tile: zero
+  PARIS_CUDA(cudaMemsetAsync(nm + idx->n, 0, norm_bytes(idx->n) - (size_t)idx->n * sizeof(float2), st));
+  const size_t rbytes = range_bytes(idx->n);
+  float4* rng = (float4*)dev_alloc(rbytes, st);
+  if (!rng) {
+    dev_free(sh, bytes, st);
+    dev_free(nm, norm_bytes(idx->n), st);
+    return fail(PARIS_ENOMEM, "row tile norm ranges");
+  }
+  tile_range_kernel<<<grid, 256, 0, st>>>(nm, idx->n, rng);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   CUtensorMap* map = new CUtensorMap;
   paris_status s = make_bf16_map(map, sh, idx->n, idx->len, BN);
   if (s != PARIS_OK) {
     delete map;
+    dev_free(sh, bytes, st);
+    dev_free(nm, norm_bytes(idx->n), st);
+    dev_free(rng, rbytes, st);
     return s;
   }
   idx->shadow = sh;
   idx->xnorm = nm;
+  idx->xtile = rng;
   idx->shadow_map = map;
   return PARIS_OK;
 }
@@ -521,7 +614,9 @@ paris_status tighten_overflowed(const QueryState& qs, const ChunkState& cs, int*
 
 void release_shadow(paris_index* idx) {
   if (idx->shadow) dev_free(idx->shadow, (size_t)idx->n * idx->len * 2, nullptr);
-  if (idx->xnorm) dev_free(idx->xnorm, (size_t)idx->n * sizeof(float2), nullptr);
+  if (idx->xnorm) dev_free(idx->xnorm, norm_bytes(idx->n), nullptr);
+  if (idx->xtile) dev_free(idx->xtile, range_bytes(idx->n), nullptr);
+  idx->xtile = nullptr;
   delete (CUtensorMap*)idx->shadow_map;
   idx->shadow = nullptr;
   idx->xnorm = nullptr;
@@ -573,6 +668,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   P.nd = nd;
   P.nd_dev = ndev;
   P.xnorm = idx->xnorm;
+  P.xtile = (const float4*)idx->xtile;
   P.qnorm = cs.dqnm;
   P.qslot = slots;
   P.q0 = cs.q0;
@@ -590,7 +686,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   const int grid = (int)std::min<int64_t>(ntiles, sm_count_dense());
   const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;
   for (int phase = 1; phase <= 2; ++phase) {
-    for (int t = 0; t < (int)tiles; ++t) {
+    for (int t = 0; t < (int)tiles; t += QTILES) {
       P.qtile = t;
       if (phase == 1)
         dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);

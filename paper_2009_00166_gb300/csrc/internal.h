@@ -24,7 +24,8 @@ struct paris_index {
   std::vector<double> beta_host;
   // BF16 shadow of the series and fp32 row norms for the mixed-precision path (made on first use)
   void* shadow = nullptr;       // device [n][len] bf16
-  float2* xnorm = nullptr;      // device [n]: (|x|^2, |x|) in fp32
+  float2* xnorm = nullptr;      // device [n rounded up to 64]: (|x|^2, |x|) in fp32, zero past n
+  void* xtile = nullptr;        // device float4 per 64-row tile: (min |x|^2, max |x|^2, max |x|, 0)
   void* shadow_map = nullptr;   // host copy of the TMA descriptor of the shadow (CUtensorMap)
   // learned approximate-search proposal (borrowed; see paris_attach_seed_model)
   const paris_seed_model* seed_model = nullptr;
