@@ -18,13 +18,13 @@
 // ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max), which still bound the distance from above.
 //
 // Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries; warp 0 streams
-// 64-row tiles of the BF16 shadow of the series, with the rows' fp32 norms, into a 3-stage
-// shared-memory ring with TMA (128-byte swizzle; the norms by a bulk copy), warp 1 issues the
-// tensor-core MMAs (one thread) of both query tiles against each row tile into double-buffered
-// TMEM accumulators (2 x 2 x 128 x 64 fp32), and warps 2-17 read the accumulators back
-// (tcgen05.ld) and run the screening epilogue: one query per thread and 32 rows of the tile per
-// warp. A stage is refilled once the MMAs have read it and the epilogue has read its norms.
-// Each row tile read from HBM serves 256 queries.
+// 64-row tiles of the BF16 shadow of the series into a 3-stage shared-memory ring with TMA
+// (128-byte swizzle), warp 1 issues the tensor-core MMAs (one thread) of both query tiles
+// against each row tile into double-buffered TMEM accumulators (2 x 2 x 128 x 64 fp32), and
+// warps 2-17 read the accumulators back (tcgen05.ld) and run the screening epilogue: one query
+// per thread and 32 rows of the tile per warp. The epilogue reads each tile's norm range from
+// global memory one tile ahead, and a row's own norms only for the rare pairs that pass the
+// range test. Each row tile read from HBM serves 256 queries.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -54,8 +54,7 @@ constexpr int MAX_KB = 4;           // len <= 256
 constexpr size_t A_TILE_BYTES = (size_t)MAX_KB * BM * 128;
 constexpr size_t A_BYTES = QTILES * A_TILE_BYTES;
 constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
-constexpr size_t NORM_STAGE_BYTES = (size_t)BN * 8 + 16;  // (|x|^2, |x|) of a row tile, then its range
-constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * (B_STAGE_BYTES + NORM_STAGE_BYTES) + 256;
+constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * B_STAGE_BYTES + 256;
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
 constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
 
@@ -117,12 +116,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return true;
 }
 
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"((uint64_t)src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
@@ -181,20 +174,17 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* smA = base;
   uint8_t* smB = base + A_BYTES;
-  const uint8_t* smN = smB + STAGES * B_STAGE_BYTES;
-  uint64_t* bars = (uint64_t*)(smB + STAGES * (B_STAGE_BYTES + NORM_STAGE_BYTES));
-  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full | norms_empty[STAGES]
-  uint32_t* tmem_holder = (uint32_t*)(bars + 3 * STAGES + 5);
+  uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
+  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + STAGES), b_accf = smem_u32(bars + 2 * STAGES),
-                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4),
-                 b_nempty = smem_u32(bars + 2 * STAGES + 5);
+                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_full + 8 * s, 1);
       mbar_init(b_empty + 8 * s, 1);
-      mbar_init(b_nempty + 8 * s, EPI_WARPS);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(b_accf + 8 * a, 1);
@@ -232,18 +222,14 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline) ||
-            !mbar_wait(b_nempty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
+        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
           *abort_flag = 1;
           break;
         }
-        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128 + NORM_STAGE_BYTES));
+        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128));
         for (int kb = 0; kb < nkb; ++kb)
           tma_load_2d(smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128), &tmB, kb * BKE,
                       (int)(t * BN), b_full + 8 * s);
-        // the norm array is padded to whole row tiles, so the copy stays inside it
-        bulk_load(smem_u32(smN + (size_t)s * NORM_STAGE_BYTES), P.xnorm + t * BN, (uint32_t)(BN * 8), b_full + 8 * s);
-        bulk_load(smem_u32(smN + (size_t)s * NORM_STAGE_BYTES + BN * 8), P.xtile + t, 16u, b_full + 8 * s);
       }
       // drain: the last loads must land before the CTA may exit
       const int issued = i;
@@ -310,23 +296,22 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) best[j] = CUDART_INF_F;
     float kth = CUDART_INF_F;
+    // norm range of the row tiles, loaded two tiles ahead (one address per warp)
+    auto load_range = [&](int64_t t) { return t < ntiles ? P.xtile[t] : make_float4(0.f, 0.f, 0.f, 0.f); };
+    float4 rng1 = load_range(tfirst), rng2 = load_range(tfirst + tstride);
     int i = 0;
     for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
-      const int s = i % STAGES;
-      const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+      const float4 rng = rng1;
+      rng1 = rng2;
+      rng2 = load_range(t + 2 * tstride);
       const int ab = i & 1;
       const uint32_t aph = (uint32_t)((i >> 1) & 1);
-      // the stage's norms cannot be overwritten before this warp releases them, so the wait on
-      // its (already completed) load phase is exact; it makes the bulk copy's data visible
-      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline) ||
-          !mbar_wait(b_full + 8 * s, ph, abort_flag, deadline)) {
+      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
       if (tile_on) {
-        const float2* nrm = (const float2*)(smN + (size_t)s * NORM_STAGE_BYTES) + h * 32;
-        const float4 rng = *(const float4*)(smN + (size_t)s * NORM_STAGE_BYTES + BN * 8);  // broadcast
         // largest margin over the tile's rows, rounded up
         const float Mmax = __fmaf_ru(c1q, rng.z, __fmul_ru(P.c2, __fadd_ru(qn, rng.y)));
         uint32_t v[32];
@@ -379,7 +364,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
             uint32_t dv = 0u;
 #pragma unroll
             for (int j = 0; j < 32; ++j) dv = (j == jj) ? v[j] : dv;
-            const float2 xx = nrm[jj];
+            const float2 xx = P.xnorm[row0 + jj];
             const float d2 = fmaf(-2.0f, __uint_as_float(dv), qn + xx.x);
             const float M = __fmaf_ru(c1q, xx.y, __fmul_ru(P.c2, __fadd_ru(qn, xx.x)));
             const float x = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
@@ -397,10 +382,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(b_acce + 8 * ab);
-        mbar_arrive(b_nempty + 8 * s);
-      }
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
     }
     if (PHASE == 1 && valid && kth < CUDART_INF_F) atomicMin(thr_ptr, __float_as_uint(__fmul_ru(kth, P.cg)));
   }
