@@ -267,7 +267,7 @@ def main():
         """Build, then answer every query: one call for the whole batch, or one per sigma group."""
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        idx = P.paris_build(X, 16, 256)
+        idx = P.paris_build_ex(X, 16, 256, bf16_shadow=prec == P.PARIS_REFINE_MIXED)
         e1.record(stream)
         if sd == P.PARIS_SEED_LEARNED:
             P.paris_attach_seed_model(idx, model, 3)
@@ -354,7 +354,7 @@ def main():
     # ---- the same batch as a captured plan (one CUDA graph per batch) on an index built once:
     # queries only, replays after the eager first run
     if args.graph_steps > 0:
-        idx = P.paris_build(X, 16, 256)
+        idx = P.paris_build_ex(X, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
         plan = P.KnnPlan(idx, nq, k, mode=mode, precision=precision)
         ref_i = P.paris_exact_knn_ex(idx, Q, k, mode=mode, precision=precision)[0]
         gi, _ = plan.run(Q)                                           # eager, then recorded
@@ -389,7 +389,8 @@ def main():
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            idx = P.paris_build(host, 16, 256)                      # host series: copied in by the library
+            # host series: copied in by the library
+            idx = P.paris_build_ex(host, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
             if seed_mode == P.PARIS_SEED_LEARNED:
                 P.paris_attach_seed_model(idx, model, 3)
             for i in range(len(SIGMAS)):

@@ -60,7 +60,11 @@ paris_status paris_build(const float* series, int64_t n, int32_t len, int32_t w,
 
 typedef struct paris_build_opts {
   int32_t leaf_capacity; /* L: rows per approximate-search leaf; 0 = 2048; max 4096 */
-  int32_t reserved[7];   /* must be zero */
+  int32_t bf16_shadow;   /* 1: the encode pass also writes the BF16 copy of the series and the
+                            row norms that PARIS_REFINE_MIXED screens with (otherwise they are
+                            built by the first MIXED query); no effect for shapes the screening
+                            does not support (len not a multiple of 64 or above 256) */
+  int32_t reserved[6];   /* must be zero */
 } paris_build_opts;
 
 /* paris_build with options (opts may be NULL = defaults). */

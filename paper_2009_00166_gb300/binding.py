@@ -29,7 +29,7 @@ class ParisError(RuntimeError):
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("leaf_capacity", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("leaf_capacity", C.c_int32), ("bf16_shadow", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class QueryOpts(C.Structure):
@@ -180,17 +180,18 @@ class ParisIndex:
             pass
 
 
-def paris_build_ex(series, w: int = 16, card: int = 256, leaf_capacity: int = 0, stream=None) -> ParisIndex:
+def paris_build_ex(series, w: int = 16, card: int = 256, leaf_capacity: int = 0, bf16_shadow: bool = False,
+                   stream=None) -> ParisIndex:
     """paris_build_ex: series is a contiguous [n][len] float32 tensor (device: borrowed; host: copied)."""
     n, length = int(series.shape[0]), int(series.shape[1])
-    opts = BuildOpts(leaf_capacity=leaf_capacity)
+    opts = BuildOpts(leaf_capacity=leaf_capacity, bf16_shadow=1 if bf16_shadow else 0)
     out = C.c_void_p()
     _check(lib().paris_build_ex(_ptr(series), n, length, w, card, C.byref(opts), _stream(stream), C.byref(out)))
     return ParisIndex(out.value, n, length, w, card, series)
 
 
 def paris_build(series, w: int = 16, card: int = 256, stream=None) -> ParisIndex:
-    return paris_build_ex(series, w, card, 0, stream)
+    return paris_build_ex(series, w, card, 0, False, stream)
 
 
 def paris_free(index: ParisIndex):

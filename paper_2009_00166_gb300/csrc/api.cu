@@ -361,9 +361,11 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   PARIS_TRY(check_shape(n, len, w, card));
   int leaf = opts && opts->leaf_capacity ? opts->leaf_capacity : 2048;
   if (leaf < 1 || leaf > kMaxLeaf) return fail(PARIS_EINVAL, "leaf_capacity must be in [1, %d]", kMaxLeaf);
-  if (opts)
-    for (int i = 0; i < 7; ++i)
+  if (opts) {
+    for (int i = 0; i < 6; ++i)
       if (opts->reserved[i]) return fail(PARIS_EINVAL, "paris_build_opts.reserved must be zero");
+    if (opts->bf16_shadow != 0 && opts->bf16_shadow != 1) return fail(PARIS_EINVAL, "bf16_shadow must be 0 or 1");
+  }
   cudaStream_t st = (cudaStream_t)stream;
   paris_index* idx = new (std::nothrow) paris_index();
   if (!idx) return fail(PARIS_ENOMEM, "index object");
@@ -400,9 +402,20 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     return bail(fail(PARIS_ENOMEM, "index arrays for %lld series", (long long)n));
   if (cudaMemsetAsync(status.p, 0, 4, st) != cudaSuccess) return bail(fail(PARIS_ECUDA, "memset"));
   RowShape sh = make_row_shape(len, w, idx->series);
+  // the mixed-precision screening's inputs, written by the same pass when asked for
+  ShadowBufs shb;
+  const bool fused = opts && opts->bf16_shadow && dense_shape_ok(len) && sh.fast && sh.s <= 16;
+  if (fused) {
+    s = alloc_shadow(idx, &shb, st);
+    if (s != PARIS_OK) return bail(s);
+  }
   s = launch_encode(idx->series, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr, idx->keys_sorted,
-                    nullptr, status.as<uint32_t>(), st);
-  if (s != PARIS_OK) return bail(s);
+                    nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm);
+  if (s == PARIS_OK && fused) s = finish_shadow(idx, &shb, st);
+  if (s != PARIS_OK) {
+    free_shadow_bufs(idx, &shb, st);
+    return bail(s);
+  }
   s = radix_sort_index(idx->keys_sorted, idx->rows_sorted, n, st);
   if (s != PARIS_OK) return bail(s);
   s = check_status_word(status.as<uint32_t>(), st, "paris_build");

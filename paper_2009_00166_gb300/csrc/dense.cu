@@ -535,46 +535,59 @@ __global__ void tile_range_kernel(const float2* __restrict__ nm, int64_t n, floa
 size_t norm_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN * BN) * sizeof(float2); }
 size_t range_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN) * sizeof(float4); }
 
-paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
-  std::lock_guard<std::mutex> lock(g_shadow_mutex);
-  if (idx->shadow) return PARIS_OK;
+bool dense_shape_ok(int len) { return len % BKE == 0 && len <= MAX_KB * BKE; }
+
+paris_status alloc_shadow(const paris_index* idx, ShadowBufs* out, cudaStream_t st) {
+  *out = ShadowBufs{};
   const size_t bytes = (size_t)idx->n * idx->len * 2;
-  void* sh = dev_alloc(bytes, st);
-  float2* nm = (float2*)dev_alloc(norm_bytes(idx->n), st);
-  if (!sh || !nm) {
-    dev_free(sh, bytes, st);
-    dev_free(nm, norm_bytes(idx->n), st);
+  out->shadow = dev_alloc(bytes, st);
+  out->xnorm = (float2*)dev_alloc(norm_bytes(idx->n), st);
+  out->xtile = (float4*)dev_alloc(range_bytes(idx->n), st);
+  if (!out->shadow || !out->xnorm || !out->xtile) {
+    free_shadow_bufs(idx, out, st);
     return fail(PARIS_ENOMEM, "BF16 shadow of the series (%zu bytes)", bytes);
   }
-  int grid = sm_count_dense() * 8;
-  shadow_kernel<<<grid, 256, 0, st>>>(idx->series, idx->n, idx->len, (__nv_bfloat16*)sh, nm, nullptr, 0, idx->n);
-  note_launches(1);
-  // norms of the rows past the series in the last row tile: zero
-  PARIS_CUDA(cudaMemsetAsync(nm + idx->n, 0, norm_bytes(idx->n) - (size_t)idx->n * sizeof(float2), st));
-  const size_t rbytes = range_bytes(idx->n);
-  float4* rng = (float4*)dev_alloc(rbytes, st);
-  if (!rng) {
-    dev_free(sh, bytes, st);
-    dev_free(nm, norm_bytes(idx->n), st);
-    return fail(PARIS_ENOMEM, "row tile norm ranges");
-  }
-  tile_range_kernel<<<grid, 256, 0, st>>>(nm, idx->n, rng);
+  return PARIS_OK;
+}
+
+void free_shadow_bufs(const paris_index* idx, ShadowBufs* b, cudaStream_t st) {
+  dev_free(b->shadow, (size_t)idx->n * idx->len * 2, st);
+  dev_free(b->xnorm, norm_bytes(idx->n), st);
+  dev_free(b->xtile, range_bytes(idx->n), st);
+  *b = ShadowBufs{};
+}
+
+// Once the shadow rows and norms are written: zero norms past the series, tile norm ranges,
+// the TMA descriptor; the index takes ownership.
+paris_status finish_shadow(paris_index* idx, ShadowBufs* b, cudaStream_t st) {
+  PARIS_CUDA(cudaMemsetAsync(b->xnorm + idx->n, 0, norm_bytes(idx->n) - (size_t)idx->n * sizeof(float2), st));
+  tile_range_kernel<<<sm_count_dense() * 8, 256, 0, st>>>(b->xnorm, idx->n, b->xtile);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   CUtensorMap* map = new CUtensorMap;
-  paris_status s = make_bf16_map(map, sh, idx->n, idx->len, BN);
+  paris_status s = make_bf16_map(map, b->shadow, idx->n, idx->len, BN);
   if (s != PARIS_OK) {
     delete map;
-    dev_free(sh, bytes, st);
-    dev_free(nm, norm_bytes(idx->n), st);
-    dev_free(rng, rbytes, st);
+    free_shadow_bufs(idx, b, st);
     return s;
   }
-  idx->shadow = sh;
-  idx->xnorm = nm;
-  idx->xtile = rng;
+  idx->shadow = b->shadow;
+  idx->xnorm = b->xnorm;
+  idx->xtile = b->xtile;
   idx->shadow_map = map;
+  *b = ShadowBufs{};
   return PARIS_OK;
+}
+
+paris_status ensure_shadow(paris_index* idx, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_shadow_mutex);
+  if (idx->shadow) return PARIS_OK;
+  ShadowBufs b;
+  PARIS_TRY(alloc_shadow(idx, &b, st));
+  shadow_kernel<<<sm_count_dense() * 8, 256, 0, st>>>(idx->series, idx->n, idx->len, (__nv_bfloat16*)b.shadow,
+                                                       b.xnorm, nullptr, 0, idx->n);
+  note_launches(1);
+  return finish_shadow(idx, &b, st);
 }
 
 paris_status launch_tighten(const QueryState& qs, const ChunkState& cs, cudaStream_t st) {

@@ -1,5 +1,7 @@
 // Index build, step 1: exact PAA -> iSAX symbols -> summary slot + interleaved key, one warp
 // per series (Sec. 2.2; Alg. 2 ConvertToSAX and SAX[position] store).
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace paris {
@@ -14,7 +16,7 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     const float* __restrict__ series, int64_t n, RowShape sh, int card, int bits,
     const uint64_t* __restrict__ beta_keys_g, uint8_t* __restrict__ sax_rot,
     uint8_t* __restrict__ sax_plain, uint64_t* __restrict__ key64, double* __restrict__ paa_out,
-    uint32_t* __restrict__ status) {
+    uint32_t* __restrict__ status, __nv_bfloat16* __restrict__ shadow, float2* __restrict__ xnorm) {
   __shared__ uint64_t beta_keys[255];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
   __syncthreads();
@@ -36,6 +38,29 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     // rotated summary slot: slot j holds segment (j + r) mod 16 (0 when that segment >= w)
     const int src = (seg + (int)(r & 15)) & 15;
     const int b = __shfl_sync(PARIS_FULL_MASK, sym, (half << 4) | src);
+    if (SEGV <= 4 && shadow) {
+      // BF16 copy of the lane's segment and the row's fp32 squared norm (the mixed-precision
+      // screening's inputs), from the values this warp has just read
+      const bool act = rv && seg < sh.w;
+      const float4* p = reinterpret_cast<const float4*>(series + r * (int64_t)sh.len + (act ? seg * sh.s : 0));
+      float acc = 0.f;
+#pragma unroll
+      for (int v = 0; v < (SEGV <= 4 ? SEGV : 1); ++v) {
+        const float4 x = act ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        acc = fmaf(x.x, x.x, acc);
+        acc = fmaf(x.y, x.y, acc);
+        acc = fmaf(x.z, x.z, acc);
+        acc = fmaf(x.w, x.w, acc);
+        if (act) {
+          __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+          uint2 pk = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+          *reinterpret_cast<uint2*>(shadow + r * (int64_t)sh.len + seg * sh.s + 4 * v) = pk;
+        }
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(PARIS_FULL_MASK, acc, o);  // within the half
+      if (rv && seg == 0) xnorm[r] = make_float2(acc, __fsqrt_ru(acc));
+    }
     if (rv) {
       sax_rot[r * PARIS_SAX_BYTES + seg] = (uint8_t)(src < sh.w ? b : 0);
       if (sax_plain && seg < sh.w) sax_plain[r * sh.w + seg] = (uint8_t)sym;
@@ -80,13 +105,16 @@ RowShape make_row_shape(int len, int w, const void* base_ptr) {
 
 paris_status launch_encode(const float* series, int64_t n, const RowShape& sh, int card, int bits,
                            const uint64_t* beta_keys, uint8_t* sax_rot, uint8_t* sax_plain,
-                           uint64_t* key64, double* paa, uint32_t* status, cudaStream_t st) {
+                           uint64_t* key64, double* paa, uint32_t* status, cudaStream_t st, void* shadow,
+                           float2* xnorm) {
   if (n <= 0) return PARIS_OK;
+  if (shadow && !(sh.fast && sh.s / 4 <= 4)) return fail(PARIS_EINVAL, "BF16 shadow during encode needs len/w <= 16");
   int grid = encode_grid(n);
   const int segv = sh.fast ? sh.s / 4 : 1;
 #define ENC(SV)                                                                                     \
   encode_kernel<SV><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, \
-                                                     sax_plain, key64, paa, status)
+                                                     sax_plain, key64, paa, status,                \
+                                                     (__nv_bfloat16*)shadow, xnorm)
   switch (segv) {
     case 1: ENC(1); break;
     case 2: ENC(2); break;

@@ -94,6 +94,16 @@ paris_status launch_row_buckets(const paris_index* idx, const int64_t* rows, int
 bool dense_supported(const paris_index* idx, int k);
 void dense_margins(int len, float* c1, float* c2);
 paris_status ensure_shadow(paris_index* idx, cudaStream_t st);
+// The shadow's buffers, for a build that writes them during the encode pass.
+struct ShadowBufs {
+  void* shadow = nullptr;   // [n][len] BF16
+  float2* xnorm = nullptr;  // [n rounded up to 64] (|x|^2, |x|)
+  float4* xtile = nullptr;  // [row tiles] norm ranges
+};
+bool dense_shape_ok(int len);
+paris_status alloc_shadow(const paris_index* idx, ShadowBufs* out, cudaStream_t st);
+void free_shadow_bufs(const paris_index* idx, ShadowBufs* b, cudaStream_t st);
+paris_status finish_shadow(paris_index* idx, ShadowBufs* b, cudaStream_t st);
 void release_shadow(paris_index* idx);
 paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkState& cs, uint32_t* overflow, int* nd_out,
                           cudaStream_t st);

@@ -66,3 +66,26 @@ def test_mixed_falls_back_when_unsupported():
     assert st["dense_queries"] == 0
     assert np.array_equal(gi, oknn.knn(x, q, 2)[0])
     idx.free()
+
+
+@pytest.mark.parametrize("length", [64, 128, 256])
+def test_shadow_written_by_encode_pass(length):
+    """bf16_shadow=1 builds the screening's inputs in the encode pass: same exact answers as an
+    index whose inputs are built by its first mixed-precision query."""
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    n = 150_001
+    x = rw(n, length, 17)
+    q, _, _ = synth.mixed_sigma_queries(x, n, length, 30, 0.5, 2.0, seed=8)
+    X = torch.from_numpy(x).to(dev)
+    fused = P.paris_build_ex(X, bf16_shadow=True)
+    lazy = P.paris_build_ex(X)
+    wi, wd = oknn.knn(x, q, 5)
+    for idx in (fused, lazy):
+        gi, gd, st = run(P, idx, q, 5, P.PARIS_REFINE_MIXED, mode=P.PARIS_MODE_BATCHED)
+        assert np.array_equal(gi, wi)
+        assert np.allclose(gd, wd, rtol=1e-5, atol=0)
+        assert st["dense_queries"] > 0
+    fused.free()
+    lazy.free()
