@@ -631,7 +631,7 @@ struct KnnJob {
            o_hist = take((size_t)qc * 2048 * 4), o_sel = take((size_t)qc * 8), o_cc = take((size_t)qc * 4),
            o_cr = take((size_t)qc * kContCap * 4), o_cl = take((size_t)qc * kContCap * kLimbs * 4),
            o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4),
-           o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4), o_pl = take((size_t)qc * 4),
+           o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4), o_pl = take((size_t)qc * 8), o_pm = take((size_t)qc * 4),
            o_ds = take((size_t)qc * 4), o_dn = take(8), o_no = take(8),
            o_dq = take(dense_query_rows(qc) * idx->len * 2), o_dm = take(dense_query_rows(qc) * 8);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
@@ -653,6 +653,7 @@ struct KnnJob {
     cs.bucket = (uint32_t*)(b + o_bk);
     cs.packed = (uint32_t*)(b + o_pk);
     cs.pilot = (uint32_t*)(b + o_pl);
+    cs.perm = (int*)(b + o_pm);
     cs.dslots = (int*)(b + o_ds);
     cs.dnd = (int*)(b + o_dn);
     cs.nover = (int*)(b + o_no);

@@ -18,6 +18,9 @@
 // A pilot pass over every 64th row group first counts each query's kept rows; a query whose
 // scaled count reaches 3/4 of its list capacity would overflow anyway and is handed to the
 // tensor-core screening before the scan (only when overflow is allowed, i.e. MIXED refinement).
+// The pilot's count of rows still within the threshold after 8 slots then orders the chunk's
+// queries, so that a tile gathers queries whose scans abandon alike (one loose query no longer
+// keeps eleven tight ones from abandoning).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -62,15 +65,18 @@ __device__ __forceinline__ void append_kept(bool keep, int64_t row, float lb, in
   if ((int64_t)base + __popc(mk) > cap) overflowed = true;
 }
 
-// FP16 pair tables of a chunk, packed once: word (pair p, entry e) = {T[2p][e], T[2p+1][e]}.
-__global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int64_t entries, uint32_t* __restrict__ out) {
+// FP16 pair tables of a chunk: word (pair p, entry e) = {T[a][e], T[b][e]} for the queries a, b
+// in tile slots 2p and 2p + 1 (slot j holds query perm[j], or j without a permutation).
+__global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int64_t entries, const int* __restrict__ perm,
+                                  uint32_t* __restrict__ out) {
   const int64_t npairs = (qc + 1) / 2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs * entries;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = i / entries, e = i - p * entries;
-    const int64_t qa = 2 * p, qb = qa + 1;
+    const int64_t sa = 2 * p, sb = sa + 1;
+    const int64_t qa = perm ? perm[sa] : sa, qb = sb < qc ? (perm ? perm[sb] : sb) : 0;
     const float va = qtable[qa * entries + e];
-    const float vb = qb < qc ? qtable[qb * entries + e] : 0.f;
+    const float vb = sb < qc ? qtable[qb * entries + e] : 0.f;
     out[i] = pack_half2_rd(va, vb);
   }
 }
@@ -79,8 +85,8 @@ __global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int6
 // one per half-warp) and returns the tile's FP32 thresholds in s_thr (-1: nothing kept).
 template <int NP>
 __device__ __forceinline__ void load_tile(const uint32_t* __restrict__ packed, int64_t entries, int qb, int qc,
-                                          const uint32_t* __restrict__ thr, int64_t q0, const bool* active,
-                                          uint32_t* s_tab, float* s_thr) {
+                                          const uint32_t* __restrict__ thr, int64_t q0, const int* __restrict__ perm,
+                                          const bool* active, uint32_t* s_tab, float* s_thr) {
   constexpr int QT = 2 * NP;
   const int npairs_chunk = (qc + 1) / 2;
   for (int64_t e4 = threadIdx.x; e4 < entries * NP / 4; e4 += blockDim.x) {  // 4 entries per thread step
@@ -97,7 +103,7 @@ __device__ __forceinline__ void load_tile(const uint32_t* __restrict__ packed, i
   }
   if (threadIdx.x < QT) {
     const int q = qb + threadIdx.x;
-    s_thr[threadIdx.x] = (q < qc && active[threadIdx.x]) ? __uint_as_float(thr[q0 + q]) : -1.0f;
+    s_thr[threadIdx.x] = (q < qc && active[threadIdx.x]) ? __uint_as_float(thr[q0 + (perm ? perm[q] : q)]) : -1.0f;
   }
 }
 
@@ -197,7 +203,8 @@ struct ScanColl {
   uint32_t* rows;
   float* lb;
   int64_t cap;
-  uint32_t* pilot;  // pilot counts [qc] (pilot launch only)
+  uint32_t* pilot;  // pilot counts (pilot launch only): kept rows [qc], then rows alive after 8 slots [qc]
+  const int* perm;  // tile slot -> chunk query (NULL: slot j holds query j)
   int stop;         // lists may overflow (MIXED): overflowed queries leave the scan
   uint32_t* status;  // device status word of the collection's call
   int cta0, ncta;
@@ -226,6 +233,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
   extern __shared__ __align__(16) uint32_t s_tab[];  // region r (64 KB): pairs 2r, 2r+1
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
+  __shared__ int s_qid[QT];  // chunk query of each tile slot
   __shared__ int s_skip;
   const ScanColl& C = W.c[coll_of_block(W)];
   const uint4* __restrict__ sax = C.sax;
@@ -251,17 +259,19 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
         int skip = 1;
         for (int q = 0; q < QT; ++q) {
           const int qq = qb + q;
+          const int qid = qq < qc ? (C.perm ? C.perm[qq] : qq) : 0;
           // a list whose count passed its capacity has flagged its overflow (or was handed to the
           // tensor-core screening beforehand): the query takes no further part in the scan
-          const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qq) > cap);
+          const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qid) > cap);
           s_active[q] = act;
+          s_qid[q] = qid;
           if (act) skip = 0;
         }
         s_skip = skip;
       }
       __syncthreads();
       if (s_skip) continue;
-      load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, s_active, s_tab, s_thr);
+      load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, C.perm, s_active, s_tab, s_thr);
       __syncthreads();
       __half2 thh[NP];
       tile_thresholds<NP>(s_thr, thh);
@@ -286,13 +296,12 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
               if (!((any >> (2 * p)) & 3u)) continue;
-              const int qa = qb + 2 * p;
+              const int qa = s_qid[2 * p], qe = s_qid[2 * p + 1];
               const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
               append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa,
                           C.rows + (int64_t)qa * cap, C.lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
-              append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qa + 1,
-                          C.rows + (int64_t)(qa + 1) * cap, C.lb + (int64_t)(qa + 1) * cap, cap,
-                          ovf[2 * p + 1], status);
+              append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qe,
+                          C.rows + (int64_t)qe * cap, C.lb + (int64_t)qe * cap, cap, ovf[2 * p + 1], status);
             }
           }
         }
@@ -308,15 +317,16 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
 }
 
 // Pilot pass: counts, per query, the kept rows among every `stride`-th group of 32 rows (same
-// test as the scan). Queries whose scaled count says the list would overflow go straight to the
-// tensor-core screening instead of appending rows that would be discarded.
+// test as the scan) and the rows still within the threshold after 8 of the 16 slots. The first
+// count routes queries whose list would overflow to the tensor-core screening (MIXED); the
+// second orders the chunk's queries so that tiles gather queries whose scans abandon alike.
 template <int NP>
 __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(const __grid_constant__ ScanWork W) {
   constexpr int QT = 2 * NP;
   extern __shared__ __align__(16) uint32_t s_tab[];
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
-  __shared__ uint32_t s_cnt[QT];
+  __shared__ uint32_t s_cnt[2 * QT];
   const ScanColl& C = W.c[coll_of_block(W)];
   const int64_t n = C.n, stride = W.stride;
   const int qc = C.qc;
@@ -332,31 +342,74 @@ __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(const __grid_consta
   for (int tile = 0; tile < C.ntiles; ++tile) {
     const int qb = tile * QT;
     __syncthreads();
-    load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, s_active, s_tab, s_thr);
-    if (threadIdx.x < QT) s_cnt[threadIdx.x] = 0u;
+    load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, nullptr, s_active, s_tab, s_thr);
+    if (threadIdx.x < 2 * QT) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     __half2 thh[NP];
     tile_thresholds<NP>(s_thr, thh);
-    uint32_t cnt[QT];
+    uint32_t cnt[QT], cnt8[QT];
 #pragma unroll
-    for (int q = 0; q < QT; ++q) cnt[q] = 0u;
+    for (int q = 0; q < QT; ++q) cnt[q] = cnt8[q] = 0u;
     for (int64_t it = s0 + wib; it < s1; it += nw) {
       const int64_t row = it * stride * 32 + lane;
       const bool rv = row < n;
       const uint4 word = rv ? __ldcg(C.sax + row) : make_uint4(0u, 0u, 0u, 0u);
-      __half2 sum[NP];
-      const uint32_t keepmask = row_keep_bits<NP>(word, rv, offp, tab, thh, sum);
+      const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
+      __half2 a0[NP], a1[NP];
 #pragma unroll
-      for (int q = 0; q < QT; ++q) cnt[q] += __popc(__ballot_sync(PARIS_FULL_MASK, (keepmask >> q) & 1u));
+      for (int p = 0; p < NP; ++p) a0[p] = a1[p] = __floats2half2_rn(0.f, 0.f);
+      add_slots<NP, 0, 8>(wv, offp, tab, a0, a1);
+      uint32_t m8 = 0u, mk = 0u;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const uint32_t m = __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
+        m8 |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
+      }
+      add_slots<NP, 8, 16>(wv, offp, tab, a0, a1);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const uint32_t m = __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
+        mk |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
+      }
+      m8 = rv ? m8 : 0u;
+      mk = rv ? mk : 0u;
+#pragma unroll
+      for (int q = 0; q < QT; ++q) {
+        cnt[q] += __popc(__ballot_sync(PARIS_FULL_MASK, (mk >> q) & 1u));
+        cnt8[q] += __popc(__ballot_sync(PARIS_FULL_MASK, (m8 >> q) & 1u));
+      }
     }
     if (lane == 0) {
 #pragma unroll
-      for (int q = 0; q < QT; ++q)
+      for (int q = 0; q < QT; ++q) {
         if (cnt[q]) atomicAdd(&s_cnt[q], cnt[q]);
+        if (cnt8[q]) atomicAdd(&s_cnt[QT + q], cnt8[q]);
+      }
     }
     __syncthreads();
-    if (threadIdx.x < QT && qb + (int)threadIdx.x < qc && s_cnt[threadIdx.x])
-      atomicAdd(C.pilot + qb + threadIdx.x, s_cnt[threadIdx.x]);
+    if (threadIdx.x < 2 * QT) {
+      const int q = threadIdx.x % QT, which = threadIdx.x / QT;
+      if (qb + q < qc && s_cnt[threadIdx.x]) atomicAdd(C.pilot + which * qc + qb + q, s_cnt[threadIdx.x]);
+    }
+  }
+}
+
+// Tile order of a chunk: queries by rows alive after 8 slots in the pilot sample (ties by
+// query), routed queries last. One block; rank by counting (qc <= 4096).
+__global__ void __launch_bounds__(1024) order_kernel(const uint32_t* __restrict__ alive8,
+                                                     const uint32_t* __restrict__ count, int qc, int64_t cap,
+                                                     int stop, int* __restrict__ perm) {
+  __shared__ unsigned long long key[4096];
+  for (int q = threadIdx.x; q < qc; q += blockDim.x) {
+    const bool routed = stop && (int64_t)count[q] > cap;
+    key[q] = ((unsigned long long)(routed ? 0xffffffffu : alive8[q]) << 32) | (unsigned)q;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < qc; q += blockDim.x) {
+    const unsigned long long k = key[q];
+    int rank = 0;
+    for (int j = 0; j < qc; ++j) rank += key[j] < k ? 1 : 0;
+    perm[rank] = q;
   }
 }
 
@@ -438,7 +491,13 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   W.block_groups = block_groups();
   W.stride = PW.stride = kPilotStride;
   double work[kMaxColl], pwork[kMaxColl];
+  int pilot_of[kMaxColl];  // scan collection of each pilot collection
   int64_t groups_total = 0, pilot_samples = 0;
+  auto pack = [&](const QueryState& qs, const ChunkState& cs, const int* perm) {
+    pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
+        qs.qtable + cs.q0 * entries, cs.qc, entries, perm, cs.packed);
+    note_launches(1);
+  };
   for (int j = 0; j < m; ++j) {
     const paris_index* idx = jobs[j].idx;
     const QueryState& qs = *jobs[j].qs;
@@ -458,21 +517,21 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     C.cap = cs.cap;
     C.stop = jobs[j].stop;
     C.status = jobs[j].status;
-    pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
-        qs.qtable + cs.q0 * entries, cs.qc, entries, cs.packed);
-    note_launches(1);
-    W.c[W.ncoll] = C;
-    work[W.ncoll++] = (double)groups * C.ntiles;
-    groups_total += groups;
-    if (C.stop && cs.cap < idx->n && groups >= 64 * kPilotStride) {
-      // lists that would overflow anyway are handed to the tensor-core screening up front
+    pack(qs, cs, nullptr);
+    const bool route = C.stop && cs.cap < idx->n;
+    if (groups >= 64 * kPilotStride && (route || C.ntiles > 1)) {
+      // the pilot pass: route lists that would overflow anyway (MIXED) and order the tiles
       C.pilot = cs.pilot;
-      PARIS_CUDA(cudaMemsetAsync(cs.pilot, 0, (size_t)cs.qc * 4, st));
+      PARIS_CUDA(cudaMemsetAsync(cs.pilot, 0, (size_t)cs.qc * 8, st));
       const int64_t samples = (groups + kPilotStride - 1) / kPilotStride;
+      pilot_of[PW.ncoll] = W.ncoll;
       PW.c[PW.ncoll] = C;
       pwork[PW.ncoll++] = (double)samples * C.ntiles;
       pilot_samples += samples;
     }
+    W.c[W.ncoll] = C;
+    work[W.ncoll++] = (double)groups * C.ntiles;
+    groups_total += groups;
   }
   if (PW.ncoll > 0) {
     const int pgrid = (int)std::max<int64_t>(PW.ncoll, std::min<int64_t>(sms, pilot_samples / 64));
@@ -481,9 +540,18 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     note_launches(1);
     for (int c = 0; c < PW.ncoll; ++c) {
       const ScanColl& C = PW.c[c];
-      pilot_route_kernel<<<(C.qc + 255) / 256, 256, 0, st>>>(C.pilot, C.qc, kPilotStride, kPilotRoute * (double)C.cap,
-                                                             C.cap, C.count);
-      note_launches(1);
+      const ChunkState& cs = *jobs[pilot_of[c]].cs;
+      if (C.stop && C.cap < C.n) {
+        pilot_route_kernel<<<(C.qc + 255) / 256, 256, 0, st>>>(C.pilot, C.qc, kPilotStride,
+                                                               kPilotRoute * (double)C.cap, C.cap, C.count);
+        note_launches(1);
+      }
+      if (C.ntiles > 1 && C.qc <= 4096) {  // the ordering ranks at most 4096 queries in one block
+        order_kernel<<<1, 1024, 0, st>>>(C.pilot + C.qc, C.count, C.qc, C.cap, C.stop, cs.perm);
+        pack(*jobs[pilot_of[c]].qs, cs, cs.perm);
+        W.c[pilot_of[c]].perm = cs.perm;
+        note_launches(1);
+      }
     }
     PARIS_CUDA(cudaGetLastError());
   }

@@ -48,7 +48,8 @@ struct ChunkState {
   uint32_t* cont_count = nullptr;  // [qc]
   uint32_t* cont_rows = nullptr;   // [qc][kContCap]
   uint32_t* cont_limbs = nullptr;  // [qc][kContCap][kLimbs]
-  uint32_t* pilot = nullptr;       // [qc] pilot-pass kept counts (batched scan)
+  uint32_t* pilot = nullptr;       // [2][qc] pilot-pass counts: kept rows, rows alive after 8 slots
+  int* perm = nullptr;             // [qc] tile slot -> chunk query of the batched scan
   int* dslots = nullptr;           // [qc] chunk slots of the queries screened by the tensor cores
   int* dnd = nullptr;              // [1] number of such queries
   int* nover = nullptr;            // [1] screened lists that overflowed
