@@ -452,17 +452,21 @@ def main():
         roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel")}
     elif args.mode == "batched":
-        # the batched scan is bound by shared-memory table lookups: 8 32-bit lookups (FP16 pairs)
-        # per (row, query); peak = 32 banks x 152 SMs x the median SM clock under load
-        qscan = nq * steps
-        lookups = 8.0 * n * qscan
+        # the batched scan is bound by shared-memory table lookups: one 32-bit lookup per lane,
+        # slot and query pair, counted by the library (early-abandoned slots are not looked up);
+        # peak = 32 banks x 152 SMs x the median SM clock under load
+        lookups = float(sum(s["lb_lookups"] for r in recs for s in r["stats"]))
+        qt_used = recs[0]["stats"][0]["query_tile"]
         ach = lookups / (ph["lbscan"] * 1e-3) / 1e9
         clk_mhz = clk.get("sm_mhz") or 2070.0
         peak_l = 32.0 * 152 * clk_mhz * 1e6 / 1e9
         roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
-                "unit": "G shared-memory lookups/s", "frac": ach / peak_l, "traffic": traffic_for("lbscan_batched_kernel"),
-                "note": "upper estimate: counts every (row, query) lookup although scans of queries sent to the "
-                        "tensor-core path stop early"}
+                "unit": "G shared-memory lookups/s", "frac": ach / peak_l,
+                "traffic": traffic_for("lbscan_batched_kernel"),
+                "lookups_per_step": lookups / steps,
+                "query_tile": qt_used,
+                "summaries_read_per_step_gb_at_most": 16.0 * n * (-(-nq // max(1, qt_used))) / 1e9,
+                "note": "time includes the pilot pass and the query ordering; lookups counted on the device"}
     else:
         roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel")}

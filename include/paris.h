@@ -129,6 +129,8 @@ typedef struct paris_query_stats {
   int32_t rescreens;   /* MIXED: repeated BF16 screenings of queries whose screened candidate list
                           overflowed (each repeat first lowers the query's threshold to the k-th
                           best candidate found; the call fails with EINTERNAL after 4 repeats) */
+  int64_t lb_lookups;  /* BATCHED: lower-bound table lookups the scans performed (one per lane,
+                          slot and pair of queries; early abandoning skips the rest) */
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */

@@ -42,7 +42,7 @@ class QueryStats(C.Structure):
                 ("leaf_rows", C.c_int64), ("dense_queries", C.c_int64), ("ms_prep", C.c_double),
                 ("ms_descent", C.c_double), ("ms_lbscan", C.c_double), ("ms_refine", C.c_double),
                 ("ms_select", C.c_double), ("ms_dense", C.c_double), ("query_tile", C.c_int32),
-                ("rescreens", C.c_int32)]
+                ("rescreens", C.c_int32), ("lb_lookups", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

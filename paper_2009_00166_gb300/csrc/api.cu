@@ -505,7 +505,7 @@ static paris_status alloc_query_state(const paris_index* idx, int64_t nq, int k,
   };
   size_t o_paa = take((size_t)nq * 16 * 8), o_key = take((size_t)nq * 8),
          o_tab = take((size_t)nq * idx->card * 16 * 4), o_thr = take((size_t)nq * 4), o_bsf = take((size_t)nq * 8),
-         o_leaf = take((size_t)nq * 16), o_seed = take((size_t)nq * 4), o_stat = take(4), o_cnt = take(4 * 8);
+         o_leaf = take((size_t)nq * 16), o_seed = take((size_t)nq * 4), o_stat = take(4), o_cnt = take(5 * 8);
   if (!block.alloc(off, st)) return fail(PARIS_ENOMEM, "query state (%zu bytes)", off);
   char* b = block.as<char>();
   qs.nq = nq;
@@ -522,7 +522,7 @@ static paris_status alloc_query_state(const paris_index* idx, int64_t nq, int k,
   qs.counters = (unsigned long long*)(b + o_cnt);
   qs.cg = gamma_scale(idx->len);
   PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-  PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+  PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
   return PARIS_OK;
 }
 
@@ -684,7 +684,7 @@ struct KnnJob {
     if (nq == 0) return PARIS_OK;
     if (o.mode == PARIS_MODE_BATCHED && qt == 0) return fail(PARIS_EINTERNAL, "query tile unknown at capture");
     PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
     PARIS_CUDA(cudaMemsetAsync(cs.nover, 0, 4, st));
     PARIS_TRY(front());
     for (int64_t c = 0; c < chunks(); ++c) {
@@ -704,7 +704,7 @@ struct KnnJob {
   paris_status run_eager(const char* what) {
     if (nq == 0) return PARIS_OK;
     PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 32, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
     dense_total = 0;
     rescreens = 0;
     PARIS_TRY(front());
@@ -794,13 +794,14 @@ struct KnnJob {
       stats->ms_lbscan = ms[2];
       stats->ms_refine = ms[3];
       stats->ms_select = ms[4];
-      unsigned long long c[4];
+      unsigned long long c[5];
       PARIS_CUDA(cudaMemcpyAsync(c, qs.counters, sizeof c, cudaMemcpyDeviceToHost, st));
       PARIS_CUDA(cudaStreamSynchronize(st));
       stats->candidates = (int64_t)c[0];
       stats->refined = (int64_t)c[1];
       stats->contenders = (int64_t)c[2];
       stats->leaf_rows = (int64_t)c[3];
+      stats->lb_lookups = (int64_t)c[4];
     }
     return PARIS_OK;
   }

@@ -161,16 +161,19 @@ __device__ __forceinline__ bool warp_alive(bool rv, const __half2 (&a0)[NP], con
 // is within its threshold (returns 0 for every lane then).
 template <int NP>
 __device__ __forceinline__ uint32_t row_keep_bits(const uint4& word, bool rv, const uint32_t (&offp)[8], uint32_t tab,
-                                                  const __half2 (&thh)[NP], __half2 (&sum)[NP]) {
+                                                  const __half2 (&thh)[NP], __half2 (&sum)[NP], uint32_t& slots) {
   const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
   __half2 a0[NP], a1[NP];  // two chains per pair: shorter latency
 #pragma unroll
   for (int p = 0; p < NP; ++p) a0[p] = a1[p] = __floats2half2_rn(0.f, 0.f);
   add_slots<NP, 0, 4>(wv, offp, tab, a0, a1);
+  slots += 4;
   if (!warp_alive<NP>(rv, a0, a1, thh)) return 0u;
   add_slots<NP, 4, 8>(wv, offp, tab, a0, a1);
+  slots += 4;
   if (!warp_alive<NP>(rv, a0, a1, thh)) return 0u;
   add_slots<NP, 8, 16>(wv, offp, tab, a0, a1);
+  slots += 8;
   uint32_t keepmask = 0u;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
@@ -206,6 +209,7 @@ struct ScanColl {
   uint32_t* pilot;  // pilot counts (pilot launch only): kept rows [qc], then rows alive after 8 slots [qc]
   const int* perm;  // tile slot -> chunk query (NULL: slot j holds query j)
   int stop;         // lists may overflow (MIXED): overflowed queries leave the scan
+  unsigned long long* lookups;  // table lookups performed (one per lane, slot and query pair)
   uint32_t* status;  // device status word of the collection's call
   int cta0, ncta;
 };
@@ -278,6 +282,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
       bool ovf[QT];
 #pragma unroll
       for (int q = 0; q < QT; ++q) ovf[q] = false;
+      uint32_t slots = 0;  // slots this warp looked up in this tile, per row group
       for (int64_t it = b0 + (int64_t)wib * kBUnroll; it < b1; it += (int64_t)nw * kBUnroll) {
         uint4 word[kBUnroll];
 #pragma unroll
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
           const int64_t row = (it + u) * 32 + lane;
           const bool rv = it + u < b1 && row < n;
           __half2 sum[NP];
-          const uint32_t keepmask = row_keep_bits<NP>(word[u], rv, offp, tab, thh, sum);
+          const uint32_t keepmask = row_keep_bits<NP>(word[u], rv, offp, tab, thh, sum, slots);
           const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
           if (any) {  // rare: some lane keeps this row for some query of the tile
 #pragma unroll
@@ -312,6 +317,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
           if (all) break;
         }
       }
+      if (lane == 0 && C.lookups && slots) atomicAdd(C.lookups, (unsigned long long)slots * (NP * 32));
     }
   }
 }
@@ -517,6 +523,7 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     C.cap = cs.cap;
     C.stop = jobs[j].stop;
     C.status = jobs[j].status;
+    C.lookups = qs.counters + 4;
     pack(qs, cs, nullptr);
     const bool route = C.stop && cs.cap < idx->n;
     if (groups >= 64 * kPilotStride && (route || C.ntiles > 1)) {

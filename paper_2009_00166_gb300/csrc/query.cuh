@@ -22,7 +22,7 @@ struct QueryState {
   int64_t* leaf = nullptr;         // [nq][2]
   float* seed = nullptr;           // [nq]
   uint32_t* status = nullptr;      // [1]
-  unsigned long long* counters = nullptr;  // [4]: candidates, refined, contenders, leaf rows
+  unsigned long long* counters = nullptr;  // [5]: candidates, refined, contenders, leaf rows, batched-scan lookups
   float cg = 1.f;                  // (1+gamma)/(1-gamma), rounded up, gamma = gamma_{len+2}
   const uint64_t* keys = nullptr;  // [nq][nk] approximate-search keys (NULL: qkey only)
   int nk = 1;

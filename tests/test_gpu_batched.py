@@ -24,6 +24,10 @@ def setup():
     idx.free()
 
 
+def x_rows(idx):
+    return idx.n
+
+
 def run(P, idx, q, k, **kw):
     i, d, st = P.paris_exact_knn_ex(idx, torch.from_numpy(q).cuda(), k, want_stats=True, **kw)
     torch.cuda.synchronize()
@@ -37,6 +41,8 @@ def test_batched_equals_oracle(setup, qt, k):
     for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
         gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=prec)
         assert st["query_tile"] in (2, 4, 8, 12) and (qt == 0 or st["query_tile"] == qt)
+        assert 0 < st["lb_lookups"] <= 16 * (st["query_tile"] // 2) * 32 * ((x_rows(idx) + 31) // 32) * (
+            -(-len(q) // st["query_tile"]))
         assert np.array_equal(gi, want[k][0])
         assert np.allclose(gd, want[k][1], rtol=1e-5, atol=0)
 
@@ -44,6 +50,7 @@ def test_batched_equals_oracle(setup, qt, k):
 def test_batched_equals_plain_and_small_chunks(setup):
     P, idx, q, _ = setup
     a = run(P, idx, q, 3, mode=P.PARIS_MODE_PLAIN)
+    assert a[2]["lb_lookups"] == 0                       # counted by the batched scans only
     b = run(P, idx, q, 3, mode=P.PARIS_MODE_BATCHED, query_tile=8, chunk=5)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
