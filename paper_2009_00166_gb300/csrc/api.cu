@@ -95,6 +95,22 @@ void dev_free(void* p, size_t bytes, cudaStream_t st) {
   cudaFreeAsync(p, st);
 }
 
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  int dev = 0, ok = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&ok, cudaDevAttrCanMapHostMemory, dev) != cudaSuccess || !ok) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.devicePointer;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -298,6 +314,8 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (int j = 0; j < nsub; ++j) PARIS_CUDA(cudaMemsetAsync(cs.count + offs[j], 0, (size_t)m * 4, st));
+  // the trial scans' lookups are not the call's (tuning runs before any chunk is scanned)
+  PARIS_CUDA(cudaMemsetAsync(qs.counters + 4, 0, 8, st));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tuned[key] = best;
   *out = best;
@@ -382,16 +400,26 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     return s;
   };
   const size_t series_bytes = (size_t)n * len * sizeof(float);
+  // pinned host series: the encode pass reads it through the host mapping and writes the
+  // device copy itself (one pass instead of a copy and a pass)
+  const float* encode_src = series;
+  float* encode_copy = nullptr;
   if (is_device_ptr(series)) {
     idx->series = series;
   } else {
     idx->series_owned = dev_alloc(series_bytes, st);
     if (!idx->series_owned) return bail(fail(PARIS_ENOMEM, "device copy of the series (%zu bytes)", series_bytes));
     idx->series_owned_bytes = series_bytes;
-    if (cudaMemcpyAsync(idx->series_owned, series, series_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    const float* mapped = (const float*)mapped_host_ptr(series);
+    if (mapped && make_row_shape(len, w, mapped).fast) {
+      encode_src = mapped;
+      encode_copy = (float*)idx->series_owned;
+    } else if (cudaMemcpyAsync(idx->series_owned, series, series_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
       return bail(fail(PARIS_ECUDA, "copying the series to the device"));
+    }
     idx->series = (const float*)idx->series_owned;
   }
+  if (!encode_copy) encode_src = idx->series;
   paris_status s = upload_breakpoints(idx, st);
   if (s != PARIS_OK) return bail(s);
   idx->sax = (uint8_t*)dev_alloc((size_t)n * PARIS_SAX_BYTES, st);
@@ -401,7 +429,7 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   if (!idx->sax || !idx->keys_sorted || !idx->rows_sorted || !status.alloc(4, st))
     return bail(fail(PARIS_ENOMEM, "index arrays for %lld series", (long long)n));
   if (cudaMemsetAsync(status.p, 0, 4, st) != cudaSuccess) return bail(fail(PARIS_ECUDA, "memset"));
-  RowShape sh = make_row_shape(len, w, idx->series);
+  RowShape sh = make_row_shape(len, w, encode_src);
   // the mixed-precision screening's inputs, written by the same pass when asked for
   ShadowBufs shb;
   const bool fused = opts && opts->bf16_shadow && dense_shape_ok(len) && sh.fast && sh.s <= 16;
@@ -409,8 +437,8 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     s = alloc_shadow(idx, &shb, st);
     if (s != PARIS_OK) return bail(s);
   }
-  s = launch_encode(idx->series, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr, idx->keys_sorted,
-                    nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm);
+  s = launch_encode(encode_src, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr, idx->keys_sorted,
+                    nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm, encode_copy);
   if (s == PARIS_OK && fused) s = finish_shadow(idx, &shb, st);
   if (s != PARIS_OK) {
     free_shadow_bufs(idx, &shb, st);

@@ -81,3 +81,37 @@ def test_build_index_order(n):
     assert np.array_equal(got_keys, want_keys)
     assert np.array_equal(got_rows, want_rows)
     idx.free()
+
+
+@pytest.mark.parametrize("where", ["pinned", "pageable"])
+@pytest.mark.parametrize("shadow", [False, True])
+def test_build_from_host_series(where, shadow):
+    """A host series: pinned memory is read by the encode pass through its device mapping (the
+    pass writes the device copy); pageable memory is copied first. Both give the index of the
+    device-built one, and exact answers from the device copy."""
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    n = 50_003
+    x = rw(n, 256, 21)
+    host = torch.from_numpy(x)
+    if where == "pinned":
+        host = host.pin_memory()
+    idx = P.paris_build_ex(host, bf16_shadow=shadow)
+    ref = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    assert np.array_equal(P.paris_export_sax(idx).cpu().numpy(), P.paris_export_sax(ref).cpu().numpy())
+    for a, b in zip(P.paris_export_order(idx), P.paris_export_order(ref)):
+        assert np.array_equal(a, b)
+    q, _, _ = synth.mixed_sigma_queries(x, n, 256, 12, 0.01, 2.0, seed=9)
+    wi, wd = oindex_knn(x, q)
+    for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
+        gi, gd = P.paris_exact_knn_ex(idx, torch.from_numpy(q).to(dev), 3, mode=P.PARIS_MODE_BATCHED, precision=prec)
+        assert np.array_equal(gi.cpu().numpy(), wi)
+        assert np.allclose(gd.cpu().numpy(), wd, rtol=1e-5, atol=0)
+    idx.free()
+    ref.free()
+
+
+def oindex_knn(x, q):
+    from oracle import knn as oknn
+    return oknn.knn(x, q, 3)
