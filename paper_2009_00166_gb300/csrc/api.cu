@@ -95,22 +95,6 @@ void dev_free(void* p, size_t bytes, cudaStream_t st) {
   cudaFreeAsync(p, st);
 }
 
-const void* mapped_host_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-  int dev = 0, ok = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&ok, cudaDevAttrCanMapHostMemory, dev) != cudaSuccess || !ok) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return a.devicePointer;
-}
-
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -370,6 +354,62 @@ static paris_status check_shape(int64_t n, int32_t len, int32_t w, int32_t card)
   return PARIS_OK;
 }
 
+namespace {
+// Library copy streams of a device (two DMA engines copy concurrently).
+std::mutex g_copy_mutex;
+cudaStream_t g_copy_streams[64][2] = {};
+
+paris_status copy_streams(cudaStream_t* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(PARIS_ECUDA, "current device");
+  std::lock_guard<std::mutex> lock(g_copy_mutex);
+  for (int i = 0; i < 2; ++i) {
+    if (!g_copy_streams[dev][i] && cudaStreamCreateWithFlags(&g_copy_streams[dev][i], cudaStreamNonBlocking) != cudaSuccess)
+      return fail(PARIS_ECUDA, "copy stream");
+    out[i] = g_copy_streams[dev][i];
+  }
+  return PARIS_OK;
+}
+}  // namespace
+
+// A host series is copied to the device in chunks on two copy streams while the encode pass
+// works through the chunks already copied. Chunks start at multiples of 16 rows (the rotation
+// of the summary slots follows the row number).
+static paris_status copy_and_encode(paris_index* idx, const float* host, const RowShape& sh, ShadowBufs& shb,
+                                    uint32_t* status, cudaStream_t st) {
+  const int64_t n = idx->n, len = idx->len;
+  const size_t row_bytes = (size_t)len * sizeof(float);
+  int64_t rows = (int64_t)((size_t)(512u << 20) / row_bytes);  // about 512 MB per chunk
+  rows = std::max<int64_t>(16, rows / 16 * 16);
+  cudaStream_t cs[2];
+  PARIS_TRY(copy_streams(cs));
+  cudaEvent_t ready;
+  PARIS_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  PARIS_CUDA(cudaEventRecord(ready, st));  // the device copy's memory is allocated on st
+  for (int i = 0; i < 2; ++i) PARIS_CUDA(cudaStreamWaitEvent(cs[i], ready, 0));
+  cudaEventDestroy(ready);
+  float* dst = (float*)idx->series_owned;
+  paris_status s = PARIS_OK;
+  int j = 0;
+  for (int64_t r0 = 0; r0 < n && s == PARIS_OK; r0 += rows, ++j) {
+    const int64_t m = std::min(rows, n - r0);
+    cudaEvent_t done;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemcpyAsync(dst + r0 * len, host + r0 * len, (size_t)m * row_bytes, cudaMemcpyHostToDevice, cs[j & 1]) !=
+            cudaSuccess ||
+        cudaEventRecord(done, cs[j & 1]) != cudaSuccess || cudaStreamWaitEvent(st, done, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PARIS_ECUDA, "copying the series to the device");
+    }
+    cudaEventDestroy(done);
+    s = launch_encode(dst + r0 * len, m, sh, idx->card, idx->bits, idx->beta_keys, idx->sax + r0 * PARIS_SAX_BYTES,
+                      nullptr, idx->keys_sorted + r0, nullptr, status, st,
+                      shb.shadow ? (void*)((uint16_t*)shb.shadow + r0 * len) : nullptr,
+                      shb.xnorm ? shb.xnorm + r0 : nullptr);
+  }
+  return s;
+}
+
 paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t w, int32_t card,
                             const paris_build_opts* opts, void* stream, paris_index** out) {
   clear_error();
@@ -400,26 +440,16 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     return s;
   };
   const size_t series_bytes = (size_t)n * len * sizeof(float);
-  // pinned host series: the encode pass reads it through the host mapping and writes the
-  // device copy itself (one pass instead of a copy and a pass)
-  const float* encode_src = series;
-  float* encode_copy = nullptr;
+  const float* host_src = nullptr;  // a host series, copied in while the encode pass runs
   if (is_device_ptr(series)) {
     idx->series = series;
   } else {
     idx->series_owned = dev_alloc(series_bytes, st);
     if (!idx->series_owned) return bail(fail(PARIS_ENOMEM, "device copy of the series (%zu bytes)", series_bytes));
     idx->series_owned_bytes = series_bytes;
-    const float* mapped = (const float*)mapped_host_ptr(series);
-    if (mapped && make_row_shape(len, w, mapped).fast) {
-      encode_src = mapped;
-      encode_copy = (float*)idx->series_owned;
-    } else if (cudaMemcpyAsync(idx->series_owned, series, series_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      return bail(fail(PARIS_ECUDA, "copying the series to the device"));
-    }
     idx->series = (const float*)idx->series_owned;
+    host_src = series;
   }
-  if (!encode_copy) encode_src = idx->series;
   paris_status s = upload_breakpoints(idx, st);
   if (s != PARIS_OK) return bail(s);
   idx->sax = (uint8_t*)dev_alloc((size_t)n * PARIS_SAX_BYTES, st);
@@ -429,7 +459,7 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   if (!idx->sax || !idx->keys_sorted || !idx->rows_sorted || !status.alloc(4, st))
     return bail(fail(PARIS_ENOMEM, "index arrays for %lld series", (long long)n));
   if (cudaMemsetAsync(status.p, 0, 4, st) != cudaSuccess) return bail(fail(PARIS_ECUDA, "memset"));
-  RowShape sh = make_row_shape(len, w, encode_src);
+  RowShape sh = make_row_shape(len, w, idx->series);
   // the mixed-precision screening's inputs, written by the same pass when asked for
   ShadowBufs shb;
   const bool fused = opts && opts->bf16_shadow && dense_shape_ok(len) && sh.fast && sh.s <= 16;
@@ -437,8 +467,9 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     s = alloc_shadow(idx, &shb, st);
     if (s != PARIS_OK) return bail(s);
   }
-  s = launch_encode(encode_src, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr, idx->keys_sorted,
-                    nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm, encode_copy);
+  s = host_src ? copy_and_encode(idx, host_src, sh, shb, status.as<uint32_t>(), st)
+               : launch_encode(idx->series, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr,
+                               idx->keys_sorted, nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm);
   if (s == PARIS_OK && fused) s = finish_shadow(idx, &shb, st);
   if (s != PARIS_OK) {
     free_shadow_bufs(idx, &shb, st);

@@ -16,8 +16,7 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     const float* __restrict__ series, int64_t n, RowShape sh, int card, int bits,
     const uint64_t* __restrict__ beta_keys_g, uint8_t* __restrict__ sax_rot,
     uint8_t* __restrict__ sax_plain, uint64_t* __restrict__ key64, double* __restrict__ paa_out,
-    uint32_t* __restrict__ status, __nv_bfloat16* __restrict__ shadow, float2* __restrict__ xnorm,
-    float* __restrict__ series_copy) {
+    uint32_t* __restrict__ status, __nv_bfloat16* __restrict__ shadow, float2* __restrict__ xnorm) {
   __shared__ uint64_t beta_keys[255];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
   __syncthreads();
@@ -39,20 +38,11 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     // rotated summary slot: slot j holds segment (j + r) mod 16 (0 when that segment >= w)
     const int src = (seg + (int)(r & 15)) & 15;
     const int b = __shfl_sync(PARIS_FULL_MASK, sym, (half << 4) | src);
-    if (series_copy && rv && seg < sh.w) {
-      // device copy of the series (the input is host memory mapped into the device), written
-      // from the values this warp has just read
-      const float4* p = reinterpret_cast<const float4*>(series + r * (int64_t)sh.len + seg * sh.s);
-      float4* d = reinterpret_cast<float4*>(series_copy + r * (int64_t)sh.len + seg * sh.s);
-#pragma unroll
-      for (int v = 0; v < SEGV; ++v) d[v] = p[v];
-    }
     if (SEGV <= 4 && shadow) {
       // BF16 copy of the lane's segment and the row's fp32 squared norm (the mixed-precision
       // screening's inputs), from the values this warp has just read
       const bool act = rv && seg < sh.w;
-      const float* src = series_copy ? series_copy : series;  // this thread's own copy when there is one
-      const float4* p = reinterpret_cast<const float4*>(src + r * (int64_t)sh.len + (act ? seg * sh.s : 0));
+      const float4* p = reinterpret_cast<const float4*>(series + r * (int64_t)sh.len + (act ? seg * sh.s : 0));
       float acc = 0.f;
 #pragma unroll
       for (int v = 0; v < (SEGV <= 4 ? SEGV : 1); ++v) {
@@ -116,16 +106,15 @@ RowShape make_row_shape(int len, int w, const void* base_ptr) {
 paris_status launch_encode(const float* series, int64_t n, const RowShape& sh, int card, int bits,
                            const uint64_t* beta_keys, uint8_t* sax_rot, uint8_t* sax_plain,
                            uint64_t* key64, double* paa, uint32_t* status, cudaStream_t st, void* shadow,
-                           float2* xnorm, float* series_copy) {
+                           float2* xnorm) {
   if (n <= 0) return PARIS_OK;
-  if (series_copy && !sh.fast) return fail(PARIS_EINVAL, "copying the series during encode needs the float4 path");
   if (shadow && !(sh.fast && sh.s / 4 <= 4)) return fail(PARIS_EINVAL, "BF16 shadow during encode needs len/w <= 16");
   int grid = encode_grid(n);
   const int segv = sh.fast ? sh.s / 4 : 1;
 #define ENC(SV)                                                                                     \
   encode_kernel<SV><<<grid, kEncodeThreads, 0, st>>>(series, n, sh, card, bits, beta_keys, sax_rot, \
                                                      sax_plain, key64, paa, status,                \
-                                                     (__nv_bfloat16*)shadow, xnorm, series_copy)
+                                                     (__nv_bfloat16*)shadow, xnorm)
   switch (segv) {
     case 1: ENC(1); break;
     case 2: ENC(2); break;

@@ -89,9 +89,7 @@ RowShape make_row_shape(int len, int w, const void* base_ptr);
 paris_status launch_encode(const float* series, int64_t n, const RowShape& sh, int card, int bits,
                            const uint64_t* beta_keys, uint8_t* sax_rot, uint8_t* sax_plain,
                            uint64_t* key64, double* paa, uint32_t* status, cudaStream_t st,
-                           void* shadow = nullptr, float2* xnorm = nullptr, float* series_copy = nullptr);
-// Device address of a host buffer the device can read directly (pinned, mapped), else NULL.
-const void* mapped_host_ptr(const void* p);
+                           void* shadow = nullptr, float2* xnorm = nullptr);
 paris_status launch_unrotate_sax(const uint8_t* sax_rot, int64_t n, int w, uint8_t* out,
                                  cudaStream_t st);
 paris_status radix_sort_index(uint64_t* keys, uint32_t* rows, int64_t n, cudaStream_t st);

@@ -86,13 +86,13 @@ def test_build_index_order(n):
 @pytest.mark.parametrize("where", ["pinned", "pageable"])
 @pytest.mark.parametrize("shadow", [False, True])
 def test_build_from_host_series(where, shadow):
-    """A host series: pinned memory is read by the encode pass through its device mapping (the
-    pass writes the device copy); pageable memory is copied first. Both give the index of the
-    device-built one, and exact answers from the device copy."""
+    """A host series is copied in 512 MB chunks on two copy streams while the encode pass works
+    through the chunks already copied (1.1 GB here: three chunks, the last one partial). Pinned
+    or pageable, the index equals the device-built one and the answers are exact."""
     import paper_2009_00166_gb300 as P
     import synth
     dev = require_gpu()
-    n = 50_003
+    n = 1_100_003
     x = rw(n, 256, 21)
     host = torch.from_numpy(x)
     if where == "pinned":
