@@ -315,6 +315,32 @@ def main():
     from paper_2009_00166_gb300 import shards
     job_rate, total_ms = shards.job_throughput(total_ms, float(nq * args.steps))
 
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region), right
+    # after the device-resident steps and before the comparisons beside them
+    e2e = None
+    if args.e2e_steps > 0:
+        out_i = torch.empty((nq, k), dtype=torch.int64, pin_memory=True)
+        out_d = torch.empty((nq, k), dtype=torch.float32, pin_memory=True)
+        hq = qhost.numpy()
+        times = []
+        for it in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            # host series: copied in by the library
+            idx = P.paris_build_ex(host, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
+            if seed_mode == P.PARIS_SEED_LEARNED:
+                P.paris_attach_seed_model(idx, model, 3)
+            P.paris_exact_knn_ex(idx, qhost, k, out_idx=out_i, out_dist=out_d, mode=mode, precision=precision,
+                                 seed=seed_mode)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            idx.free()
+        t = sum(times[1:])                                          # first pass warms the allocator
+        e2e = {"value": nq * args.e2e_steps * world / t, "unit": "queries/s",
+               "h2d_bytes_per_step": int(host.numel() * 4 + hq.size * 4),
+               "d2h_bytes_per_step": int(nq * k * 12)}
+        del hq
+
     # ---- beside it: the plain method (one query per lower-bound pass, fp32 refinement) with the
     # descent seed and with the learned seed, and the headline form per sigma group; answers of
     # every form are compared with the headline's
@@ -385,33 +411,6 @@ def main():
                                   "identical_answers": bool(torch.equal(gi, ref_i))}
         plan.free()
         idx.free()
-
-    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if args.e2e_steps > 0:
-        out_i = torch.empty((nq, k), dtype=torch.int64, pin_memory=True)
-        out_d = torch.empty((nq, k), dtype=torch.float32, pin_memory=True)
-        hq = qhost.numpy()
-        times = []
-        for it in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            # host series: copied in by the library
-            idx = P.paris_build_ex(host, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
-            if seed_mode == P.PARIS_SEED_LEARNED:
-                P.paris_attach_seed_model(idx, model, 3)
-            for i in range(len(SIGMAS)):
-                sl = slice(i * args.per_sigma, (i + 1) * args.per_sigma)
-                P.paris_exact_knn_ex(idx, qhost[sl], k, out_idx=out_i[sl], out_dist=out_d[sl], mode=mode,
-                                     precision=precision, seed=seed_mode)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-            idx.free()
-        t = sum(times[1:])                                          # first pass warms the allocator
-        e2e = {"value": nq * args.e2e_steps * world / t, "unit": "queries/s",
-               "h2d_bytes_per_step": int(host.numel() * 4 + hq.size * 4),
-               "d2h_bytes_per_step": int(nq * k * 12)}
-        del hq
 
     if rank != 0:
         if world > 1:
