@@ -15,7 +15,7 @@
 // sum is within its threshold; partial sums of non-negative terms never decrease, so the kept
 // set and the stored bounds are unchanged.
 //
-// A pilot pass over every 64th row group first counts each query's kept rows; a query whose
+// A pilot pass over every 128th row group first counts each query's kept rows; a query whose
 // scaled count reaches 3/4 of its list capacity would overflow anyway and is handed to the
 // tensor-core screening before the scan (only when overflow is allowed, i.e. MIXED refinement).
 // The pilot's count of rows still within the threshold after 8 slots then orders the chunk's
@@ -36,7 +36,7 @@ constexpr int kBThreads = 768;
 constexpr int kBUnroll = 4;
 constexpr float kHalfKeep = 1.0f - 1.0f / 64.0f;
 constexpr float kHalfCap = 4000.0f;
-constexpr int64_t kPilotStride = 64;  // the pilot pass reads every 64th group of 32 rows
+constexpr int64_t kPilotStride = 128;  // the pilot pass reads every 128th group of 32 rows
 constexpr double kPilotRoute = 0.75;  // routed when the scaled pilot count reaches 0.75 * capacity
 
 __device__ __forceinline__ uint32_t pack_half2_rd(float a, float b) {
@@ -371,14 +371,17 @@ __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(const __grid_consta
         const uint32_t m = __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
         m8 |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
       }
-      add_slots<NP, 8, 16>(wv, offp, tab, a0, a1);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const uint32_t m = __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
-        mk |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
-      }
       m8 = rv ? m8 : 0u;
-      mk = rv ? mk : 0u;
+      // a pair dead after 8 slots stays dead (partial sums only grow): finish only when alive
+      if (__any_sync(PARIS_FULL_MASK, m8 != 0u)) {
+        add_slots<NP, 8, 16>(wv, offp, tab, a0, a1);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const uint32_t m = __hle2_mask(__hadd2(a0[p], a1[p]), thh[p]);
+          mk |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * p);
+        }
+        mk = rv ? mk : 0u;
+      }
 #pragma unroll
       for (int q = 0; q < QT; ++q) {
         cnt[q] += __popc(__ballot_sync(PARIS_FULL_MASK, (mk >> q) & 1u));

@@ -64,7 +64,7 @@ def test_bad_query_tile(setup):
 
 
 def test_pilot_routing_keeps_answers_exact():
-    """A collection large enough for the pilot pass (every 64th group of 32 rows): queries whose
+    """A collection large enough for the pilot pass (every 128th group of 32 rows): queries whose
     lists would overflow go to the tensor-core screening up front, tight ones are scanned, and
     every answer still equals the oracle's; a tile mixing both kinds is covered by the order."""
     import paper_2009_00166_gb300 as P
