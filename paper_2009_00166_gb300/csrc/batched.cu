@@ -487,12 +487,9 @@ template <int NP>
 paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   const int card = jobs[0].idx->card;
   const size_t smem = batched_smem(NP, card);
-  static int configured = 0;
-  if ((int)smem > configured) {
-    PARIS_CUDA(cudaFuncSetAttribute(lbscan_batched_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PARIS_CUDA(cudaFuncSetAttribute(pilot_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = (int)smem;
-  }
+  // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
+  PARIS_CUDA(cudaFuncSetAttribute(lbscan_batched_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PARIS_CUDA(cudaFuncSetAttribute(pilot_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t entries = (int64_t)card * 16;
   const int sms = sm_count_b();
   ScanWork W{}, PW{};

@@ -246,14 +246,17 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
     const float4* p = reinterpret_cast<const float4*>(row + (active ? (int64_t)seg * s : 0));
     constexpr bool kCache = SEGV <= 4;
     float4 cache[kCache ? SEGV : 1];
-    // pass 1: the largest magnitude as bits (NaN and infinity sort above every finite value)
-    uint32_t mb = 0u;
+    // pass 1: the largest magnitude as bits (NaN and infinity sort above every finite value) and
+    // the smallest nonzero one (as bits - 1, so that zeros drop out of the minimum)
+    uint32_t mb = 0u, mn = 0xffffffffu;
 #pragma unroll
     for (int v = 0; v < SEGV; ++v) {
       float4 x = active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (kCache) cache[kCache ? v : 0] = x;
-      mb = max(mb, max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu),
-                       max(__float_as_uint(x.z) & 0x7fffffffu, __float_as_uint(x.w) & 0x7fffffffu)));
+      const uint32_t u0 = __float_as_uint(x.x) & 0x7fffffffu, u1 = __float_as_uint(x.y) & 0x7fffffffu;
+      const uint32_t u2 = __float_as_uint(x.z) & 0x7fffffffu, u3 = __float_as_uint(x.w) & 0x7fffffffu;
+      mb = max(mb, max(max(u0, u1), max(u2, u3)));
+      mn = min(mn, min(min(u0 - 1u, u1 - 1u), min(u2 - 1u, u3 - 1u)));
     }
     if (mb >= 0x7f800000u) {
       finite = false;
@@ -268,23 +271,28 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
       const int lambda = emax - 126 + sh.log2s - 63;
       const int te = lambda + 23 + 127;                      // biased exponent of 2^(lambda+23)
       const uint32_t tbits = te >= 1 ? (uint32_t)te << 23 : 0u;  // 0: every fp32 value qualifies
-      const int na = -lambda;                                // scale by 2^na = 2^a * 2^b
-      const int a = na >> 1, b2 = na - a;
-      const float sa = __int_as_float((a + 127) << 23), sb = __int_as_float((b2 + 127) << 23);
-      bool tiny = false;
-      int64_t S = 0;
-#pragma unroll
-      for (int v = 0; v < SEGV; ++v) {
-        float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
-        const float xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t ub = __float_as_uint(xs[c]) & 0x7fffffffu;
-          tiny |= (ub - 1u) < (tbits - 1u) && tbits != 0u;  // nonzero and below 2^(lambda+23)
-          S += __float2ll_rz((xs[c] * sa) * sb);             // exact: an integer below 2^62
-        }
-      }
+      const bool tiny = tbits != 0u && mn < tbits - 1u;      // a nonzero magnitude below 2^(lambda+23)
       if (!tiny) {
+        // each value is (24-bit significand) * 2^(e - 150): in units of 2^lambda that is the
+        // significand shifted left by e - 150 - lambda (0..39), added exactly in int64 with
+        // integer operations only (no 64-bit conversion instructions)
+        int64_t S = 0;
+#pragma unroll
+        for (int v = 0; v < SEGV; ++v) {
+          float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
+          const uint32_t xb[4] = {__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z),
+                                  __float_as_uint(x.w)};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t ub = xb[c] & 0x7fffffffu;
+            const int e = (int)(ub >> 23);
+            // normal: implicit leading bit, exponent e; subnormal and zero: none, exponent 1
+            const uint32_t m = e ? ((ub & 0x7fffffu) | 0x800000u) : (ub & 0x7fffffu);
+            const int shl = max((e ? e : 1) - 150 - lambda, 0);  // >= 0 for every nonzero value here
+            const int64_t mag = (int64_t)((uint64_t)m << shl);
+            S += (xb[c] >> 31) ? -mag : mag;
+          }
+        }
         paa_out = fixed_to_double(S, lambda - sh.log2s);  // s is a power of two on this path
         done = true;
       }

@@ -650,12 +650,9 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   PARIS_CUDA(cudaGetLastError());
   CUtensorMap mapA;
   PARIS_TRY(make_bf16_map(&mapA, cs.dqbf, cs.dq_rows, idx->len, BM));
-  static bool attr = false;
-  if (!attr) {
-    PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
-    PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
-    attr = true;
-  }
+  // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
+  PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
+  PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
   DenseParams P;
   P.n = idx->n;
   P.len = idx->len;

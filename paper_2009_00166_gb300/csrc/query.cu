@@ -911,11 +911,8 @@ static paris_status lbscan_common(const paris_index* idx, const float* table, co
                                   float thr_value, uint32_t* count, uint32_t* rows, float* lb,
                                   int64_t cap, uint32_t* status, int stop_on_overflow, cudaStream_t st) {
   size_t smem = (size_t)idx->card * 64 * sizeof(float);
-  static int configured_smem = 0;
-  if ((int)smem > configured_smem) {
-    PARIS_CUDA(cudaFuncSetAttribute(lbscan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured_smem = (int)smem;
-  }
+  // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
+  PARIS_CUDA(cudaFuncSetAttribute(lbscan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int64_t groups = (idx->n + 31) / 32;
   int64_t need_blocks = (groups + (kLbThreads / 32) * kLbUnroll - 1) / ((kLbThreads / 32) * kLbUnroll);
   int grid = (int)std::min<int64_t>(need_blocks, (int64_t)sm_count() * 2);

@@ -210,12 +210,9 @@ paris_status radix_sort_index(uint64_t* keys, uint32_t* rows, int64_t n, cudaStr
   DevBuf kalt, ralt, hist;
   if (!kalt.alloc((size_t)n * 8, st) || !ralt.alloc((size_t)n * 4, st) || !hist.alloc((size_t)m * 4, st))
     return fail(PARIS_ENOMEM, "radix sort scratch (%lld rows)", (long long)n);
-  static bool attr_set = false;
-  if (!attr_set) {
-    PARIS_CUDA(cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(ScatterSmem)));
-    attr_set = true;
-  }
+  // set on every call: the attribute is per device, and a cached flag would not be thread-safe
+  PARIS_CUDA(cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(ScatterSmem)));
   uint64_t* kbuf[2] = {keys, kalt.as<uint64_t>()};
   uint32_t* rbuf[2] = {rows, ralt.as<uint32_t>()};
   for (int pass = 0; pass < 8; ++pass) {
