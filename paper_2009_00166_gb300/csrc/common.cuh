@@ -27,6 +27,9 @@ __device__ __forceinline__ uint64_t double_order_key(double v) {
 
 // RN64(S) * 2^e for a signed 64-bit integer S, built bit by bit (round to nearest even).
 // Requires the result to be a normal double (|S| * 2^e within [2^-1022, 2^1023]).
+// 2^k as a double, exact for -1022 <= k <= 1023.
+__device__ __forceinline__ double exp2_int(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
 __device__ __forceinline__ double fixed_to_double(int64_t S, int e) {
   if (S == 0) return 0.0;
   uint64_t sign = S < 0 ? 0x8000000000000000ull : 0ull;
@@ -263,6 +266,30 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
       done = true;
     } else if (mb == 0u) {
       paa_out = 0.0;
+      done = true;
+    } else if ((mb >> 23) != 0u && (int)((mn + 1u) >> 23) >= 25 && (int)(mb >> 23) <= 250 &&
+               (int)(mb >> 23) - (int)((mn + 1u) >> 23) < 16) {
+      // common case, exponents of the nonzero values within 16 binades, above 2^-102 and below
+      // 2^124 (so that sums of up to 16 values cannot overflow): an fp32
+      // pair (hi, lo) with error-free TwoSum steps holds the sum exactly. Every value, partial
+      // sum and rounding error is a multiple of mu = ulp(smallest value); |lo| <= 8 ulp(max |hi|)
+      // < 2^(emax-142) <= 2^(mu+24) keeps each lo update exact, and no quantity is subnormal.
+      // One FP64 addition of the exact pair then rounds the sum once, as the integer path does.
+      float hi = 0.f, lo = 0.f;
+#pragma unroll
+      for (int v = 0; v < SEGV; ++v) {
+        float4 x = kCache ? cache[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float sum = __fadd_rn(hi, xs[c]);
+          const float bb = __fsub_rn(sum, hi);
+          const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(xs[c], bb));
+          hi = sum;
+          lo = __fadd_rn(lo, err);
+        }
+      }
+      paa_out = __dadd_rn((double)hi, (double)lo) * exp2_int(-sh.log2s);  // s is a power of two here
       done = true;
     } else if ((mb >> 23) != 0u) {
       // values are integer multiples of 2^lambda when no nonzero magnitude is below 2^(lambda+23);
