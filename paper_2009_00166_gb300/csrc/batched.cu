@@ -184,6 +184,29 @@ __device__ __forceinline__ uint32_t row_keep_bits(const uint4& word, bool rv, co
   return rv ? keepmask : 0u;
 }
 
+// Appends one row group's kept (row, query) pairs to the queries' lists; returns the updated
+// overflow bits (bit q: the list of tile slot q passed its capacity). Kept out of line: it runs
+// for few row groups, and inlining it into the unrolled scan loop crowds the instruction cache.
+template <int NP>
+__device__ __noinline__ uint32_t emit_row(uint32_t keepmask, uint32_t any, const uint32_t* sums, int64_t row, int lane,
+                                         const int* s_qid, uint32_t* count, uint32_t* rows, float* lbs, int64_t cap,
+                                         uint32_t ovf, uint32_t* status) {
+  for (int p = 0; p < NP; ++p) {
+    if (!((any >> (2 * p)) & 3u)) continue;
+    const uint32_t sp = sums[p];
+    const __half2 h2 = *reinterpret_cast<const __half2*>(&sp);
+    const float lv[2] = {__low2float(h2) * kHalfKeep, __high2float(h2) * kHalfKeep};
+    for (int j = 0; j < 2; ++j) {
+      const int slot = 2 * p + j, q = s_qid[slot];
+      bool o = (ovf >> slot) & 1u;
+      append_kept(((keepmask >> slot) & 1u) != 0u, row, lv[j], lane, count + q, rows + (int64_t)q * cap,
+                  lbs + (int64_t)q * cap, cap, o, status);
+      ovf |= (o ? 1u : 0u) << slot;
+    }
+  }
+  return ovf;
+}
+
 __device__ __forceinline__ void lane_offsets(int lane, uint32_t (&offp)[8]) {
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -279,9 +302,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
       __syncthreads();
       __half2 thh[NP];
       tile_thresholds<NP>(s_thr, thh);
-      bool ovf[QT];
-#pragma unroll
-      for (int q = 0; q < QT; ++q) ovf[q] = false;
+      uint32_t ovf = 0u;   // bit q: the list of tile slot q passed its capacity
       uint32_t slots = 0;  // slots this warp looked up in this tile, per row group
       for (int64_t it = b0 + (int64_t)wib * kBUnroll; it < b1; it += (int64_t)nw * kBUnroll) {
         uint4 word[kBUnroll];
@@ -298,22 +319,16 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
           const uint32_t keepmask = row_keep_bits<NP>(word[u], rv, offp, tab, thh, sum, slots);
           const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
           if (any) {  // rare: some lane keeps this row for some query of the tile
+            uint32_t sv[NP];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              if (!((any >> (2 * p)) & 3u)) continue;
-              const int qa = s_qid[2 * p], qe = s_qid[2 * p + 1];
-              const float la = __low2float(sum[p]) * kHalfKeep, lbq = __high2float(sum[p]) * kHalfKeep;
-              append_kept(((keepmask >> (2 * p)) & 1u) != 0u, row, la, lane, count + qa,
-                          C.rows + (int64_t)qa * cap, C.lb + (int64_t)qa * cap, cap, ovf[2 * p], status);
-              append_kept(((keepmask >> (2 * p)) & 2u) != 0u, row, lbq, lane, count + qe,
-                          C.rows + (int64_t)qe * cap, C.lb + (int64_t)qe * cap, cap, ovf[2 * p + 1], status);
-            }
+            for (int p = 0; p < NP; ++p) sv[p] = *reinterpret_cast<const uint32_t*>(&sum[p]);
+            ovf = emit_row<NP>(keepmask, any, sv, row, lane, s_qid, count, C.rows, C.lb, cap, ovf, status);
           }
         }
         if (stop_on_overflow) {
           bool all = true;
 #pragma unroll
-          for (int q = 0; q < QT; ++q) all = all && (ovf[q] || s_thr[q] < 0.f);
+          for (int q = 0; q < QT; ++q) all = all && (((ovf >> q) & 1u) || s_thr[q] < 0.f);
           if (all) break;
         }
       }
