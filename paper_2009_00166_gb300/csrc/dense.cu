@@ -44,17 +44,17 @@ constexpr int BM = 128;             // queries per tile (MMA M)
 constexpr int BN = 64;              // series rows per tile (MMA N)
 constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
 constexpr int QTILES = 2;           // query tiles sharing each row tile
-constexpr int STAGES = 3;           // shared-memory ring depth for row tiles
+constexpr int STAGES = 7;           // shared-memory ring depth for row tiles
 constexpr int DENSE_THREADS = 576;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-17: epilogue
 constexpr int EPI_WARPS = 16;       // per TMEM lane quadrant: one per (query tile, 32-row half)
 constexpr int SAMPLE = 16;          // pass 1 visits one row tile in SAMPLE
 constexpr int KMAX = 16;            // largest k the screening supports
-constexpr uint32_t TMEM_COLS = 2 * QTILES * BN;  // double-buffered accumulators of both query tiles
+constexpr uint32_t TMEM_COLS = 512;  // accumulators (2 buffers x 2 query tiles x 64) then the query tiles
+constexpr uint32_t A_COL0 = 2 * QTILES * BN;  // first TMEM column of the query tiles (K/2 columns each)
 constexpr int MAX_KB = 4;           // len <= 256
-constexpr size_t A_TILE_BYTES = (size_t)MAX_KB * BM * 128;
-constexpr size_t A_BYTES = QTILES * A_TILE_BYTES;
+
 constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
-constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * B_STAGE_BYTES + 256;
+constexpr size_t DENSE_SMEM = 1024 + STAGES * B_STAGE_BYTES + 256;
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
 constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
 
@@ -64,6 +64,7 @@ struct DenseParams {
   int qtile, nd;         // nd < 0: the count of screened queries is read from nd_dev
   const int* nd_dev;
   const float2* xnorm;  // [n]: (|x|^2, |x|)
+  const uint32_t* qbf;  // BF16 query rows, [rows][len] (pairs of elements per word)
   const float4* xtile;  // [row tiles]: (min |x|^2, max |x|^2, max |x|, 0) of the tile's rows
   const float2* qnorm;  // [nd_pad]
   const int* qslot;     // [nd]: chunk-local slot of dense query d
@@ -144,6 +145,27 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       : "memory");
 }
 
+// Same MMA with the A operand (the query tile, K-major) read from tensor memory.
+__device__ __forceinline__ void umma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -172,8 +194,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   if (P.qtile * BM >= nd) return;
   const int nq_tiles = (P.qtile + 1) * BM < nd ? 2 : 1;  // query tiles of this launch that hold queries
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* smA = base;
-  uint8_t* smB = base + A_BYTES;
+  uint8_t* smB = base;
   uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
   // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full
   uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
@@ -204,6 +225,34 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  {
+    // the query tiles go to tensor memory once (lane = query row, column j = elements 2j, 2j+1):
+    // warp (quadrant qd, tile c, half h) writes its 32 rows' columns [64h, 64h + 64) of tile c
+    const int w = threadIdx.x >> 5;
+    if (w >= 2) {
+      const int qd = w & 3, c = ((w - 2) >> 2) & 1, h = (w - 2) >> 3;
+      if (c < nq_tiles) {
+        const int64_t grow = (int64_t)(P.qtile + c) * BM + qd * 32 + (threadIdx.x & 31);
+        const uint32_t* src = P.qbf + grow * (P.len / 2);
+        for (int j0 = h * 64; j0 < h * 64 + 64 && j0 < P.len / 2; j0 += 32) {
+          uint32_t v[32];
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            const uint4 q4 = *reinterpret_cast<const uint4*>(src + j0 + j);
+            v[j] = q4.x;
+            v[j + 1] = q4.y;
+            v[j + 2] = q4.z;
+            v[j + 3] = q4.w;
+          }
+          tmem_st32(tmem_base + ((uint32_t)(qd * 32) << 16) + A_COL0 + (uint32_t)(c * (MAX_KB * 32) + j0), v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
   const int64_t ntiles = (P.n + BN - 1) / BN;
   // pass 1 needs the upper ends of any k rows: it visits every SAMPLE-th tile; pass 2 visits all
   const int64_t tstep = (PHASE == 1 ? SAMPLE : 1);
@@ -213,11 +262,6 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer
-      mbar_expect_tx(b_afull, (uint32_t)(nq_tiles * nkb * BM * 128));
-      for (int qt = 0; qt < nq_tiles; ++qt)
-        for (int kb = 0; kb < nkb; ++kb)
-          tma_load_2d(smem_u32(smA + qt * A_TILE_BYTES + (size_t)kb * BM * 128), &tmA, kb * BKE,
-                      (P.qtile + qt) * BM, b_afull);
       int i = 0;
       for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
@@ -235,12 +279,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       const int issued = i;
       for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
         mbar_wait(b_full + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), abort_flag, deadline + 100000000ull);
-      mbar_wait(b_afull, 0u, abort_flag, deadline + 100000000ull);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      bool ok = mbar_wait(b_afull, 0u, abort_flag, deadline);
+      bool ok = true;
       int i = 0;
       for (int64_t t = tfirst; ok && t < ntiles; t += tstride, ++i) {
         const int s = i % STAGES;
@@ -256,12 +299,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
         for (int qt = 0; qt < nq_tiles; ++qt) {
           const uint32_t d_tmem = tmem_base + (uint32_t)((ab * QTILES + qt) * BN);
           for (int kb = 0; kb < nkb; ++kb) {
-            const uint32_t a0 = smem_u32(smA + qt * A_TILE_BYTES + (size_t)kb * BM * 128);
+            const uint32_t a0 = tmem_base + A_COL0 + (uint32_t)(qt * (MAX_KB * 32) + kb * 32);
             const uint32_t b0 = smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)  // 16 BF16 = 32 bytes per MMA step along K
-              umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
-                        (kb | ks) ? 1u : 0u);
+            for (int ks = 0; ks < 4; ++ks)  // 16 BF16 per MMA step along K: 8 columns of A, 32 bytes of B
+              umma_bf16_tmem_a(d_tmem, a0 + 8 * ks, smem_desc_sw128(b0 + 32 * ks), idesc, (kb | ks) ? 1u : 0u);
           }
         }
         umma_commit(b_empty + 8 * s);
@@ -660,6 +702,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   P.nd = nd;
   P.nd_dev = ndev;
   P.xnorm = idx->xnorm;
+  P.qbf = (const uint32_t*)cs.dqbf;
   P.xtile = (const float4*)idx->xtile;
   P.qnorm = cs.dqnm;
   P.qslot = slots;
