@@ -17,14 +17,16 @@
 // that survive get the exact interval above. Pass 1 ranks the looser upper ends
 // ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max), which still bound the distance from above.
 //
-// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries; warp 0 streams
-// 64-row tiles of the BF16 shadow of the series into a 3-stage shared-memory ring with TMA
-// (128-byte swizzle), warp 1 issues the tensor-core MMAs (one thread) of both query tiles
-// against each row tile into double-buffered TMEM accumulators (2 x 2 x 128 x 64 fp32), and
-// warps 2-17 read the accumulators back (tcgen05.ld) and run the screening epilogue: one query
-// per thread and 32 rows of the tile per warp. The epilogue reads each tile's norm range from
-// global memory one tile ahead, and a row's own norms only for the rare pairs that pass the
-// range test. Each row tile read from HBM serves 256 queries.
+// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries in tensor memory
+// (lane = query, K-major BF16 pairs per column, written once with tcgen05.st); warp 0 streams
+// 64-row tiles of the BF16 shadow of the series into a 7-stage shared-memory ring with TMA
+// (128-byte swizzle), warp 1 issues the tensor-core MMAs (one thread; A from tensor memory, B
+// from shared memory) of both query tiles against each row tile into double-buffered TMEM
+// accumulators (2 x 2 x 128 x 64 fp32), and warps 2-17 read the accumulators back (tcgen05.ld)
+// and run the screening epilogue: one query per thread and 32 rows of the tile per warp. The
+// epilogue reads each tile's norm range from global memory two tiles ahead, and a row's own
+// norms only for the rare pairs that pass the range test. Each row tile read from HBM serves
+// 256 queries.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -187,7 +189,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 template <int PHASE>
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
-    dense_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DenseParams P) {
+    dense_kernel(const __grid_constant__ CUtensorMap tmB, DenseParams P) {
   extern __shared__ uint8_t dsm_raw[];
   // a launch for a query tile past the screened queries has nothing to do (uniform per grid)
   const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
@@ -196,12 +198,12 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* smB = base;
   uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
-  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2] | a_full
-  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+  // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2]
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + STAGES), b_accf = smem_u32(bars + 2 * STAGES),
-                 b_acce = smem_u32(bars + 2 * STAGES + 2), b_afull = smem_u32(bars + 2 * STAGES + 4);
+                 b_acce = smem_u32(bars + 2 * STAGES + 2);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_full + 8 * s, 1);
@@ -211,7 +213,6 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       mbar_init(b_accf + 8 * a, 1);
       mbar_init(b_acce + 8 * a, EPI_WARPS);
     }
-    mbar_init(b_afull, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -690,8 +691,6 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   dense_reset_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.count, slots, ndev);
   note_launches(2);
   PARIS_CUDA(cudaGetLastError());
-  CUtensorMap mapA;
-  PARIS_TRY(make_bf16_map(&mapA, cs.dqbf, cs.dq_rows, idx->len, BM));
   // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
   PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
   PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
@@ -724,9 +723,9 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
     for (int t = 0; t < (int)tiles; t += QTILES) {
       P.qtile = t;
       if (phase == 1)
-        dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);
+        dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
       else
-        dense_kernel<2><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(mapA, *mapB, P);
+        dense_kernel<2><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
       note_launches(1);
       PARIS_CUDA(cudaGetLastError());
     }
