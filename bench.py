@@ -208,6 +208,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bind_local_cpus(dev_index):
+    """Runs this process on the CPUs next to the GPU, so that its host buffers (first touched here)
+    sit in the memory the GPU's link reaches directly; returns the CPU count or None."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return len(cpus)
+    except (OSError, ValueError, AttributeError):
+        pass
+    return None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -220,6 +245,7 @@ def main():
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    local_cpus = bind_local_cpus(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -336,9 +362,15 @@ def main():
             times.append(time.perf_counter() - t0)
             idx.free()
         t = sum(times[1:])                                          # first pass warms the allocator
+        # the host link's copy rate, beside it (plain copy of the series, not part of the number)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        X.copy_(host, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = host.numel() * 4 / (time.perf_counter() - c0) / 1e9
         e2e = {"value": nq * args.e2e_steps * world / t, "unit": "queries/s",
                "h2d_bytes_per_step": int(host.numel() * 4 + hq.size * 4),
-               "d2h_bytes_per_step": int(nq * k * 12)}
+               "d2h_bytes_per_step": int(nq * k * 12), "h2d_copy_gbs": h2d_gbs, "host_cpus_bound": local_cpus}
         del hq
 
     # ---- beside it: the plain method (one query per lower-bound pass, fp32 refinement) with the
