@@ -151,7 +151,8 @@ def cpu_baseline(host_np, queries_np, target_s):
 
 
 def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source (the
+    SHA-256 prefix of the kernel's source files, concatenated in the listed order)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -162,8 +163,13 @@ def traffic_for(kernel: str):
     if not d:
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_2009_00166_gb300", "csrc", d["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+    h = hashlib.sha256()
+    for name in d.get("sources", [d.get("source")]):
+        src = os.path.join(ROOT, "paper_2009_00166_gb300", "csrc", name or "")
+        if not name or not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    if h.hexdigest()[:16] != d["source_sha"]:
         return None
     return float(d["bytes_per_launch"]) * (d.get("scale", 1.0))
 
