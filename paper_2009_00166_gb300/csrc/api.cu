@@ -268,9 +268,16 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
   };
   DevBuf scratch_status;
   if (!scratch_status.alloc(4, st)) return fail(PARIS_ENOMEM, "tuning scratch");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  struct Events {  // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  PARIS_CUDA(cudaEventCreate(&ev.a));
+  PARIS_CUDA(cudaEventCreate(&ev.b));
+  const cudaEvent_t e0 = ev.a, e1 = ev.b;
   int best = 2;
   float best_t = 1e30f;
   for (int i = 0; i < kNumQueryTiles; ++i) {
@@ -295,8 +302,6 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
       best = qt;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   for (int j = 0; j < nsub; ++j) PARIS_CUDA(cudaMemsetAsync(cs.count + offs[j], 0, (size_t)m * 4, st));
   // the trial scans' lookups are not the call's (tuning runs before any chunk is scanned)
   PARIS_CUDA(cudaMemsetAsync(qs.counters + 4, 0, 8, st));
