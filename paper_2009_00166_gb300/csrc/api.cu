@@ -398,13 +398,15 @@ static paris_status copy_and_encode(paris_index* idx, const float* host, const R
   int j = 0;
   for (int64_t r0 = 0; r0 < n && s == PARIS_OK; r0 += rows, ++j) {
     const int64_t m = std::min(rows, n - r0);
-    cudaEvent_t done;
+    cudaEvent_t done = nullptr;
     if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemcpyAsync(dst + r0 * len, host + r0 * len, (size_t)m * row_bytes, cudaMemcpyHostToDevice, cs[j & 1]) !=
             cudaSuccess ||
         cudaEventRecord(done, cs[j & 1]) != cudaSuccess || cudaStreamWaitEvent(st, done, 0) != cudaSuccess) {
       cudaGetLastError();
-      return fail(PARIS_ECUDA, "copying the series to the device");
+      if (done) cudaEventDestroy(done);
+      s = fail(PARIS_ECUDA, "copying the series to the device");
+      break;
     }
     cudaEventDestroy(done);
     s = launch_encode(dst + r0 * len, m, sh, idx->card, idx->bits, idx->beta_keys, idx->sax + r0 * PARIS_SAX_BYTES,
@@ -412,6 +414,9 @@ static paris_status copy_and_encode(paris_index* idx, const float* host, const R
                       shb.shadow ? (void*)((uint16_t*)shb.shadow + r0 * len) : nullptr,
                       shb.xnorm ? shb.xnorm + r0 : nullptr);
   }
+  // on failure the caller frees the device copy: no copy may still be writing into it
+  if (s != PARIS_OK)
+    for (int i = 0; i < 2; ++i) cudaStreamSynchronize(cs[i]);
   return s;
 }
 
