@@ -54,3 +54,49 @@ def test_argument_errors_without_gpu(L):
     assert L.paris_breakpoints(100, None) == 1
     assert "power of two" in binding.paris_last_error()
     assert L.paris_exact_knn(None, None, 1, 1, None, None, None) == 1
+
+
+STRUCTS = {
+    "paris_build_opts": ("BuildOpts", ["leaf_capacity", "bf16_shadow", "reserved"]),
+    "paris_query_opts": ("QueryOpts", ["mode", "query_tile", "chunk", "precision", "seed", "reserved"]),
+    "paris_query_stats": ("QueryStats", ["candidates", "refined", "contenders", "leaf_rows", "dense_queries",
+                                         "ms_prep", "ms_descent", "ms_lbscan", "ms_refine", "ms_select", "ms_dense",
+                                         "query_tile", "rescreens", "lb_lookups"]),
+    "paris_knn_plan_stats": ("PlanStats", ["graph_kernels", "replays", "eager_runs", "captured", "query_tile"]),
+    "paris_index_view": ("IndexView", ["n", "len", "w", "card", "leaf_capacity", "series", "keys_sorted",
+                                       "rows_sorted"]),
+}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field offsets (compiled with gcc)."""
+    import shutil
+    import subprocess
+    from paper_2009_00166_gb300 import binding
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "paris.h"', "int main(void) {"]
+    for cname, (_, fields) in STRUCTS.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, what, val = line.split()
+        got[(cname, what)] = int(val)
+    for cname, (pyname, fields) in STRUCTS.items():
+        cls = getattr(binding, pyname)
+        assert C.sizeof(cls) == got[(cname, "size")], cname
+        for f in fields:
+            assert getattr(cls, f).offset == got[(cname, f)], (cname, f)
+
+
+def test_every_declared_function_has_a_signature(L):
+    """The binding declares argument and result types for every entry point of the header."""
+    for n in declared_functions():
+        assert getattr(L, n).argtypes is not None, n
