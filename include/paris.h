@@ -16,7 +16,8 @@
  *     (PARIS_EINVAL otherwise) and are expected to be z-normalised (Sec. 2.1); the library
  *     does not normalise.
  *   - Device memory the library needs is taken from the allocator installed with
- *     paris_set_allocator (default: cudaMallocAsync / cudaFreeAsync on the call's stream).
+ *     paris_set_allocator (default: the library's own stream-ordered pool per device, whose
+ *     freed blocks stay cached until paris_trim_memory).
  */
 #ifndef PARIS_H
 #define PARIS_H
@@ -50,7 +51,8 @@ typedef enum paris_status {
  * that order sharing a key prefix with at most leaf_capacity rows.
  *
  *   series  device or host, [n][len] fp32. Device series are BORROWED: keep them alive and
- *           unchanged until paris_free (refinement reads them). Host series are copied.
+ *           unchanged until paris_free (refinement reads them). Host series are copied into
+ *           an index-owned device array, in chunks that the encode pass consumes as they land.
  *   n       1 <= n < 2^32;  len >= 1;  1 <= w <= 16 with len % w == 0;
  *   card    alphabet size, a power of two in [2, 256] (256 = 8-bit symbols).
  *   out     receives the new index; *out is NULL on failure.
