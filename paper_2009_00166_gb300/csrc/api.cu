@@ -248,14 +248,15 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
       return PARIS_OK;
     }
   }
-  // Trial launches on up to three spread samples of 12 queries (start, middle and end of the
-  // chunk), so the choice sees the chunk's mix of tight and loose thresholds.
+  // Trial launches on up to three spread samples of 24 queries (start, middle and end of the
+  // chunk; 24 fills the largest tile), so the choice sees the chunk's mix of tight and loose
+  // thresholds.
   int offs[3] = {0, 0, 0}, nsub = 1, m = (int)std::min<int64_t>(cs.qc, 24);
-  if (cs.qc >= 36) {
-    m = 12;
+  if (cs.qc >= 72) {
+    m = 24;
     nsub = 3;
-    offs[1] = cs.qc / 2 - 6;
-    offs[2] = cs.qc - 12;
+    offs[1] = cs.qc / 2 - 12;
+    offs[2] = cs.qc - 24;
   }
   auto sub_of = [&](int j) {
     ChunkState sub = cs;
@@ -618,7 +619,7 @@ static paris_status check_query_opts(const paris_index* idx, const paris_query_o
     bool known = false;
     for (int i = 0; i < kNumQueryTiles; ++i) known = known || kQueryTiles[i] == o.query_tile;
     if (!known || !query_tile_fits(o.query_tile, idx->card))
-      return fail(PARIS_EINVAL, "query_tile %d is not one of 2, 4, 8, 12 or does not fit", o.query_tile);
+      return fail(PARIS_EINVAL, "query_tile %d is not one of 2, 4, 8, 12, 16, 24 or does not fit", o.query_tile);
   }
   return PARIS_OK;
 }

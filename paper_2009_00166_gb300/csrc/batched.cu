@@ -3,8 +3,11 @@
 // the 16-byte summaries serves QT queries.
 //
 // Each CTA keeps the tile's lower-bound tables in shared memory as FP16 pairs: one 32-bit word
-// holds the entries of two queries for the same (symbol, segment), so one conflict-free lookup
-// (same rotated layout as the single-query scan) feeds two queries and HADD2 sums both.
+// holds the entries of two queries for the same (symbol, segment), and the words of two pairs
+// sit side by side, so one 64-bit lookup feeds four queries (two HADD2). A lane reads the
+// segment its rotated summary slot names; a 64-bit access is served per half-warp, and the 16
+// lanes of a half read 16 different segments of the same 128-byte region row, so the lookups
+// are conflict-free with a single copy of the tables.
 // Entries are rounded down to FP16 (and capped at 4000) so each stays below the exact
 // contribution; the 16-term FP16 sum has relative error below 16 * 2^-11, so a row is kept when
 // (sum * (1 - 2^-6)) <= threshold, and that scaled value is what is stored as its lower bound.
@@ -83,23 +86,36 @@ __global__ void pack_pairs_kernel(const float* __restrict__ qtable, int qc, int6
 
 // Copies the FP16 pair tables of query tile `qb` into shared memory (two copies per symbol row,
 // one per half-warp) and returns the tile's FP32 thresholds in s_thr (-1: nothing kept).
+// Shared-memory word of (pair p, symbol c, segment i): pairs 2r and 2r+1 form region r; two
+// regions share each 256-byte symbol row of a 64 KB block (region r: block r/2, half r%2); in a
+// region the two pairs' words of a segment are adjacent.
+__host__ __device__ constexpr int table_word(int p, int c, int i) {
+  return (p >> 2) * 16384 + c * 64 + ((p >> 1) & 1) * 32 + i * 2 + (p & 1);
+}
+
+// Copies the FP16 pair tables of query tile `qb` into shared memory and returns the tile's FP32
+// thresholds in s_thr (-1: nothing kept).
 template <int NP>
 __device__ __forceinline__ void load_tile(const uint32_t* __restrict__ packed, int64_t entries, int qb, int qc,
                                           const uint32_t* __restrict__ thr, int64_t q0, const int* __restrict__ perm,
                                           const bool* active, uint32_t* s_tab, float* s_thr) {
-  constexpr int QT = 2 * NP;
+  constexpr int QT = 2 * NP, NR = (NP + 1) / 2;
   const int npairs_chunk = (qc + 1) / 2;
-  for (int64_t e4 = threadIdx.x; e4 < entries * NP / 4; e4 += blockDim.x) {  // 4 entries per thread step
-    const int64_t e = 4 * e4;
-    const int p = (int)(e / entries);
-    const int64_t rem = e - (int64_t)p * entries;
+  // one step: 4 segments of one symbol for both pairs of a region (two 16-byte stores)
+  for (int64_t t = threadIdx.x; t < (int64_t)NR * entries / 4; t += blockDim.x) {
+    const int r = (int)(t / (entries / 4));
+    const int64_t rem = 4 * (t - (int64_t)r * (entries / 4));
     const int c = (int)(rem >> 4), i = (int)(rem & 15);
-    const int pg = qb / 2 + p;  // pair index within the chunk
-    const uint4 word = pg < npairs_chunk ? *reinterpret_cast<const uint4*>(packed + (int64_t)pg * entries + rem)
-                                         : make_uint4(0u, 0u, 0u, 0u);
-    const int w0 = (p >> 1) * 16384 + c * 64 + (p & 1) * 32 + i;
-    *reinterpret_cast<uint4*>(&s_tab[w0]) = word;
-    *reinterpret_cast<uint4*>(&s_tab[w0 + 16]) = word;
+    const int pa = 2 * r, pb = 2 * r + 1;
+    const int ga = qb / 2 + pa, gb = qb / 2 + pb;  // pair indices within the chunk
+    const uint4 A = ga < npairs_chunk ? *reinterpret_cast<const uint4*>(packed + (int64_t)ga * entries + rem)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 B = (pb < NP && gb < npairs_chunk)
+                        ? *reinterpret_cast<const uint4*>(packed + (int64_t)gb * entries + rem)
+                        : make_uint4(0u, 0u, 0u, 0u);
+    const int w0 = table_word(pa, c, i);
+    *reinterpret_cast<uint4*>(&s_tab[w0]) = make_uint4(A.x, B.x, A.y, B.y);
+    *reinterpret_cast<uint4*>(&s_tab[w0 + 4]) = make_uint4(A.z, B.z, A.w, B.w);
   }
   if (threadIdx.x < QT) {
     const int q = qb + threadIdx.x;
@@ -122,7 +138,7 @@ __device__ __forceinline__ void tile_thresholds(const float* s_thr, __half2 (&th
 }
 
 // Adds the FP16 pair entries of slots [K0, K1) of one row to the two summation chains of every
-// pair (even slots to a0, odd slots to a1).
+// pair (even slots to a0, odd slots to a1): one 64-bit lookup per slot and region.
 template <int NP, int K0, int K1>
 __device__ __forceinline__ void add_slots(const uint32_t (&wv)[4], const uint32_t (&offp)[8], uint32_t tab,
                                           __half2 (&a0)[NP], __half2 (&a1)[NP]) {
@@ -133,13 +149,23 @@ __device__ __forceinline__ void add_slots(const uint32_t (&wv)[4], const uint32_
     const uint32_t ad0 = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel0);
     const uint32_t ad1 = tab + __byte_perm(wv[(kk + 1) >> 2], offp[kk >> 1], sel1);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const uint32_t off = (uint32_t)((p >> 1) * 65536 + (p & 1) * 128);
-      uint32_t v0, v1;
-      asm("ld.shared.b32 %0, [%1];" : "=r"(v0) : "r"(ad0 + off));
-      asm("ld.shared.b32 %0, [%1];" : "=r"(v1) : "r"(ad1 + off));
-      a0[p] = __hadd2(a0[p], *reinterpret_cast<__half2*>(&v0));
-      a1[p] = __hadd2(a1[p], *reinterpret_cast<__half2*>(&v1));
+    for (int r = 0; r < (NP + 1) / 2; ++r) {
+      const uint32_t off = (uint32_t)((r >> 1) * 65536 + (r & 1) * 128);
+      if (2 * r + 1 < NP) {
+        uint32_t v0x, v0y, v1x, v1y;
+        asm("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v0x), "=r"(v0y) : "r"(ad0 + off));
+        asm("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v1x), "=r"(v1y) : "r"(ad1 + off));
+        a0[2 * r] = __hadd2(a0[2 * r], *reinterpret_cast<__half2*>(&v0x));
+        a0[2 * r + 1] = __hadd2(a0[2 * r + 1], *reinterpret_cast<__half2*>(&v0y));
+        a1[2 * r] = __hadd2(a1[2 * r], *reinterpret_cast<__half2*>(&v1x));
+        a1[2 * r + 1] = __hadd2(a1[2 * r + 1], *reinterpret_cast<__half2*>(&v1y));
+      } else {  // a region holding one pair
+        uint32_t v0, v1;
+        asm("ld.shared.b32 %0, [%1];" : "=r"(v0) : "r"(ad0 + off));
+        asm("ld.shared.b32 %0, [%1];" : "=r"(v1) : "r"(ad1 + off));
+        a0[2 * r] = __hadd2(a0[2 * r], *reinterpret_cast<__half2*>(&v0));
+        a1[2 * r] = __hadd2(a1[2 * r], *reinterpret_cast<__half2*>(&v1));
+      }
     }
   }
 }
@@ -209,9 +235,9 @@ __device__ __noinline__ uint32_t emit_row(uint32_t keepmask, uint32_t any, const
 
 __device__ __forceinline__ void lane_offsets(int lane, uint32_t (&offp)[8]) {
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    uint32_t o0 = 4u * (16u * (lane >> 4) + ((2 * m + lane) & 15));
-    uint32_t o1 = 4u * (16u * (lane >> 4) + ((2 * m + 1 + lane) & 15));
+  for (int m = 0; m < 8; ++m) {  // byte offset of the lane's segment in a region row, per slot
+    uint32_t o0 = 8u * ((2 * m + lane) & 15);
+    uint32_t o1 = 8u * ((2 * m + 1 + lane) & 15);
     offp[m] = o0 | (o1 << 16);
   }
 }
@@ -445,9 +471,8 @@ __global__ void pilot_route_kernel(const uint32_t* __restrict__ pilot, int qc, i
 }
 
 size_t batched_smem(int np, int card) {
-  const int regions = (np + 1) / 2;
-  // region r spans 64 KB of 256-byte symbol rows; the last region only needs card rows
-  return (size_t)(regions - 1) * 65536 + (size_t)card * 256;
+  const int blocks = (np + 3) / 4;  // 64 KB blocks of 256-byte symbol rows, two regions each
+  return (size_t)(blocks - 1) * 65536 + (size_t)card * 256;
 }
 
 // Row groups (32 rows) per CTA row block. By default a CTA's whole row range is one block: every
@@ -587,7 +612,7 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
 
 }  // namespace
 
-const int kQueryTiles[kNumQueryTiles] = {2, 4, 8, 12};
+const int kQueryTiles[kNumQueryTiles] = {2, 4, 8, 12, 16, 24};
 
 bool query_tile_fits(int qt, int card) { return batched_smem(qt / 2, card) <= 200 * 1024; }
 
@@ -601,7 +626,9 @@ paris_status launch_lbscan_batched_multi(const ScanJob* jobs, int m, int qt, cud
     case 4: return launch_np<2>(jobs, m, st);
     case 8: return launch_np<4>(jobs, m, st);
     case 12: return launch_np<6>(jobs, m, st);
-    default: return fail(PARIS_EINVAL, "query_tile must be one of 2, 4, 8, 12 (got %d)", qt);
+    case 16: return launch_np<8>(jobs, m, st);
+    case 24: return launch_np<12>(jobs, m, st);
+    default: return fail(PARIS_EINVAL, "query_tile must be one of 2, 4, 8, 12, 16, 24 (got %d)", qt);
   }
 }
 

@@ -69,7 +69,7 @@ paris_status launch_lbscan_threshold(const paris_index* idx, const float* table,
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st);
 // Batched lower-bound scan (batched.cu): one persistent launch for a chunk, tiles of qt queries.
-constexpr int kNumQueryTiles = 4;
+constexpr int kNumQueryTiles = 6;
 extern const int kQueryTiles[kNumQueryTiles];
 bool query_tile_fits(int qt, int card);
 paris_status launch_lbscan_batched(const paris_index* idx, const QueryState& qs, const ChunkState& cs, int qt,

@@ -34,13 +34,13 @@ def run(P, idx, q, k, **kw):
     return i.cpu().numpy(), d.cpu().numpy(), st
 
 
-@pytest.mark.parametrize("qt", [0, 2, 4, 8, 12])
+@pytest.mark.parametrize("qt", [0, 2, 4, 8, 12, 16, 24])
 @pytest.mark.parametrize("k", [1, 10])
 def test_batched_equals_oracle(setup, qt, k):
     P, idx, q, want = setup
     for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
         gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=prec)
-        assert st["query_tile"] in (2, 4, 8, 12) and (qt == 0 or st["query_tile"] == qt)
+        assert st["query_tile"] in (2, 4, 8, 12, 16, 24) and (qt == 0 or st["query_tile"] == qt)
         # at most 16 slots per row group and query pair (a CTA's range end may add a few
         # partial unrolled steps)
         full = 16 * (st["query_tile"] // 2) * 32 * ((x_rows(idx) + 31) // 32) * (-(-len(q) // st["query_tile"]))
