@@ -150,14 +150,16 @@ def cpu_baseline(host_np, queries_np, target_s):
                       f"time scaled by {n / rows:.3g} to the full collection; {t:.1f} s of CPU work"}
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, query_tile: int = 0):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source (the
-    SHA-256 prefix of the kernel's source files, concatenated in the listed order)."""
+    SHA-256 prefix of the kernel's source files, concatenated in the listed order) and, for the
+    batched scan, with the same query tile."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path)).get(kernel)
+        table = json.load(open(path))
+        d = table.get(f"{kernel}@qt{query_tile}") if query_tile else table.get(kernel)
     except Exception:
         return None
     if not d:
@@ -516,7 +518,7 @@ def main():
         peak_l = 32.0 * 152 * clk_mhz * 1e6 / 1e9
         roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
                 "unit": "G shared-memory lookups/s", "frac": ach / peak_l,
-                "traffic": traffic_for("lbscan_batched_kernel"),
+                "traffic": traffic_for("lbscan_batched_kernel", qt_used),
                 "lookups_per_step": lookups / steps,
                 "query_tile": qt_used,
                 "summaries_read_per_step_gb_at_most": 16.0 * n * (-(-nq // max(1, qt_used))) / 1e9,

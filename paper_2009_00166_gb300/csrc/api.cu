@@ -298,7 +298,9 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
       total += ms;
     }
     const float per_query = total / (float)(m * nsub);
-    if (per_query < best_t) {
+    // tiles are tried from small to large; a larger tile within 3% of the best so far wins
+    // (fewer passes over the summaries, and a stable choice when trial timings are this close)
+    if (per_query < best_t * 1.03f) {
       best_t = per_query;
       best = qt;
     }
