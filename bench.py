@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--train-epochs", type=int, default=10)
     p.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain fp32 method shown beside")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--query-tile", type=int, default=0,
+                   help="queries per batched summary pass (0: the library tunes it)")
     p.add_argument("--graph-steps", type=int, default=3,
                    help="timed replays of the captured batch (index built once) shown beside")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
@@ -312,7 +314,8 @@ def main():
             P.paris_attach_seed_model(idx, model, 3)
         per_sigma_stats = []
         for g in (groups if split else [Q]):
-            out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, seed=sd, want_stats=collect is not None)
+            out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, seed=sd, want_stats=collect is not None,
+                                       query_tile=args.query_tile if md == P.PARIS_MODE_BATCHED else 0)
             if collect is not None:
                 per_sigma_stats.append(out[2])
             if answers is not None:
