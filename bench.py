@@ -16,6 +16,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -50,6 +51,7 @@ def parse():
                    help="timed replays of the captured batch (index built once) shown beside")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--clocks-csv", default="", help="keep the raw nvidia-smi clock samples of the timed region here")
     return p.parse_args()
 
 
@@ -74,9 +76,14 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+    def __init__(self, gpu_index: int, path: str | None = None):
+        if path:
+            self.path = path
+            os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        else:
+            fd, self.path = tempfile.mkstemp(prefix=f"clocks_bench_{gpu_index}_", suffix=".csv")
+            os.close(fd)
+        self.temporary = not path
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -86,6 +93,8 @@ class Clocks:
 
     def stop(self):
         if not self.proc:
+            if self.temporary:
+                os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         self.proc.wait()
@@ -103,6 +112,8 @@ class Clocks:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        if self.temporary:
+            os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm.sort()
@@ -333,7 +344,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_csv)
     launches0 = P.paris_kernel_launches()
     recs = []
     torch.cuda.synchronize()
