@@ -163,10 +163,10 @@ def cpu_baseline(host_np, queries_np, target_s):
                       f"time scaled by {n / rows:.3g} to the full collection; {t:.1f} s of CPU work"}
 
 
-def traffic_for(kernel: str, query_tile: int = 0):
+def traffic_for(kernel: str, query_tile: int = 0, workload: dict | None = None):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source (the
-    SHA-256 prefix of the kernel's source files, concatenated in the listed order) and, for the
-    batched scan, with the same query tile."""
+    SHA-256 prefix of the kernel's source files, concatenated in the listed order), for the same
+    workload sizes and, for the batched scan, with the same query tile."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -176,6 +176,8 @@ def traffic_for(kernel: str, query_tile: int = 0):
     except Exception:
         return None
     if not d:
+        return None
+    if any((workload or {}).get(key) != val for key, val in d.get("workload", {}).items()):
         return None
     import hashlib
     h = hashlib.sha256()
@@ -510,6 +512,7 @@ def main():
     refine_bytes_total = refined * (length * 4.0) + cands * 12.0
     refine_gbs = refine_bytes_total / (ph["refine"] * 1e-3) / 1e9 if ph["refine"] > 0 else 0.0
     dominant = max(ph, key=ph.get)
+    wl = {"n": n, "len": length, "queries": nq}    # committed DRAM counters hold only at their own sizes
     if dominant == "dense":
         # algorithmic work of the BF16 screening: two passes (threshold, emission) of 2*len flops
         # per (query, row) pair over the dense queries
@@ -517,10 +520,10 @@ def main():
         tf = flops / (ph["dense"] * 1e-3) / 1e12
         peak_tf = bf16_peak_sustained()
         roof = {"kernel": "dense_kernel", "bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": tf / peak_tf, "traffic": traffic_for("dense_kernel")}
+                "frac": tf / peak_tf, "traffic": traffic_for("dense_kernel", 0, wl)}
     elif dominant == "refine":
         roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel")}
+                "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel", 0, wl)}
     elif args.mode == "batched":
         # the batched scan is bound by shared-memory table lookups: one 32-bit lookup per lane,
         # slot and query pair, counted by the library (early-abandoned slots are not looked up);
@@ -532,14 +535,14 @@ def main():
         peak_l = 32.0 * 152 * clk_mhz * 1e6 / 1e9
         roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
                 "unit": "G shared-memory lookups/s", "frac": ach / peak_l,
-                "traffic": traffic_for("lbscan_batched_kernel", qt_used),
+                "traffic": traffic_for("lbscan_batched_kernel", qt_used, wl),
                 "lookups_per_step": lookups / steps,
                 "query_tile": qt_used,
                 "summaries_read_per_step_gb_at_most": 16.0 * n * (-(-nq // max(1, qt_used))) / 1e9,
                 "note": "time includes the pilot pass and the query ordering; lookups counted on the device"}
     else:
         roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel")}
+                "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel", 0, wl)}
     roof["peak_kind"] = peak_kind
     value = job_rate
     line = {

@@ -29,3 +29,16 @@ def test_reference_arm_other_ranks_exit_quietly():
                           "--per-sigma", "3", "--steps", "1", "--warmup", "0"],
                          capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_dram_traffic_only_for_the_sizes_and_source_it_was_taken_on():
+    sys.path.insert(0, ROOT)
+    import bench
+    table = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for key, entry in table.items():
+        kernel, _, qt = key.partition("@qt")
+        wl = dict(entry.get("workload", {}))
+        wl.setdefault("queries", 3000)
+        got = bench.traffic_for(kernel, int(qt or 0), wl)
+        assert got is None or abs(got - entry["bytes_per_launch"] * entry.get("scale", 1.0)) < 1.0
+        assert bench.traffic_for(kernel, int(qt or 0), dict(wl, n=wl.get("n", 0) + 16)) is None
