@@ -267,13 +267,17 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
     } else if (mb == 0u) {
       paa_out = 0.0;
       done = true;
-    } else if ((mb >> 23) != 0u && (int)((mn + 1u) >> 23) >= 25 && (int)(mb >> 23) <= 250 &&
-               (int)(mb >> 23) - (int)((mn + 1u) >> 23) < 16) {
-      // common case, exponents of the nonzero values within 16 binades, above 2^-102 and below
-      // 2^124 (so that sums of up to 16 values cannot overflow): an fp32
-      // pair (hi, lo) with error-free TwoSum steps holds the sum exactly. Every value, partial
-      // sum and rounding error is a multiple of mu = ulp(smallest value); |lo| <= 8 ulp(max |hi|)
-      // < 2^(emax-142) <= 2^(mu+24) keeps each lo update exact, and no quantity is subnormal.
+    } else if ((mb >> 23) != 0u && (int)((mn + 1u) >> 23) >= 25 && (int)(mb >> 23) <= 253 - sh.log2s &&
+               (int)(mb >> 23) - (int)((mn + 1u) >> 23) <= 24 - 2 * sh.log2s) {
+      // common case: an fp32 pair (hi, lo) with error-free TwoSum steps holds the sum exactly.
+      // With s = 2^L values whose nonzero biased exponents lie in [emin, emax]:
+      //  * every value, partial sum and TwoSum error is a multiple of mu = 2^(emin-150) (the ulp
+      //    of the smallest value), and any multiple of mu of magnitude <= 2^24 mu is an fp32 value;
+      //  * |hi| < 2^(emax-126+L), so each error is at most 2^(emax-150+L) and the s-1 nonzero
+      //    errors sum to less than 2^(emax-150+2L) <= 2^24 mu when emax - emin <= 24 - 2L: every
+      //    lo update is then exact (span <= 16 binades at s = 16, 12 at s = 64, 10 at s = 128);
+      //  * emax <= 253 - L keeps every partial sum below the fp32 overflow threshold, and
+      //    emin >= 25 keeps mu and every error above the subnormal range.
       // One FP64 addition of the exact pair then rounds the sum once, as the integer path does.
       float hi = 0.f, lo = 0.f;
 #pragma unroll

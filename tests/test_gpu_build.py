@@ -3,6 +3,7 @@ Bit-exact: symbols, keys, sorted order, and the FP64 PAA values themselves."""
 import numpy as np
 import pytest
 
+import planted
 from gpu_common import require_gpu, rw, small_dataset, torch
 from oracle import index as oindex
 from oracle import isax
@@ -50,6 +51,43 @@ def test_encode_tiny_and_exact_values():
     x[9, 32:48] = np.float32(3.0e38)        # large but finite
     x[9, 48:64] = np.float32(-3.0e38)
     check_encode(x, 16, 256)
+
+
+@pytest.mark.parametrize("length", [512, 1024, 2048, 4096])
+def test_encode_planted_exactness(length):
+    """Segments built to break a summation that drops low bits (w = 16, so s = len / 16 values
+    per segment): the wide-span pattern 1.9999999 / 2^-15+2^-18-2^-38 in four orders and signs,
+    random segments at exponent spans around every span limit a TwoSum argument could use, and
+    segments whose exact mean lies less than 2^-38/s below the breakpoints 64, 128, 160, 192.
+    The PAA bytes must equal the correctly rounded segment sums / s, and the symbols must be
+    the lower region's."""
+    s = length // 16
+    lg = s.bit_length() - 1
+    rng = np.random.default_rng(length)
+    x = rw(96, length, 40 + length)
+    r = 0
+    for variant in range(4):
+        for seg in (0, 7, 15):
+            x[r, seg * s:(seg + 1) * s] = planted.wide_span(s, rng, variant)
+            r += 1
+    for span in sorted({24 - 2 * lg - 1, 24 - 2 * lg, 24 - 2 * lg + 1, 10, 12, 15, 16}):
+        for _ in range(3):
+            seg = int(rng.integers(16))
+            x[r, seg * s:(seg + 1) * s] = planted.gate(s, span, rng)
+            r += 1
+    beta = isax.breakpoints(256)
+    near = []
+    for j in (64, 128, 160, 192):
+        for order in ("plain", "reversed", "shuffled"):
+            seg = int(rng.integers(16))
+            x[r, seg * s:(seg + 1) * s] = planted.below_breakpoint(beta[j - 1], s, order, seed=j)
+            near.append((r, seg, j - 1))
+            r += 1
+    assert r <= x.shape[0]
+    check_encode(x, 16, 256)
+    sax, _, _ = encode_gpu(x, 16, 256)
+    for row, seg, sym in near:
+        assert sax[row, seg] == sym
 
 
 def test_encode_rejects_nonfinite():

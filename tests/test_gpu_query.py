@@ -4,6 +4,7 @@ approximate-search leaves, the lower-bound candidate sets, ties, host buffers an
 import numpy as np
 import pytest
 
+import planted
 from gpu_common import require_gpu, rw, small_dataset, torch
 from oracle import index as oindex
 from oracle import isax
@@ -195,3 +196,33 @@ def test_bad_queries_rejected(built):
         run_knn(idx, q, 1)
     gi, _ = run_knn(idx, q[:0], 1)
     assert gi.shape == (0, 1)
+
+
+@pytest.mark.parametrize("length", [1024, 2048])
+def test_query_prep_planted_exactness(length):
+    """Query PAA (Sec. 3.3.1 query preparation) on queries whose segment 0 has an exact mean just
+    below breakpoint 64, 128, 160 or 192: the query word, hence its key and the approximate
+    search's leaf, must be the lower region's, and the answers exact."""
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    s = length // 16
+    x = rw(8000, length, 60 + length)
+    q = rw(12, length, 61 + length)
+    beta = isax.breakpoints(256)
+    for t in range(12):
+        j = (192, 160, 128, 64)[t % 4]
+        order = ("plain", "reversed", "shuffled")[t // 4]
+        q[t, :s] = planted.below_breakpoint(beta[j - 1], s, order, seed=t)
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    sax = isax.isax_words(x, 16, 256)
+    _, keys = oindex.sort_order(isax.key64(sax, 256))
+    leaf, _ = P.paris_approx_search(idx, torch.from_numpy(q).to(dev), 1)
+    leaf = leaf.cpu().numpy()
+    for t in range(q.shape[0]):
+        word = isax.symbols(isax.paa(q[t], 16)[0], 256)
+        assert word[0] == (192, 160, 128, 64)[t % 4] - 1
+        qkey = isax.key128(word, 256) >> 64
+        assert tuple(leaf[t]) == oindex.leaf_range(keys, qkey, 2048, 1)
+    gi, gd = run_knn(idx, q, 3)
+    assert_matches(x, q, 3, gi, gd)
+    idx.free()

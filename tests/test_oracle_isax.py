@@ -80,6 +80,28 @@ def test_paa_is_exact_sum_rounded_once():
     assert p[7, 0] == (1.0 + 2.0 ** -20) / 8
 
 
+def test_paa_planted_segments_exact():
+    """Segments whose sum needs every low bit (the planted inputs of the GPU exactness tests):
+    the oracle's PAA equals the Fraction sum rounded once / s, and a segment whose exact mean
+    sits less than 2^-38/s below breakpoint j takes symbol j - 1."""
+    import planted
+    beta = isax.breakpoints(256)
+    rng = np.random.default_rng(3)
+    for s in (32, 64, 128, 256):
+        rows = [planted.wide_span(s, rng, v) for v in range(4)]
+        rows += [planted.gate(s, span, rng) for span in (10, 12, 15, 16)]
+        for j in (64, 128, 160, 192):
+            for order in ("plain", "reversed", "shuffled"):
+                v = planted.below_breakpoint(beta[j - 1], s, order, seed=j)
+                gap = Fraction(float(beta[j - 1])) - planted.exact_mean(v)
+                assert 0 < gap <= Fraction(2) ** -38 / s
+                p = isax.paa(v[None, :], 1)[0, 0]
+                assert isax.symbols(np.array([p]), 256)[0] == j - 1
+                rows.append(v)
+        for v in rows:
+            assert isax.paa(v[None, :], 1)[0, 0] == float(planted.exact_mean(v) * s) / s
+
+
 def test_symbols_brute_force_and_monotone():
     rng = np.random.default_rng(3)
     card = 256
