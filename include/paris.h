@@ -284,6 +284,12 @@ paris_status paris_seed_model_get_weights(const paris_seed_model* model, float* 
 /* logits (device [m][4096]) of device PAA inputs [m][16]. */
 paris_status paris_seed_model_forward(const paris_seed_model* model, const double* paa, int64_t m, float* logits,
                                       void* stream);
+/* The top_r (1..8) highest-scoring buckets of each input, best first, equal logits ranked by
+ * lower bucket: the selection the learned proposal makes before the approximate search of
+ * Sec. 3.3 visits those buckets' leaves (PARIS_SEED_LEARNED). paa device FP64 [m][16],
+ * out_buckets device int32 [m][top_r]. Waits on `stream` before returning. */
+paris_status paris_seed_model_topr(const paris_seed_model* model, const double* paa, int64_t m, int32_t top_r,
+                                   int32_t* out_buckets, void* stream);
 /* Mean cross-entropy of one batch (device paa [m][16], labels [m]) and its gradients (device
  * [PARIS_SEED_MODEL_PARAMS], parameter order above); *loss_host may be NULL. No update. */
 paris_status paris_seed_model_gradients(const paris_seed_model* model, const double* paa, const int32_t* labels,
@@ -320,6 +326,8 @@ paris_status paris_row_buckets(const paris_index* idx, const int64_t* rows, int6
  * array; larger requests fail with PARIS_EINVAL and a message naming the limit.
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * Every call waits on `stream` before it returns: the per-query counts are copied back to the
+ * host through a stack buffer.
  * Sharing: all calls share the one array and it keeps the previous call's contents (the call
  * clears what must start at zero). Calls that overlap on the GPU -- on different streams or
  * from different threads -- race on it and must not be issued.

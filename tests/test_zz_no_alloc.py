@@ -83,3 +83,33 @@ def test_noalloc_counts_only_and_limit(setup):
     st = L.paris_lb_scan_noalloc(idx.handle, Q.data_ptr(), 64, th.ctypes.data, None, None, 0, counts.ctypes.data,
                                  torch.cuda.current_stream().cuda_stream)
     assert st == 1 and "static scratch" in P.paris_last_error()
+
+
+def test_noalloc_calls_no_allocator(setup):
+    """The defining property: with a counting allocator installed (every library allocation goes
+    through it), paris_lb_scan allocates and paris_lb_scan_noalloc does not."""
+    P, idx, x, qa, _ = setup
+    thr = thresholds(P, idx, qa)
+    noalloc(P, idx, qa, thr, 16)                          # device set-up done before counting
+    calls = {"alloc": 0, "free": 0}
+
+    def alloc(nbytes, stream, _ctx):
+        calls["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+
+    def free(ptr, _nbytes, _stream, _ctx):
+        calls["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    P.paris_set_allocator(alloc, free)
+    try:
+        P.paris_lb_scan(idx, torch.from_numpy(qa[0]).cuda(), float(thr[0]))
+        torch.cuda.synchronize()
+        assert calls["alloc"] > 0                           # the counter sees the library
+        calls["alloc"] = calls["free"] = 0
+        for _ in range(2):
+            _, _, counts = noalloc(P, idx, qa, thr, x.shape[0])
+            assert counts.sum() > 0
+        assert calls == {"alloc": 0, "free": 0}
+    finally:
+        P.paris_set_allocator(None, None)
