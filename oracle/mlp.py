@@ -85,8 +85,15 @@ def adamw_step(params, grads, state, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, we
     return out
 
 
-def topr_buckets(params, x, r):
-    """The r highest-scoring buckets per row (ties by lower bucket)."""
-    logits, _ = forward(params, x)
-    order = np.lexsort((np.arange(logits.shape[1])[None, :].repeat(logits.shape[0], 0), -logits), axis=1)
+def topr_of_logits(logits, r):
+    """The r highest-scoring buckets of each row of a logit matrix [B][4096], best first; equal
+    logits are ranked by lower bucket (a stable sort on the negated scores)."""
+    logits = np.asarray(logits)
+    order = np.argsort(-logits, axis=1, kind="stable")
     return order[:, :r]
+
+
+def topr_buckets(params, x, r):
+    """The r highest-scoring buckets per row of the network's logits (ties by lower bucket)."""
+    logits, _ = forward(params, x)
+    return topr_of_logits(logits, r)

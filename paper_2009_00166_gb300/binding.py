@@ -107,6 +107,7 @@ def lib():
             "paris_seed_model_get_weights": ([VP, P, VP], I32),
             "paris_seed_model_forward": ([VP, P, I64, P, VP], I32),
             "paris_seed_model_gradients": ([VP, P, P, I32, P, C.POINTER(F32), VP], I32),
+            "paris_seed_model_topr": ([VP, P, I64, I32, P, VP], I32),
             "paris_seed_model_train": ([VP, P, P, I64, I32, I32, F32, F32, C.c_uint64, P, VP], I32),
             "paris_attach_seed_model": ([VP, VP, I32], I32),
             "paris_row_buckets": ([VP, P, I64, P, VP], I32),
@@ -423,6 +424,14 @@ class SeedModel:
         m = int(paa.shape[0])
         out = torch.empty((m, 4096), dtype=torch.float32, device=paa.device)
         _check(lib().paris_seed_model_forward(self.handle, _ptr(paa), m, _ptr(out), _stream(None)))
+        return out
+
+    def topr(self, paa, r: int):
+        """paris_seed_model_topr on device FP64 PAA [m][16]: device int32 buckets [m][r]."""
+        import torch
+        m = int(paa.shape[0])
+        out = torch.empty((m, r), dtype=torch.int32, device=paa.device)
+        _check(lib().paris_seed_model_topr(self.handle, _ptr(paa), m, r, _ptr(out), _stream(None)))
         return out
 
     def gradients(self, paa, labels):

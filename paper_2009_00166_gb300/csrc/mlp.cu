@@ -548,6 +548,34 @@ paris_status paris_seed_model_forward(const paris_seed_model* md, const double* 
   return PARIS_OK;
 }
 
+paris_status paris_seed_model_topr(const paris_seed_model* md, const double* paa, int64_t m, int32_t r,
+                                   int32_t* out_buckets, void* stream) {
+  clear_error();
+  if (!md || (m > 0 && (!paa || !out_buckets))) return fail(PARIS_EINVAL, "NULL argument");
+  if (r < 1 || r > 8) return fail(PARIS_EINVAL, "top_r must be in [1, 8]");
+  if (m < 0) return fail(PARIS_EINVAL, "m < 0");
+  if (m == 0) return PARIS_OK;
+  if (!is_device_ptr(paa) || !is_device_ptr(out_buckets))
+    return fail(PARIS_EINVAL, "paa and out_buckets must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace ws;
+  const int B = 1024;
+  PARIS_TRY(ws.alloc(B, st));
+  DevBuf xf;
+  if (!xf.alloc((size_t)m * 16 * 4, st)) return fail(PARIS_ENOMEM, "inputs");
+  paa_to_f32_kernel<<<(unsigned)((m * 16 + 255) / 256), 256, 0, st>>>(paa, m, xf.as<float>());
+  note_launches(1);
+  for (int64_t b0 = 0; b0 < m; b0 += B) {
+    const int nb = (int)std::min<int64_t>(B, m - b0);
+    forward(md, xf.as<float>() + b0 * 16, nb, ws, st);
+    topr_kernel<<<(nb + 7) / 8, 256, 0, st>>>(ws.lg, nb, paris_seed_model::OUT, r, out_buckets + b0 * r);
+    note_launches(1);
+  }
+  PARIS_CUDA(cudaGetLastError());
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  return PARIS_OK;
+}
+
 paris_status paris_seed_model_gradients(const paris_seed_model* md, const double* paa, const int32_t* labels, int32_t m,
                                         float* grads, float* loss_host, void* stream) {
   clear_error();

@@ -71,3 +71,26 @@ def test_training_lowers_loss():
         _, g = mlp.loss_and_grads(p, x, y)
         p = mlp.adamw_step(p, g, st, t, lr=3e-3)
     assert mlp.loss_and_grads(p, x, y)[0] < 0.5 * l0
+
+
+def test_topr_brute_force_with_ties():
+    """Top-r buckets against a brute-force ordering by (score descending, bucket ascending), on
+    logits with planted ties (equal scores, +0 and -0, a tie straddling the r-th place)."""
+    rng = np.random.default_rng(11)
+    L = rng.standard_normal((6, 4096)).astype(np.float32)
+    L[0, [5, 900, 4095]] = 9.0                      # a three-way tie for first place
+    L[1, :] = 0.0                                   # all tied: the lowest buckets win
+    L[2, [3, 7]] = [0.0, -0.0]
+    L[2, :] = np.minimum(L[2, :], 0.0)
+    L[3, [10, 20, 30, 40]] = 5.0                    # tie across the r-th place (r = 3)
+    L[4, ::2] = L[4, 1::2]                          # every even bucket ties with its right neighbour
+    for r in (1, 3, 8):
+        got = mlp.topr_of_logits(L, r)
+        for b in range(L.shape[0]):
+            want = sorted(range(4096), key=lambda i: (-float(L[b, i]), i))[:r]
+            assert got[b].tolist() == want
+    assert mlp.topr_of_logits(L, 3)[3].tolist() == [10, 20, 30]
+    assert mlp.topr_of_logits(L, 3)[1].tolist() == [0, 1, 2]
+    p = small_params(4)
+    x = rng.standard_normal((3, 16))
+    assert np.array_equal(mlp.topr_buckets(p, x, 4), mlp.topr_of_logits(mlp.forward(p, x)[0], 4))
