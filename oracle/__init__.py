@@ -10,7 +10,8 @@ Modules
   isax   -- breakpoints, PAA, iSAX symbols, the interleaved key, MINDIST (Sec. 2.2, 3.3.1)
   knn    -- exact k-NN by brute force with exact integer re-ranking of near ties (Sec. 2.1)
   index  -- sorted-key order, approximate-search leaf and seed (Sec. 3.3), LB candidate set
-            (Alg. 8), the full exact search driver (Alg. 7)
+            (Alg. 8), page envelopes and their box MINDIST (leaf pruning), the full exact
+            search driver (Alg. 7)
   mlp    -- the learned best-so-far proposal network (forward, backward, AdamW), FP64
 
 Parity pinning: every function is checked by ``tests/test_oracle_*.py`` against values fixed by

@@ -9,6 +9,10 @@ Passages followed (ParIS+ paper):
   Alg. 9 (RDC worker): for each kept pair still under BSF, compute the real distance and lower
     BSF when smaller.  Alg. 7 ties these steps together.
 
+  Leaf pruning (ADS+ leaves; applied to in-memory leaves by the MESSI follow-up): every series
+    under a tree node has, per segment, a symbol inside the node's range, so the MINDIST from
+    the query to the node's box of regions bounds the MINDIST of each of its series.
+
 Readings (also in the design notes):
   * the tree is the fixed-order trie over the bit-plane interleaved key (top 64 bits) stored as
     a sorted array ordered by (key, row); a trie node at depth l is the run of keys sharing
@@ -18,7 +22,10 @@ Readings (also in the design notes):
     anchor with at most L' = max(L, k) rows; if it holds fewer than k rows the leaf becomes the k
     consecutive sorted positions starting at its first position (shifted left to fit); if even
     depth 64 holds more than L' rows the leaf is the first L' rows of that node;
-  * for k-NN the BSF is the k-th best distance; ties keep the lower row.
+  * for k-NN the BSF is the k-th best distance; ties keep the lower row;
+  * the pruned units are pages of a fixed number of consecutive rows of the index order (each
+    page lies inside the trie node of its common key prefix); a page's box is the per-segment
+    range of its rows' symbols.
 """
 from __future__ import annotations
 
@@ -73,6 +80,38 @@ def approx_seed(X, rows_sorted, leaf, q, k):
     rows = np.sort(rows_sorted[lo:hi])
     ex = sorted((knn.exact_sq_int(X[r], q), int(r)) for r in rows)
     return ex[k - 1][0], rows
+
+
+def page_envelopes(sax_in_order: np.ndarray, page_rows: int):
+    """Per page of `page_rows` consecutive rows of the index order: the smallest and the largest
+    symbol of every segment (the page's box of iSAX regions). Returns (lo, hi), [pages][w]."""
+    sym = np.asarray(sax_in_order, dtype=np.int64)
+    N, w = sym.shape
+    pages = (N + page_rows - 1) // page_rows
+    lo = np.empty((pages, w), dtype=np.int64)
+    hi = np.empty((pages, w), dtype=np.int64)
+    for p in range(pages):
+        blk = sym[p * page_rows:(p + 1) * page_rows]
+        lo[p] = blk.min(axis=0)
+        hi[p] = blk.max(axis=0)
+    return lo, hi
+
+
+def box_mindist_sq(paa_q, lo, hi, n: int, card: int) -> np.ndarray:
+    """MINDIST^2 from a query PAA to boxes of iSAX regions (Sec. 2.2 ADS+ nodes and leaves cover
+    a region per segment; Sec. 3.3.1's three branches per segment): segment i of a box spans
+    symbols lo_i..hi_i, i.e. [beta_lo(lo_i), beta_hi(hi_i)]; d_i is the distance from PAA_i to
+    that interval (BELOW / ABOVE / IN), and the bound is (n/w) * sum_i d_i^2."""
+    beta = isax.breakpoints(card)
+    ext = np.concatenate(([-np.inf], beta, [np.inf]))
+    lo = np.atleast_2d(np.asarray(lo, dtype=np.int64))
+    hi = np.atleast_2d(np.asarray(hi, dtype=np.int64))
+    w = lo.shape[1]
+    left = ext[lo]
+    right = ext[hi + 1]
+    p = np.asarray(paa_q, dtype=np.float64)[None, :]
+    d = np.where(p < left, left - p, np.where(p > right, p - right, 0.0))
+    return (n / w) * (d * d).sum(axis=1)
 
 
 def candidates(paa_q, sax, n, card, bsf_sq: float):

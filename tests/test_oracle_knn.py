@@ -125,3 +125,55 @@ def test_exact_search_reaches_brute_force(k):
         assert res["seed_sq"] >= want[1][t][-1] ** 2 * (1 - 1e-12)
         # pruning never removes an answer row
         assert set(want[0][t].tolist()) <= set(res["candidates"].tolist())
+
+
+def test_box_mindist_hand_value_and_special_cases():
+    """MINDIST to a box of iSAX regions: a hand-computed 2-segment, 4-symbol case; a box of one
+    word equals that word's MINDIST; a box spanning every symbol gives 0."""
+    from statistics import NormalDist
+    b1 = NormalDist().inv_cdf(0.25)                      # breakpoints -0.674.., 0, 0.674..
+    # segment 0 spans symbols 0..1 (PAA <= 0): PAA 1.0 lies 1.0 above it;
+    # segment 1 spans symbols 1..3 (PAA >= b1): PAA -1.0 lies b1 + 1.0 below it
+    got = index.box_mindist_sq(np.array([1.0, -1.0]), [[0, 1]], [[1, 3]], 8, 4)[0]
+    want = (8 / 2) * (1.0 ** 2 + (b1 - (-1.0)) ** 2)
+    assert abs(got - want) <= 1e-15 * want
+    rng = np.random.default_rng(4)
+    words = rng.integers(0, 256, (50, 16))
+    paa_q = rng.standard_normal(16)
+    assert np.array_equal(index.box_mindist_sq(paa_q, words, words, 256, 256),
+                          isax.mindist_sq(paa_q, words, 256, 256))
+    assert index.box_mindist_sq(paa_q, np.zeros((1, 16), int), np.full((1, 16), 255), 256, 256)[0] == 0.0
+
+
+def test_page_envelopes_bound_every_row():
+    """Envelopes hold every row's symbols and attain their ends; a page's box MINDIST is a lower
+    bound of each of its rows' MINDIST (hence of their distances), reached by a one-row page;
+    widening a box never raises its bound."""
+    x = _rw(3000, 64, 31)
+    sax = isax.isax_words(x, 16, 256)
+    rows, _ = index.sort_order(isax.key64(sax, 256))
+    words = sax[rows]
+    for P in (1, 32, 256, 1000):
+        lo, hi = index.page_envelopes(words, P)
+        assert lo.shape[0] == -(-3000 // P)
+        for p in range(lo.shape[0]):
+            blk = words[p * P:(p + 1) * P].astype(int)
+            assert np.all(blk >= lo[p]) and np.all(blk <= hi[p])
+            for i in range(16):
+                assert lo[p, i] in blk[:, i] and hi[p, i] in blk[:, i]
+    q = _rw(5, 64, 32)
+    lo, hi = index.page_envelopes(words, 64)
+    for t in range(q.shape[0]):
+        pq = isax.paa(q[t], 16)[0]
+        box = index.box_mindist_sq(pq, lo, hi, 64, 256)
+        row_lb = isax.mindist_sq(pq, words, 64, 256)
+        ed2 = ((x[rows].astype(np.float64) - q[t]) ** 2).sum(axis=1)
+        for p in range(lo.shape[0]):
+            seg = slice(p * 64, (p + 1) * 64)
+            assert box[p] <= row_lb[seg].min() + 1e-12
+            assert box[p] <= ed2[seg].min() + 1e-9
+        wide = index.box_mindist_sq(pq, np.maximum(lo - 3, 0), np.minimum(hi + 3, 255), 64, 256)
+        assert np.all(wide <= box)
+    one_lo, one_hi = index.page_envelopes(words, 1)
+    assert np.array_equal(index.box_mindist_sq(isax.paa(q[0], 16)[0], one_lo, one_hi, 64, 256),
+                          isax.mindist_sq(isax.paa(q[0], 16)[0], words, 64, 256))
