@@ -116,7 +116,14 @@ typedef struct paris_query_opts {
   int32_t chunk;       /* queries whose candidate lists are resident at once; 0 = automatic */
   int32_t precision;   /* PARIS_REFINE_*; default FP32 */
   int32_t seed;        /* PARIS_SEED_*; default DESCENT */
-  int32_t reserved[3]; /* must be zero */
+  int32_t no_leaf_pruning; /* 0 (default): leaf pruning -- every page of 256 consecutive rows in
+                              index order (rows sorted by key, so each page lies inside one ADS+
+                              subtree) keeps the per-segment range of its symbols, and a row scan
+                              visits only the pages whose MINDIST to the query (the distance to
+                              that box of iSAX regions) passes the same test as a row; pages that
+                              fail hold no row that could pass. 1: scan every summary (Alg. 8 as
+                              printed). Same answers either way. */
+  int32_t reserved[2]; /* must be zero */
 } paris_query_opts;
 
 typedef struct paris_query_stats {
@@ -133,6 +140,8 @@ typedef struct paris_query_stats {
                           best candidate found; the call fails with EINTERNAL after 4 repeats) */
   int64_t lb_lookups;  /* BATCHED: lower-bound table lookups the scans performed (one per lane,
                           slot and pair of queries; early abandoning skips the rest) */
+  int64_t pages_examined; /* leaf pruning: page lower bounds computed (pages x queries) */
+  int64_t pages_kept;     /* ... of which passed (their rows were scanned for that query) */
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */
@@ -262,6 +271,17 @@ paris_status paris_approx_search(const paris_index* idx, const float* queries, i
 paris_status paris_lb_scan(const paris_index* idx, const float* query, float threshold_sq,
                            uint32_t* out_rows, float* out_lb, int64_t capacity, int64_t* out_count,
                            void* stream);
+
+/* Leaf pruning alone for one query against a squared threshold (Sec. 2.2 ADS+ leaves; the
+ * MINDIST of Sec. 3.3.1 taken to a page's box of iSAX regions). The index order (rows sorted
+ * by key, paris_export_order) is cut into pages of PARIS_PAGE_ROWS consecutive positions; page
+ * p covers positions [p * PARIS_PAGE_ROWS, (p + 1) * PARIS_PAGE_ROWS). Bit p of out_bits
+ * (device uint32 [(pages + 31) / 32], bit p % 32 of word p / 32) is set when the page's box
+ * MINDIST^2 lower bound passes the row test of paris_lb_scan; a page that fails holds no row
+ * that paris_lb_scan would keep. *out_kept (host) receives the number of set bits. */
+#define PARIS_PAGE_ROWS 256
+paris_status paris_leaf_scan(const paris_index* idx, const float* query, float threshold_sq, uint32_t* out_bits,
+                             int64_t* out_kept, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Learned best-so-far proposal (not in the paper; it only chooses which extra leaves the

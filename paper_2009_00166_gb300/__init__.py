@@ -36,6 +36,8 @@ from .binding import (  # noqa: F401
     paris_index_describe,
     paris_kernel_launches,
     paris_lb_scan,
+    paris_leaf_scan,
+    PARIS_PAGE_ROWS,
     paris_row_buckets,
     paris_last_error,
     paris_set_allocator,

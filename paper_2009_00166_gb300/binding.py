@@ -34,7 +34,8 @@ class BuildOpts(C.Structure):
 
 class QueryOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("query_tile", C.c_int32), ("chunk", C.c_int32),
-                ("precision", C.c_int32), ("seed", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("precision", C.c_int32), ("seed", C.c_int32), ("no_leaf_pruning", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class QueryStats(C.Structure):
@@ -42,7 +43,8 @@ class QueryStats(C.Structure):
                 ("leaf_rows", C.c_int64), ("dense_queries", C.c_int64), ("ms_prep", C.c_double),
                 ("ms_descent", C.c_double), ("ms_lbscan", C.c_double), ("ms_refine", C.c_double),
                 ("ms_select", C.c_double), ("ms_dense", C.c_double), ("query_tile", C.c_int32),
-                ("rescreens", C.c_int32), ("lb_lookups", C.c_int64)]
+                ("rescreens", C.c_int32), ("lb_lookups", C.c_int64), ("pages_examined", C.c_int64),
+                ("pages_kept", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +102,7 @@ def lib():
             "paris_approx_search": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_lb_scan": ([VP, P, F32, P, P, I64, C.POINTER(I64), VP], I32),
             "paris_lb_scan_noalloc": ([VP, P, I64, P, P, P, I64, P, VP], I32),
+            "paris_leaf_scan": ([VP, P, F32, P, C.POINTER(I64), VP], I32),
             "paris_approx_search_ex": ([VP, P, I64, I32, I32, P, P, VP], I32),
             "paris_seed_model_create": ([C.c_uint64, VP, C.POINTER(VP)], I32),
             "paris_seed_model_free": ([VP], None),
@@ -201,7 +204,8 @@ def paris_free(index: ParisIndex):
 
 def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, mode: int = PARIS_MODE_PLAIN,
                        query_tile: int = 0, chunk: int = 0, precision: int = PARIS_REFINE_FP32,
-                       seed: int = PARIS_SEED_DESCENT, want_stats: bool = False, stream=None):
+                       seed: int = PARIS_SEED_DESCENT, want_stats: bool = False, stream=None,
+                       leaf_pruning: bool = True):
     """paris_exact_knn_ex: returns (idx [nq][k] int64, dist [nq][k] float32[, stats dict]).
 
     Outputs are allocated like the queries (same device) when not given.
@@ -213,7 +217,8 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
         out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed)
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed,
+                     no_leaf_pruning=0 if leaf_pruning else 1)
     stats = QueryStats()
     _check(lib().paris_exact_knn_ex(index.handle, _ptr(queries), nq, k, _ptr(out_idx), _ptr(out_dist),
                                     C.byref(opts), C.byref(stats) if want_stats else None, _stream(stream)))
@@ -224,7 +229,7 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
 
 def paris_exact_knn_multi(indexes, queries, k: int, mode: int = PARIS_MODE_BATCHED, query_tile: int = 0,
                           chunk: int = 0, precision: int = PARIS_REFINE_FP32, seed: int = PARIS_SEED_DESCENT,
-                          want_stats: bool = False, stream=None):
+                          want_stats: bool = False, stream=None, leaf_pruning: bool = True):
     """paris_exact_knn_multi: one (idx [nq][k], dist [nq][k]) pair per collection[, stats dicts]."""
     import torch
     m = len(indexes)
@@ -242,7 +247,8 @@ def paris_exact_knn_multi(indexes, queries, k: int, mode: int = PARIS_MODE_BATCH
     nqs = (C.c_int64 * m)(*[int(q.shape[0]) for q in queries])
     oi = VPA(*[_ptr(o[0]) for o in outs])
     od = VPA(*[_ptr(o[1]) for o in outs])
-    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed)
+    opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed,
+                     no_leaf_pruning=0 if leaf_pruning else 1)
     stats = (QueryStats * m)()
     _check(lib().paris_exact_knn_multi(hs, m, qp, nqs, k, oi, od, C.byref(opts), stats if want_stats else None,
                                        _stream(stream)))
@@ -255,9 +261,10 @@ class KnnPlan:
     """paris_knn_plan_*: a batch of exactly ``nq`` queries recorded once as a CUDA graph."""
 
     def __init__(self, index: ParisIndex, nq: int, k: int, mode: int = PARIS_MODE_BATCHED, query_tile: int = 0,
-                 chunk: int = 0, precision: int = PARIS_REFINE_FP32):
+                 chunk: int = 0, precision: int = PARIS_REFINE_FP32, leaf_pruning: bool = True):
         self.index, self.nq, self.k = index, int(nq), int(k)
-        opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision)
+        opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision,
+                         no_leaf_pruning=0 if leaf_pruning else 1)
         h = C.c_void_p()
         _check(lib().paris_knn_plan_create(index.handle, self.nq, self.k, C.byref(opts), C.byref(h)))
         self.handle = h
@@ -356,6 +363,22 @@ def paris_lb_scan(index: ParisIndex, query, threshold_sq: float, capacity: int |
                                C.byref(cnt), _stream(stream)))
     m = min(cnt.value, cap)
     return rows[:m].to(torch.int64) & 0xFFFFFFFF, lbs[:m], cnt.value
+
+
+PARIS_PAGE_ROWS = 256
+
+
+def paris_leaf_scan(index: ParisIndex, query, threshold_sq: float, stream=None):
+    """Leaf pruning of one device query: (bits, kept) -- device uint32 page bits of the index
+    order (bit p: page p may hold a row that the lower-bound scan keeps) and their count."""
+    import torch
+    n = paris_index_describe(index)["n"]
+    words = ((n + PARIS_PAGE_ROWS - 1) // PARIS_PAGE_ROWS + 31) // 32
+    bits = torch.zeros(words, dtype=torch.int32, device=query.device)
+    kept = C.c_int64()
+    _check(lib().paris_leaf_scan(index.handle, _ptr(query), float(threshold_sq), _ptr(bits), C.byref(kept),
+                                 _stream(stream)))
+    return bits, kept.value
 
 
 _alloc_keepalive = []

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -154,6 +155,8 @@ void release_index(paris_index* idx) {
   dev_free(idx->sax, (size_t)idx->n * PARIS_SAX_BYTES, st);
   dev_free(idx->keys_sorted, (size_t)idx->n * 8, st);
   dev_free(idx->rows_sorted, (size_t)idx->n * 4, st);
+  dev_free(idx->sax_sorted, (size_t)idx->n * PARIS_SAX_BYTES, st);
+  dev_free(idx->env, (size_t)idx->npages * 32, st);
   dev_free(idx->beta_keys, (size_t)(idx->card - 1) * 8, st);
   dev_free(idx->beta_ext, (size_t)(idx->card + 1) * 8, st);
   release_shadow(idx);
@@ -235,11 +238,14 @@ struct PhaseTimer {
 // Query tile of the batched scan for a (len, card) shape: the fastest of the candidate tiles per
 // query, timed once per shape on the first chunk that needs it, then remembered.
 std::mutex g_tune_mutex;
-std::map<std::pair<int, int>, int> g_tuned;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
 
-paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, const ChunkState& cs, cudaStream_t st,
-                              int* out) {
-  const auto key = std::make_pair(idx->len, idx->card);
+paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, const ChunkState& cs, bool prune,
+                              cudaStream_t st, int* out) {
+  // one choice per device, shape, collection size (binary order of magnitude) and pruning mode
+  int lg = 0;
+  while (lg < 62 && (int64_t(1) << (lg + 1)) <= idx->n) ++lg;
+  const auto key = std::make_tuple(idx->device, idx->len, idx->card, lg, prune ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
@@ -265,6 +271,7 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
     sub.count = cs.count + offs[j];
     sub.rows = cs.rows + (int64_t)offs[j] * cs.cap;
     sub.lb = cs.lb + (int64_t)offs[j] * cs.cap;
+    if (cs.pagebits) sub.pagebits = cs.pagebits + (int64_t)offs[j] * page_words(idx->n);
     return sub;
   };
   DevBuf scratch_status;
@@ -490,6 +497,8 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   }
   s = radix_sort_index(idx->keys_sorted, idx->rows_sorted, n, st);
   if (s != PARIS_OK) return bail(s);
+  s = build_leaf_envelopes(idx, st);
+  if (s != PARIS_OK) return bail(s);
   s = check_status_word(status.as<uint32_t>(), st, "paris_build");
   if (s != PARIS_OK) return bail(s);
   *out = idx;
@@ -577,7 +586,8 @@ static paris_status alloc_query_state(const paris_index* idx, int64_t nq, int k,
   };
   size_t o_paa = take((size_t)nq * 16 * 8), o_key = take((size_t)nq * 8),
          o_tab = take((size_t)nq * idx->card * 16 * 4), o_thr = take((size_t)nq * 4), o_bsf = take((size_t)nq * 8),
-         o_leaf = take((size_t)nq * 16), o_seed = take((size_t)nq * 4), o_stat = take(4), o_cnt = take(5 * 8);
+         o_leaf = take((size_t)nq * 16), o_seed = take((size_t)nq * 4), o_stat = take(4), o_cnt = take(8 * 8),
+         o_sym = take((size_t)nq * 16);
   if (!block.alloc(off, st)) return fail(PARIS_ENOMEM, "query state (%zu bytes)", off);
   char* b = block.as<char>();
   qs.nq = nq;
@@ -592,9 +602,10 @@ static paris_status alloc_query_state(const paris_index* idx, int64_t nq, int k,
   qs.seed = (float*)(b + o_seed);
   qs.status = (uint32_t*)(b + o_stat);
   qs.counters = (unsigned long long*)(b + o_cnt);
+  qs.qsym = (uint8_t*)(b + o_sym);
   qs.cg = gamma_scale(idx->len);
   PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-  PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
+  PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 64, st));
   return PARIS_OK;
 }
 
@@ -608,8 +619,9 @@ static paris_status check_query_args(const paris_index* idx, const float* querie
 }
 
 static paris_status check_query_opts(const paris_index* idx, const paris_query_opts& o) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.no_leaf_pruning != 0 && o.no_leaf_pruning != 1) return fail(PARIS_EINVAL, "no_leaf_pruning must be 0 or 1");
   if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
   if (o.seed == PARIS_SEED_LEARNED && !idx->seed_model)
     return fail(PARIS_EINVAL, "PARIS_SEED_LEARNED needs a model attached with paris_attach_seed_model");
@@ -649,6 +661,9 @@ struct KnnJob {
   int qt = 0;
   int64_t dense_total = 0;
   int rescreens = 0;
+  bool prune = true;          // leaf pruning: page lower bounds before the row scans
+  int64_t paged_chunk = -1;   // chunk whose page bits are ready (BATCHED)
+  int64_t pages_examined = 0;
 
   int64_t chunks() const { return qc > 0 ? (nq + qc - 1) / qc : 0; }
 
@@ -705,7 +720,9 @@ struct KnnJob {
            o_r2 = take((size_t)qc * cap * 4), o_l2 = take((size_t)qc * cap * 4), o_bk = take((size_t)qc * 32 * 4),
            o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4), o_pl = take((size_t)qc * 8), o_pm = take((size_t)qc * 4),
            o_ds = take((size_t)qc * 4), o_dn = take(8), o_no = take(8),
-           o_dq = take(dense_query_rows(qc) * idx->len * 2), o_dm = take(dense_query_rows(qc) * 8);
+           o_dq = take(dense_query_rows(qc) * idx->len * 2), o_dm = take(dense_query_rows(qc) * 8),
+           o_pb = take((size_t)qc * page_words(idx->n) * 4), o_pls = take((size_t)page_count(idx->n) * 4),
+           o_pc = take(8);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
     char* b = cblock.as<char>();
     cs.cap = cap;
@@ -732,7 +749,24 @@ struct KnnJob {
     cs.dqbf = (void*)(b + o_dq);
     cs.dqnm = (float2*)(b + o_dm);
     cs.dq_rows = (int64_t)dense_query_rows(qc);
+    prune = o.no_leaf_pruning == 0;
+    cs.pagebits = prune ? (uint32_t*)(b + o_pb) : nullptr;
+    cs.page_list = (uint32_t*)(b + o_pls);
+    cs.page_count = (uint32_t*)(b + o_pc);
+    paged_chunk = -1;
+    pages_examined = 0;
     qt = o.mode == PARIS_MODE_BATCHED ? o.query_tile : 0;
+    return PARIS_OK;
+  }
+
+  // Page bits of the current chunk's queries (BATCHED leaf pruning).
+  paris_status page_pass(int64_t c) {
+    if (!prune || o.mode != PARIS_MODE_BATCHED || paged_chunk == c) return PARIS_OK;
+    timer.begin(2);
+    PARIS_TRY(launch_page_lb(idx, qs, cs.q0, cs.qc, cs.pagebits, nullptr, nullptr, st));
+    timer.end(2);
+    pages_examined += idx->npages * (int64_t)cs.qc;
+    paged_chunk = c;
     return PARIS_OK;
   }
 
@@ -756,13 +790,16 @@ struct KnnJob {
     if (nq == 0) return PARIS_OK;
     if (o.mode == PARIS_MODE_BATCHED && qt == 0) return fail(PARIS_EINTERNAL, "query tile unknown at capture");
     PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 64, st));
     PARIS_CUDA(cudaMemsetAsync(cs.nover, 0, 4, st));
     PARIS_TRY(front());
+    paged_chunk = -1;
+    pages_examined = 0;
     for (int64_t c = 0; c < chunks(); ++c) {
       cs.q0 = c * qc;
       cs.qc = (int)std::min<int64_t>(qc, nq - cs.q0);
       PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
+      PARIS_TRY(page_pass(c));
       PARIS_TRY(scan_chunk());
       if (mixed) PARIS_TRY(launch_dense(const_cast<paris_index*>(idx), qs, cs, lb_status, nullptr, st));
       PARIS_TRY(launch_refine(idx, qs, cs, st));
@@ -776,9 +813,11 @@ struct KnnJob {
   paris_status run_eager(const char* what) {
     if (nq == 0) return PARIS_OK;
     PARIS_CUDA(cudaMemsetAsync(qs.status, 0, 4, st));
-    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 40, st));
+    PARIS_CUDA(cudaMemsetAsync(qs.counters, 0, 64, st));
     dense_total = 0;
     rescreens = 0;
+    paged_chunk = -1;
+    pages_examined = 0;
     PARIS_TRY(front());
     for (int64_t c = 0; c < chunks(); ++c) {
       PARIS_TRY(begin_chunk(c));
@@ -793,7 +832,8 @@ struct KnnJob {
     cs.q0 = c * qc;
     cs.qc = (int)std::min<int64_t>(qc, nq - cs.q0);
     PARIS_CUDA(cudaMemsetAsync(cs.count, 0, (size_t)cs.qc * 4, st));
-    if (o.mode == PARIS_MODE_BATCHED && qt == 0) PARIS_TRY(tuned_query_tile(idx, qs, cs, st, &qt));
+    PARIS_TRY(page_pass(c));  // before tuning: the trial scans visit the kept pages only
+    if (o.mode == PARIS_MODE_BATCHED && qt == 0) PARIS_TRY(tuned_query_tile(idx, qs, cs, prune, st, &qt));
     return PARIS_OK;
   }
 
@@ -802,6 +842,16 @@ struct KnnJob {
     timer.begin(2);
     if (o.mode == PARIS_MODE_BATCHED) {
       PARIS_TRY(launch_lbscan_batched(idx, qs, cs, qt, mixed ? 1 : 0, lb_status, st));
+    } else if (prune) {
+      // the paper's one-query pass, over the pages whose envelope may hold a kept row
+      for (int j = 0; j < cs.qc; ++j) {
+        PARIS_CUDA(cudaMemsetAsync(cs.page_count, 0, 4, st));
+        PARIS_TRY(launch_page_lb(idx, qs, cs.q0 + j, 1, cs.pagebits, cs.page_list, cs.page_count, st));
+        PARIS_TRY(launch_lbscan_pages(idx, qs, cs.q0 + j, cs.page_list, cs.page_count, cs.count + j,
+                                      cs.rows + (int64_t)j * cs.cap, cs.lb + (int64_t)j * cs.cap, cs.cap, lb_status,
+                                      mixed ? 1 : 0, st));
+      }
+      pages_examined += idx->npages * (int64_t)cs.qc;
     } else {
       for (int j = 0; j < cs.qc; ++j)
         PARIS_TRY(launch_lbscan(idx, qs, cs.q0 + j, cs.count + j, cs.rows + (int64_t)j * cs.cap,
@@ -866,7 +916,7 @@ struct KnnJob {
       stats->ms_lbscan = ms[2];
       stats->ms_refine = ms[3];
       stats->ms_select = ms[4];
-      unsigned long long c[5];
+      unsigned long long c[8];
       PARIS_CUDA(cudaMemcpyAsync(c, qs.counters, sizeof c, cudaMemcpyDeviceToHost, st));
       PARIS_CUDA(cudaStreamSynchronize(st));
       stats->candidates = (int64_t)c[0];
@@ -874,6 +924,8 @@ struct KnnJob {
       stats->contenders = (int64_t)c[2];
       stats->leaf_rows = (int64_t)c[3];
       stats->lb_lookups = (int64_t)c[4];
+      stats->pages_kept = (int64_t)c[5];
+      stats->pages_examined = pages_examined;
     }
     return PARIS_OK;
   }
@@ -1186,6 +1238,31 @@ paris_status paris_approx_search_ex(const paris_index* idx, const float* queries
   PARIS_TRY(sl.finish(st));
   PARIS_TRY(ss.finish(st));
   return check_status_word(qs.status, st, "paris_approx_search");
+}
+
+paris_status paris_leaf_scan(const paris_index* idx, const float* query, float threshold_sq, uint32_t* out_bits,
+                             int64_t* out_kept, void* stream) {
+  clear_error();
+  PARIS_TRY(check_query_args(idx, query, 1, 1));
+  if (!out_bits || !out_kept) return fail(PARIS_EINVAL, "NULL output");
+  if (!is_device_ptr(out_bits)) return fail(PARIS_EINVAL, "out_bits must be device memory");
+  if (!(threshold_sq >= 0.f)) return fail(PARIS_EINVAL, "threshold_sq must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged sq;
+  PARIS_TRY(sq.in(query, (size_t)idx->len * 4, st));
+  QueryState qs;
+  DevBuf qblock;
+  PARIS_TRY(alloc_query_state(idx, 1, 1, (const float*)sq.dev, qs, qblock, st));
+  PARIS_TRY(launch_query_prep(idx, qs, st));
+  uint32_t tb = 0;
+  std::memcpy(&tb, &threshold_sq, 4);
+  PARIS_CUDA(cudaMemcpyAsync(qs.thr, &tb, 4, cudaMemcpyHostToDevice, st));
+  PARIS_TRY(launch_page_lb(idx, qs, 0, 1, out_bits, nullptr, nullptr, st));
+  unsigned long long kept = 0;
+  PARIS_CUDA(cudaMemcpyAsync(&kept, qs.counters + 5, 8, cudaMemcpyDeviceToHost, st));
+  PARIS_TRY(check_status_word(qs.status, st, "paris_leaf_scan"));
+  *out_kept = (int64_t)kept;
+  return PARIS_OK;
 }
 
 paris_status paris_lb_scan(const paris_index* idx, const float* query, float threshold_sq, uint32_t* out_rows,

@@ -12,8 +12,11 @@
 // contribution; the 16-term FP16 sum has relative error below 16 * 2^-11, so a row is kept when
 // (sum * (1 - 2^-6)) <= threshold, and that scaled value is what is stored as its lower bound.
 //
-// Work order: each CTA owns a contiguous row range and every query tile passes over it (the
-// range may be cut into blocks that all tiles visit in turn). Within a tile a warp checks its
+// Work order: the summaries are read in index order (rows sorted by their interleaved key, so
+// the ADS+ leaves are contiguous). Each CTA owns a contiguous range of pages of kPageRows
+// positions and every query tile passes over it, visiting only the pages that the leaf pruning
+// kept for some active query of the tile (all pages without it); a tile with no kept page in the
+// CTA's range does not even load its tables. Within a tile a warp checks its
 // 32 rows after 4 and after 8 of the 16 slots and drops them as soon as no (row, query) partial
 // sum is within its threshold; partial sums of non-negative terms never decrease, so the kept
 // set and the stored bounds are unchanged.
@@ -27,7 +30,6 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
-#include <cstdlib>
 
 #include "query.cuh"
 
@@ -245,7 +247,10 @@ __device__ __forceinline__ void lane_offsets(int lane, uint32_t (&offp)[8]) {
 // One collection's share of a batched scan launch: its summaries, the chunk's packed tables,
 // thresholds and candidate lists, and the CTAs [cta0, cta0 + ncta) that split its rows.
 struct ScanColl {
-  const uint4* sax;
+  const uint4* sax;      // index-order summaries (position p rotated by p mod 16)
+  const uint32_t* pos_row;  // row of each index-order position
+  const uint32_t* pagebits;  // [qc][words] kept pages per chunk query (NULL: every page)
+  int64_t words;
   int64_t n;
   const uint32_t* packed;
   const uint32_t* thr;
@@ -269,7 +274,6 @@ static_assert(kMaxColl == kMaxScanJobs, "one scan descriptor per collection of a
 struct ScanWork {
   int ncoll;
   int card;
-  int64_t block_groups;  // row groups per block of a CTA's range
   int64_t stride;        // pilot: every stride-th row group
   ScanColl c[kMaxColl];
 };
@@ -280,14 +284,19 @@ __device__ __forceinline__ int coll_of_block(const ScanWork& W) {
   return ci;
 }
 
+constexpr int kWinPages = 1024;  // pages per window of a CTA's range (the kept-page list in shared memory)
+
 template <int NP>
 __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __grid_constant__ ScanWork W) {
   constexpr int QT = 2 * NP;
+  constexpr int kGpp = kPageRows / 32;  // 32-row groups per page
   extern __shared__ __align__(16) uint32_t s_tab[];  // region r (64 KB): pairs 2r, 2r+1
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
   __shared__ int s_qid[QT];  // chunk query of each tile slot
   __shared__ int s_skip;
+  __shared__ uint32_t s_pages[kWinPages];  // kept pages of the current window (any order)
+  __shared__ int s_np;
   const ScanColl& C = W.c[coll_of_block(W)];
   const uint4* __restrict__ sax = C.sax;
   const int64_t n = C.n, cap = C.cap;
@@ -298,49 +307,83 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
   uint32_t offp[8];
   lane_offsets(lane, offp);
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
-  const int64_t groups = (n + 31) >> 5;
-  const int64_t per = (groups + C.ncta - 1) / C.ncta;
-  const int64_t g0 = (int64_t)(blockIdx.x - C.cta0) * per, g1 = min(groups, g0 + per);
+  // the CTA's range of index-order pages, in whole 32-page words
+  const int64_t npages = (n + kPageRows - 1) / kPageRows;
+  const int64_t nwords = (npages + 31) >> 5;
+  const int64_t wper = (nwords + C.ncta - 1) / C.ncta;
+  const int64_t pg0 = (int64_t)(blockIdx.x - C.cta0) * wper * 32, pg1 = min(npages, pg0 + wper * 32);
   const int64_t entries = (int64_t)W.card * 16;
-  // The CTA's row range may be cut into blocks that every query tile passes over in turn.
-  for (int64_t b0 = g0; b0 < g1; b0 += W.block_groups) {
-    const int64_t b1 = min(g1, b0 + W.block_groups);
-    for (int tile = 0; tile < C.ntiles; ++tile) {
-      const int qb = tile * QT;
-      __syncthreads();  // the previous tile's tables and flags are no longer read
-      if (threadIdx.x == 0) {
-        int skip = 1;
-        for (int q = 0; q < QT; ++q) {
-          const int qq = qb + q;
-          const int qid = qq < qc ? (C.perm ? C.perm[qq] : qq) : 0;
-          // a list whose count passed its capacity has flagged its overflow (or was handed to the
-          // tensor-core screening beforehand): the query takes no further part in the scan
-          const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qid) > cap);
-          s_active[q] = act;
-          s_qid[q] = qid;
-          if (act) skip = 0;
+  for (int tile = 0; tile < C.ntiles; ++tile) {
+    const int qb = tile * QT;
+    __syncthreads();  // the previous tile's tables and flags are no longer read
+    if (threadIdx.x == 0) {
+      int skip = 1;
+      for (int q = 0; q < QT; ++q) {
+        const int qq = qb + q;
+        const int qid = qq < qc ? (C.perm ? C.perm[qq] : qq) : 0;
+        // a list whose count passed its capacity has flagged its overflow (or was handed to the
+        // tensor-core screening beforehand): the query takes no further part in the scan
+        const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qid) > cap);
+        s_active[q] = act;
+        s_qid[q] = qid;
+        if (act) skip = 0;
+      }
+      s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    bool loaded = false;
+    __half2 thh[NP];
+    uint32_t ovf = 0u;   // bit q: the list of tile slot q passed its capacity
+    uint32_t slots = 0;  // slots this warp looked up in this tile, per row group
+    for (int64_t w0 = pg0; w0 < pg1; w0 += kWinPages) {
+      const int64_t w1 = min(pg1, w0 + kWinPages);
+      __syncthreads();  // the previous window's page list and count are no longer read
+      if (threadIdx.x == 0) s_np = 0;
+      __syncthreads();
+      // pages of the window that some active query of the tile keeps (leaf pruning)
+      for (int64_t wi = threadIdx.x; wi < (w1 - w0 + 31) >> 5; wi += blockDim.x) {
+        const int64_t wd = (w0 >> 5) + wi;
+        uint32_t u = 0u;
+        if (C.pagebits) {
+          for (int q = 0; q < QT; ++q)
+            if (s_active[q]) u |= __ldg(C.pagebits + (int64_t)s_qid[q] * C.words + wd);
+        } else {
+          u = ~0u;
         }
-        s_skip = skip;
+        const int64_t lim = w1 - wd * 32;  // pages of this word inside the window
+        if (lim < 32) u &= (1u << lim) - 1u;
+        if (u) {
+          int base = atomicAdd(&s_np, __popc(u));
+          while (u) {
+            const int b = __ffs(u) - 1;
+            u &= u - 1u;
+            s_pages[base++] = (uint32_t)(wd * 32 + b);
+          }
+        }
       }
       __syncthreads();
-      if (s_skip) continue;
-      load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, C.perm, s_active, s_tab, s_thr);
-      __syncthreads();
-      __half2 thh[NP];
-      tile_thresholds<NP>(s_thr, thh);
-      uint32_t ovf = 0u;   // bit q: the list of tile slot q passed its capacity
-      uint32_t slots = 0;  // slots this warp looked up in this tile, per row group
-      for (int64_t it = b0 + (int64_t)wib * kBUnroll; it < b1; it += (int64_t)nw * kBUnroll) {
+      const int np = s_np;
+      if (np == 0) continue;
+      if (!loaded) {
+        load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, C.perm, s_active, s_tab, s_thr);
+        __syncthreads();
+        tile_thresholds<NP>(s_thr, thh);
+        loaded = true;
+      }
+      const int64_t vgroups = (int64_t)np * kGpp;
+      for (int64_t it = (int64_t)wib * kBUnroll; it < vgroups; it += (int64_t)nw * kBUnroll) {
         uint4 word[kBUnroll];
+        int64_t pos[kBUnroll];
 #pragma unroll
         for (int u = 0; u < kBUnroll; ++u) {
-          const int64_t row = (it + u) * 32 + lane;
-          word[u] = (it + u < b1 && row < n) ? __ldcg(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+          const int64_t v = it + u;
+          pos[u] = v < vgroups ? ((int64_t)s_pages[v / kGpp] * kGpp + v % kGpp) * 32 + lane : n;
+          word[u] = pos[u] < n ? __ldcg(sax + pos[u]) : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int u = 0; u < kBUnroll; ++u) {
-          const int64_t row = (it + u) * 32 + lane;
-          const bool rv = it + u < b1 && row < n;
+          const bool rv = pos[u] < n;
           __half2 sum[NP];
           const uint32_t keepmask = row_keep_bits<NP>(word[u], rv, offp, tab, thh, sum, slots);
           const uint32_t any = __reduce_or_sync(PARIS_FULL_MASK, keepmask);
@@ -348,6 +391,7 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
             uint32_t sv[NP];
 #pragma unroll
             for (int p = 0; p < NP; ++p) sv[p] = *reinterpret_cast<const uint32_t*>(&sum[p]);
+            const uint32_t row = rv ? C.pos_row[pos[u]] : 0u;
             ovf = emit_row<NP>(keepmask, any, sv, row, lane, s_qid, count, C.rows, C.lb, cap, ovf, status);
           }
         }
@@ -358,8 +402,8 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
           if (all) break;
         }
       }
-      if (lane == 0 && C.lookups && slots) atomicAdd(C.lookups, (unsigned long long)slots * (NP * 32));
     }
+    if (lane == 0 && C.lookups && slots) atomicAdd(C.lookups, (unsigned long long)slots * (NP * 32));
   }
 }
 
@@ -475,16 +519,6 @@ size_t batched_smem(int np, int card) {
   return (size_t)(blocks - 1) * 65536 + (size_t)card * 256;
 }
 
-// Row groups (32 rows) per CTA row block. By default a CTA's whole row range is one block: every
-// query tile streams the summaries from HBM (measured faster at 20M rows than L2-sized blocks,
-// whose tile tables must be reloaded per block). PARIS_BATCHED_BLOCK_ROWS sets rows per block.
-int64_t block_groups() {
-  int64_t rows = 0;
-  if (const char* env = std::getenv("PARIS_BATCHED_BLOCK_ROWS")) rows = std::atoll(env);
-  if (rows <= 0) return INT64_MAX / 64;
-  return std::max<int64_t>(1, (rows + 31) / 32);
-}
-
 int sm_count_b() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -534,7 +568,6 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   const int sms = sm_count_b();
   ScanWork W{}, PW{};
   W.card = PW.card = card;
-  W.block_groups = block_groups();
   W.stride = PW.stride = kPilotStride;
   double work[kMaxColl], pwork[kMaxColl];
   int pilot_of[kMaxColl];  // scan collection of each pilot collection
@@ -550,7 +583,10 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     const ChunkState& cs = *jobs[j].cs;
     const int64_t groups = (idx->n + 31) / 32;
     ScanColl C{};
-    C.sax = reinterpret_cast<const uint4*>(idx->sax);
+    C.sax = reinterpret_cast<const uint4*>(idx->sax_sorted);
+    C.pos_row = idx->rows_sorted;
+    C.pagebits = cs.pagebits;
+    C.words = page_words(idx->n);
     C.n = idx->n;
     C.packed = cs.packed;
     C.thr = qs.thr;

@@ -19,6 +19,12 @@ struct paris_index {
   uint8_t* sax = nullptr;           // device [n][16], slot j of row r = segment (j + r) % 16
   uint64_t* keys_sorted = nullptr;  // device [n]
   uint32_t* rows_sorted = nullptr;  // device [n]
+  // index order (leaf pruning): position p's summary rotated by p mod 16, and the envelope of
+  // every page of kPageRows positions (smallest then largest symbol per segment, 16 B each,
+  // rotated by the page number mod 16)
+  uint8_t* sax_sorted = nullptr;    // device [n][16]
+  uint8_t* env = nullptr;           // device [npages][2][16]
+  int64_t npages = 0;
   uint64_t* beta_keys = nullptr;    // device [card-1] order keys of the breakpoints
   double* beta_ext = nullptr;       // device [card+1]: -inf, beta_1..beta_{card-1}, +inf
   std::vector<double> beta_host;

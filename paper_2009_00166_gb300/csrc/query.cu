@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
                                                    int card, int bits, const uint64_t* __restrict__ beta_keys_g,
                                                    const double* __restrict__ beta_ext, double* __restrict__ qpaa,
                                                    uint64_t* __restrict__ qkey, float* __restrict__ qtable,
-                                                   uint32_t* __restrict__ status) {
+                                                   uint8_t* __restrict__ qsym, uint32_t* __restrict__ status) {
   __shared__ uint64_t beta_keys[255];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
   __syncthreads();
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
     const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     if (!qv) continue;
     qpaa[q * 16 + seg] = seg < sh.w ? paa : 0.0;
+    if (qsym) qsym[q * 16 + seg] = (uint8_t)sym;  // 0 past w, like the summaries' unused slots
     if (seg == 0) qkey[q] = key;
     const double P = paa;
     float* T = qtable + q * (int64_t)card * 16;
@@ -339,11 +340,14 @@ __device__ __forceinline__ bool flush_stage(uint32_t* s_row, float* s_lb, int nf
   return (int64_t)base + nflush <= cap;
 }
 
+// With a page list (leaf pruning), the pass visits only the 32-row groups of the listed pages of
+// the index-order summaries and reports each kept position's row (pos_row).
 __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
     const uint4* __restrict__ sax, int64_t n, const float* __restrict__ table, int card,
     const uint32_t* __restrict__ thr_ptr, float thr_value, uint32_t* __restrict__ count,
     uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap,
-    uint32_t* __restrict__ status, int stop_on_overflow) {
+    uint32_t* __restrict__ status, int stop_on_overflow, const uint32_t* __restrict__ page_list,
+    const uint32_t* __restrict__ page_count, const uint32_t* __restrict__ pos_row) {
   extern __shared__ __align__(16) float s_tab[];
   __shared__ uint32_t s_stage_row[kLbThreads / 32][kStage];
   __shared__ float s_stage_lb[kLbThreads / 32][kStage];
@@ -368,15 +372,19 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
     offp[m] = o0 | (o1 << 16);
   }
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
-  const int64_t groups = (n + 31) >> 5;
+  constexpr int kGpp = kPageRows / 32;  // 32-row groups per page
+  const int64_t groups = page_list ? (int64_t)(*page_count) * kGpp : (n + 31) >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t it = gw * kLbUnroll; it < groups; it += W * kLbUnroll) {
     uint4 word[kLbUnroll];
+    int64_t pos[kLbUnroll];
 #pragma unroll
     for (int u = 0; u < kLbUnroll; ++u) {
-      int64_t row = (it + u) * 32 + lane;
-      word[u] = (row < n) ? __ldcs(sax + row) : make_uint4(0u, 0u, 0u, 0u);
+      const int64_t v = it + u;
+      const int64_t g = page_list ? (v < groups ? (int64_t)page_list[v / kGpp] * kGpp + v % kGpp : n) : v;
+      pos[u] = v < groups ? g * 32 + lane : n;
+      word[u] = (pos[u] < n) ? __ldcs(sax + pos[u]) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < kLbUnroll; ++u) {
@@ -390,13 +398,12 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
         asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
         lb += v;
       }
-      const int64_t row = (it + u) * 32 + lane;
-      const bool keep = row < n && lb * kKeepScale <= thr;
+      const bool keep = pos[u] < n && lb * kKeepScale <= thr;
       const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
       if (mk) {
         if (keep) {
           int p = fill + __popc(mk & lt_mask);
-          st_row[p] = (uint32_t)row;
+          st_row[p] = pos_row ? pos_row[pos[u]] : (uint32_t)pos[u];
           st_lb[p] = lb;
         }
         fill += __popc(mk);
@@ -855,7 +862,7 @@ paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cud
   const int segv = sh.fast ? sh.s / 4 : 1;
 #define PREP(SV)                                                                                      \
   prep_kernel<SV><<<grid, 256, 0, st>>>(qs.queries, qs.nq, sh, idx->card, idx->bits, idx->beta_keys, \
-                                        idx->beta_ext, qs.qpaa, qs.qkey, qs.qtable, qs.status)
+                                        idx->beta_ext, qs.qpaa, qs.qkey, qs.qtable, qs.qsym, qs.status)
   switch (segv) {
     case 1: PREP(1); break;
     case 2: PREP(2); break;
@@ -919,7 +926,26 @@ static paris_status lbscan_common(const paris_index* idx, const float* table, co
   if (grid < 1) grid = 1;
   lbscan_kernel<<<grid, kLbThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax), idx->n, table,
                                                 idx->card, thr_ptr, thr_value, count, rows, lb, cap, status,
-                                                stop_on_overflow);
+                                                stop_on_overflow, nullptr, nullptr, nullptr);
+  note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+paris_status launch_lbscan_pages(const paris_index* idx, const QueryState& qs, int64_t q, const uint32_t* page_list,
+                                 const uint32_t* page_count, uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
+                                 uint32_t* status, int stop_on_overflow, cudaStream_t st) {
+  size_t smem = (size_t)idx->card * 64 * sizeof(float);
+  PARIS_CUDA(cudaFuncSetAttribute(lbscan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the kept page count is on the device: a grid for the full pass, whose warps leave early
+  int64_t groups = (idx->n + 31) / 32;
+  int64_t need_blocks = (groups + (kLbThreads / 32) * kLbUnroll - 1) / ((kLbThreads / 32) * kLbUnroll);
+  int grid = (int)std::min<int64_t>(need_blocks, (int64_t)sm_count() * 2);
+  if (grid < 1) grid = 1;
+  lbscan_kernel<<<grid, kLbThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->sax_sorted), idx->n,
+                                                qs.qtable + q * (int64_t)idx->card * 16, idx->card, qs.thr + q, 0.f,
+                                                count, rows, lb, cap, status, stop_on_overflow, page_list,
+                                                page_count, idx->rows_sorted);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;

@@ -8,6 +8,7 @@ constexpr int kContCap = 512;   // exact re-rank contenders per query
 constexpr int kLimbs = 20;      // 640-bit exact squared distances, least significant bit 2^-298
 constexpr int kMaxLeaf = 4096;  // leaf capacity limit
 constexpr int kDenseRetries = 4;  // repeated screenings of an overflowed list before giving up
+constexpr int kPageRows = 256;    // index-order positions per leaf envelope (a multiple of 32)
 
 // Per-call query state, all device pointers.
 struct QueryState {
@@ -16,13 +17,15 @@ struct QueryState {
   const float* queries = nullptr;  // device [nq][len]
   double* qpaa = nullptr;          // [nq][16]
   uint64_t* qkey = nullptr;        // [nq]
+  uint8_t* qsym = nullptr;         // [nq][16] iSAX symbols in segment order (0 past w); may be NULL
   float* qtable = nullptr;         // [nq][card][16] conservative MINDIST^2 contributions
   uint32_t* thr = nullptr;         // [nq] fp32 bits: prune/abandon threshold on squared ED
   unsigned long long* bsf = nullptr;  // [nq] packed (F bits << 32 | row), k = 1
   int64_t* leaf = nullptr;         // [nq][2]
   float* seed = nullptr;           // [nq]
   uint32_t* status = nullptr;      // [1]
-  unsigned long long* counters = nullptr;  // [5]: candidates, refined, contenders, leaf rows, batched-scan lookups
+  unsigned long long* counters = nullptr;  // [8]: candidates, refined, contenders, leaf rows, batched-scan
+                                           // lookups, pages kept by the leaf pruning, (2 unused)
   float cg = 1.f;                  // (1+gamma)/(1-gamma), rounded up, gamma = gamma_{len+2}
   const uint64_t* keys = nullptr;  // [nq][nk] approximate-search keys (NULL: qkey only)
   int nk = 1;
@@ -56,6 +59,10 @@ struct ChunkState {
   void* dqbf = nullptr;            // [dq_rows][len] BF16 query tiles of the screening
   float2* dqnm = nullptr;          // [dq_rows] (|q|^2, |q|) of those queries
   int64_t dq_rows = 0;             // qc rounded up to whole query tiles
+  // leaf pruning (NULL pagebits: every page is scanned)
+  uint32_t* pagebits = nullptr;    // [qc][page words]: bit p of query j = page p may hold a kept row
+  uint32_t* page_list = nullptr;   // [npages] kept pages of the query being scanned (PLAIN)
+  uint32_t* page_count = nullptr;  // [1]
 };
 
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
@@ -66,6 +73,18 @@ paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t
 paris_status launch_lbscan_threshold(const paris_index* idx, const float* table, float thr,
                                      uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
                                      uint32_t* status, cudaStream_t st);
+// Leaf pruning (leaf.cu): index-order summaries and page envelopes (build), page lower bounds.
+int64_t page_count(int64_t n);
+int64_t page_words(int64_t n);
+paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st);
+// Page bits of chunk queries [q0, q0 + nq) into bits ([nq][words]); with one query, `list` and
+// `list_count` (zeroed by the caller) also receive the kept pages.
+paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_t q0, int64_t nq, uint32_t* bits,
+                            uint32_t* list, uint32_t* list_count, cudaStream_t st);
+// The lower-bound scan of query q over the index-order pages in page_list (count on the device).
+paris_status launch_lbscan_pages(const paris_index* idx, const QueryState& qs, int64_t q, const uint32_t* page_list,
+                                 const uint32_t* page_count, uint32_t* count, uint32_t* rows, float* lb, int64_t cap,
+                                 uint32_t* status, int stop_on_overflow, cudaStream_t st);
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st);
 // Batched lower-bound scan (batched.cu): one persistent launch for a chunk, tiles of qt queries.
