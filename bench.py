@@ -317,7 +317,7 @@ def main():
     if want_model and seed_mode == P.PARIS_SEED_LEARNED:
         model, training = train_model()
 
-    def step(collect=None, md=mode, prec=precision, sd=seed_mode, answers=None, split=False):
+    def step(collect=None, md=mode, prec=precision, sd=seed_mode, answers=None, split=False, prune=True):
         """Build, then answer every query: one call for the whole batch, or one per sigma group."""
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
@@ -328,7 +328,8 @@ def main():
         per_sigma_stats = []
         for g in (groups if split else [Q]):
             out = P.paris_exact_knn_ex(idx, g, k, mode=md, precision=prec, seed=sd, want_stats=collect is not None,
-                                       query_tile=args.query_tile if md == P.PARIS_MODE_BATCHED else 0)
+                                       query_tile=args.query_tile if md == P.PARIS_MODE_BATCHED else 0,
+                                       leaf_pruning=prune)
             if collect is not None:
                 per_sigma_stats.append(out[2])
             if answers is not None:
@@ -417,8 +418,15 @@ def main():
             tq = sum(st_["ms_prep"] + st_["ms_descent"] + st_["ms_lbscan"] + st_["ms_refine"] + st_["ms_select"] +
                      st_["ms_dense"] for r in rs for st_ in [r["stats"][i]])
             c = sum(r["stats"][i]["candidates"] for r in rs) / (len(rs) * args.per_sigma)
+            pk = sum(r["stats"][i]["pages_kept"] for r in rs) / (len(rs) * args.per_sigma)
+            pe = sum(r["stats"][i]["pages_examined"] for r in rs) / (len(rs) * args.per_sigma)
+            # summary bytes a query's scans must read: kept pages' summaries plus every page's
+            # envelope with leaf pruning, the whole summary array without
+            scan_bytes = pk * 256 * 16 + pe * 32 if pe else 16.0 * n
             by.append({"sigma": s_, "queries_per_s": args.per_sigma * len(rs) / (tq * 1e-3),
                        "candidates_per_query": c, "pruning_ratio": 1.0 - c / n,
+                       "pages_kept_per_query": pk, "page_keep_ratio": pk / pe if pe else None,
+                       "summary_bytes_per_query": scan_bytes,
                        "dense_queries": sum(r["stats"][i]["dense_queries"] for r in rs) / len(rs),
                        "lbscan_ms": sum(r["stats"][i]["ms_lbscan"] for r in rs) / len(rs)})
         return {"form": label, "value": nq * len(rs) / (sum(ms) * 1e-3), "unit": "queries/s",
@@ -430,12 +438,15 @@ def main():
     if args.plain_steps > 0:
         ans_ref = []
         step(answers=ans_ref)
-        forms = [("plain_descent", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32, sd=P.PARIS_SEED_DESCENT))]
+        forms = [("plain_descent", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32, sd=P.PARIS_SEED_DESCENT)),
+                 ("plain_no_leaf_pruning", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32,
+                                                sd=P.PARIS_SEED_DESCENT, prune=False))]
         if model is not None:
             forms.append(("plain_learned", dict(md=P.PARIS_MODE_PLAIN, prec=P.PARIS_REFINE_FP32,
                                                 sd=P.PARIS_SEED_LEARNED)))
             forms.append(("headline_learned", dict(sd=P.PARIS_SEED_LEARNED)))
         forms.append(("headline_by_sigma", dict()))
+        forms.append(("headline_by_sigma_no_leaf_pruning", dict(prune=False)))
         for name, kw in forms:
             ans = []
             step(answers=ans, split=True, **kw)
@@ -445,7 +456,7 @@ def main():
                 step(collect=rs, split=True, **kw)
             beside[name] = summarize(rs, name)
             beside[name]["identical_answers"] = same
-            if name == "plain_descent":
+            if name == "plain_no_leaf_pruning":
                 plain_recs = rs
             if name == "headline_by_sigma":
                 per_sigma = beside[name]["by_sigma"]
@@ -498,8 +509,8 @@ def main():
             dense_q += s["dense_queries"]
     build_ms = sum(r["build_ms"] for r in recs) / steps
     query_ms = sum(r["query_ms"] for r in recs) / steps
-    # LB-scan roofline (the paper's scan: one query per pass over the summaries) from complete
-    # single-query scans: the sigma = 0.01 group of the plain-method steps
+    # LB-scan roofline (the paper's scan: one query per pass over every summary) from complete
+    # single-query scans: the sigma = 0.01 group of the plain-method steps without leaf pruning
     lb_src = plain_recs
     lb_gbs = lb_launch_ms = lb_bytes = None
     if lb_src:
@@ -514,9 +525,9 @@ def main():
     dominant = max(ph, key=ph.get)
     wl = {"n": n, "len": length, "queries": nq}    # committed DRAM counters hold only at their own sizes
     if dominant == "dense":
-        # algorithmic work of the BF16 screening: two passes (threshold, emission) of 2*len flops
-        # per (query, row) pair over the dense queries
-        flops = 2.0 * 2.0 * length * n * dense_q
+        # algorithmic work of the BF16 screening: 2*len flops per (query, row) pair in the
+        # emission pass over every row tile, plus the threshold pass over one row tile in 16
+        flops = 2.0 * length * n * dense_q * (1.0 + 1.0 / 16.0)
         tf = flops / (ph["dense"] * 1e-3) / 1e12
         peak_tf = bf16_peak_sustained()
         roof = {"kernel": "dense_kernel", "bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
@@ -532,7 +543,8 @@ def main():
         qt_used = recs[0]["stats"][0]["query_tile"]
         ach = lookups / (ph["lbscan"] * 1e-3) / 1e9
         clk_mhz = clk.get("sm_mhz") or 2070.0
-        peak_l = 32.0 * 152 * clk_mhz * 1e6 / 1e9
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_l = 32.0 * sms * clk_mhz * 1e6 / 1e9
         roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
                 "unit": "G shared-memory lookups/s", "frac": ach / peak_l,
                 "traffic": traffic_for("lbscan_batched_kernel", qt_used, wl),
@@ -559,7 +571,8 @@ def main():
         "lb_scan": None if lb_gbs is None else {
             "achieved_gbs": lb_gbs, "frac_of_hbm": lb_gbs / hbm_peak, "peak_kind": peak_kind,
             "us_per_launch": lb_launch_ms * 1e3, "bytes_per_launch": lb_bytes,
-            "launches": "complete one-query scans (sigma=0.01 group of the plain-method steps)"},
+            "launches": "complete one-query scans (sigma=0.01 group of the plain-method steps without leaf pruning)"},
+        "lb_scan_frac_of_hbm": None if lb_gbs is None else lb_gbs / hbm_peak,
         "build": {"ms": build_ms, "gb_per_s": n * length * 4 / (build_ms * 1e-3) / 1e9,
                   "series_per_s": n / (build_ms * 1e-3)},
         "query_ms_per_step": query_ms,

@@ -1,6 +1,7 @@
 """Multi-rank host logic on CPU gloo ranks (world size 2): job throughput aggregation (max time,
 summed units) and the k-best merge of row-range shards, whose merged answer must equal the
-oracle on the whole collection."""
+oracle on the whole collection -- including a planted cross-shard pair whose distances round to
+the same fp32 value, where only the exact distance gives the right order."""
 import os
 
 import numpy as np
@@ -9,6 +10,24 @@ import pytest
 torch = pytest.importorskip("torch")
 import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
+
+
+def planted_collection():
+    """3000 x 64 random walks; rows 5 (first shard) and 2000 (second shard) sit at squared
+    distances 1 + 2^-30 and 1 from query 0, which both round to the fp32 distance 1.0, and no
+    other row is that close. The lower row is the farther one."""
+    import synth
+    x = synth.random_walk(3000, 64, seed=12)
+    q = synth.random_walk(6, 64, seed=13)
+    base = np.zeros(64, np.float32)
+    base[0] = 40.0                                         # far from every z-normalised row
+    q[0] = base
+    a = base.copy()
+    a[1], a[2] = 1.0, 2.0 ** -15                           # |a - q|^2 = 1 + 2^-30
+    b = base.copy()
+    b[3] = 1.0                                             # |b - q|^2 = 1
+    x[5], x[2000] = a, b
+    return x, q
 
 
 def _worker(rank, world, port, q):
@@ -20,18 +39,34 @@ def _worker(rank, world, port, q):
         sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
         from oracle import knn as oknn
         from paper_2009_00166_gb300 import shards
-        import synth
         rate, slow = shards.job_throughput(100.0 + 50.0 * rank, 1000.0)
-        x = synth.random_walk(3000, 64, seed=12)
-        queries = synth.random_walk(5, 64, seed=13)
+        x, queries = planted_collection()
         half = x.shape[0] // world
         lo, hi = rank * half, (rank + 1) * half if rank < world - 1 else x.shape[0]
-        i_loc, d_loc = oknn.knn(x[lo:hi], queries, 4)              # the per-shard exact search
-        d, i = shards.merge_topk(torch.from_numpy(d_loc.astype(np.float32)), torch.from_numpy(i_loc), lo, 4)
-        want_i, _ = oknn.knn(x, queries, 4)
-        q.put((rank, rate, slow, bool(np.array_equal(i.numpy(), want_i))))
+        results = []
+        for k in (1, 2, 4):
+            # the per-shard exact search returns fp32 distances, as the library does
+            i_loc, d_loc = oknn.knn(x[lo:hi], queries, k)
+            d32 = d_loc.astype(np.float32)
+            d, i = shards.merge_topk_exact(torch.from_numpy(d32), torch.from_numpy(i_loc), lo, k, queries,
+                                           lambda r: x[lo + r])
+            want_i, want_d = oknn.knn(x, queries, k)
+            results.append((bool(np.array_equal(i.numpy(), want_i)),
+                            bool(np.allclose(d.numpy(), want_d, rtol=1e-6)), int(i[0, 0])))
+        _, d1 = oknn.knn(x[lo:hi], queries[:1], 1)         # each shard's best: fp32 distance 1.0
+        q.put((rank, rate, slow, results, float(np.float32(d1[0, 0]))))
     finally:
         dist.destroy_process_group()
+
+
+def test_planted_pair_rounds_to_one_fp32_distance():
+    """The fixture really is an fp32 tie that row order gets wrong (checked on one process)."""
+    from oracle import knn as oknn
+    x, q = planted_collection()
+    i, d = oknn.knn(x, q[:1], 2)
+    assert i[0].tolist() == [2000, 5]
+    assert np.float32(d[0, 0]) == np.float32(d[0, 1]) == np.float32(1.0)
+    assert d[0, 0] < d[0, 1]
 
 
 def test_two_gloo_ranks():
@@ -45,7 +80,10 @@ def test_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, rate, slow, ok in res:
+    for rank, rate, slow, results, d_first in res:
         assert slow == 150.0
         assert abs(rate - 2000.0 / 0.150) < 1e-6
-        assert ok
+        for same_rows, same_dist, first in results:
+            assert same_rows and same_dist
+            assert first == 2000
+        assert d_first == 1.0
