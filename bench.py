@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--clocks-csv", default="", help="keep the raw nvidia-smi clock samples of the timed region here")
+    p.add_argument("--batch-n", type=int, default=50_000_000,
+                   help="rows of the 4096-query batch workload reported beside (0: skip it)")
+    p.add_argument("--multi-scale", type=float, default=1.0,
+                   help="size factor of the three-collection workload reported beside (0: skip it)")
     return p.parse_args()
 
 
@@ -189,6 +193,120 @@ def traffic_for(kernel: str, query_tile: int = 0, workload: dict | None = None):
     if h.hexdigest()[:16] != d["source_sha"]:
         return None
     return float(d["bytes_per_launch"]) * (d.get("scale", 1.0))
+
+
+def timed(fn, stream, reps):
+    """Device time of `reps` calls of fn (after one untimed call), ms per call."""
+    import torch
+    fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, out
+
+
+def run_batch_workload(args, P, host20, model, dev, stream):
+    """4096-query batches over 50M x 256 random walks (rows [0, 20M) are the headline collection's;
+    sigma ~ U[0.01, 2], seed 5), k in {1, 10}: the batched mixed-precision form with the descent
+    and with the learned seed (index built once; batch time), beside the plain GPU method (one query
+    per lower-bound pass, fp32 refinement) on the first 512 queries of the batch."""
+    import numpy as np
+    import torch
+
+    import synth
+    n = args.batch_n
+    n20 = host20.shape[0]
+    t0 = time.perf_counter()
+    host = torch.empty((n, 256), dtype=torch.float32, pin_memory=True)
+    keep = min(n, n20) if host20.shape[1] == 256 else 0
+    if keep:
+        host[:keep].copy_(host20[:keep])
+    synth.random_walk(n, 256, seed=1, out=host.numpy(), start_row=keep)
+    q, sig, _ = synth.mixed_sigma_queries(host.numpy(), n, 256, 4096, 0.01, 2.0, seed=5)
+    gen_s = time.perf_counter() - t0
+    X = host.to(dev)
+    Q = torch.from_numpy(q).to(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    idx = P.paris_build_ex(X, 16, 256, bf16_shadow=True)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": f"{n}x256 random walks, 4096-query batches, sigma ~ U[0.01, 2]", "generate_s": gen_s,
+           "build_ms": ev[0].elapsed_time(ev[1]), "by_k": []}
+    sub = Q[:512]
+    for k in (1, 10):
+        head_ms, (hi, _, hst) = timed(lambda: P.paris_exact_knn_ex(idx, Q, k, mode=P.PARIS_MODE_BATCHED,
+                                                                    precision=P.PARIS_REFINE_MIXED, want_stats=True),
+                                      stream, 2)
+        rec = {"k": k, "batched_mixed_queries_per_s": 4096 / (head_ms * 1e-3), "batch_ms": head_ms,
+               "dense_queries": hst["dense_queries"], "pages_kept_per_query": hst["pages_kept"] / 4096,
+               "candidates_per_query": hst["candidates"] / 4096}
+        if model is not None:
+            P.paris_attach_seed_model(idx, model, 3)
+            lms, (li, _) = timed(lambda: P.paris_exact_knn_ex(idx, Q, k, mode=P.PARIS_MODE_BATCHED,
+                                                              precision=P.PARIS_REFINE_MIXED,
+                                                              seed=P.PARIS_SEED_LEARNED), stream, 1)
+            rec["learned_queries_per_s"] = 4096 / (lms * 1e-3)
+            rec["learned_identical_answers"] = bool(torch.equal(li, hi))
+        pms, (pi, _) = timed(lambda: P.paris_exact_knn_ex(idx, sub, k, mode=P.PARIS_MODE_PLAIN), stream, 1)
+        rec["plain_queries_per_s"] = 512 / (pms * 1e-3)
+        rec["plain_identical_answers"] = bool(torch.equal(pi, hi[:512]))
+        out["by_k"].append(rec)
+    idx.free()
+    del X, Q, host
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_three_collections(args, P, dev, stream):
+    """30M x 128 + 10M x 256 + 2M x 1024 random walks (dataset seeds 11, 12, 13) and 2048 queries
+    (683 / 683 / 682, sigma ~ U[0.01, 2], query seeds 111, 112, 113) in one multi-collection call,
+    k in {1, 10}, beside the plain GPU method per collection on 96 queries each."""
+    import numpy as np
+    import torch
+
+    import synth
+    f = args.multi_scale
+    shapes = [(int(30_000_000 * f), 128, 11, 683), (int(10_000_000 * f), 256, 12, 683),
+              (int(2_000_000 * f), 1024, 13, 682)]
+    t0 = time.perf_counter()
+    hosts, qs = [], []
+    for n, length, seed, m in shapes:
+        h = torch.empty((n, length), dtype=torch.float32, pin_memory=True)
+        synth.random_walk(n, length, seed=seed, out=h.numpy())
+        hosts.append(h)
+        qs.append(synth.mixed_sigma_queries(h.numpy(), n, length, m, 0.01, 2.0, seed=seed + 100)[0])
+    gen_s = time.perf_counter() - t0
+    Xs = [h.to(dev) for h in hosts]
+    Qs = [torch.from_numpy(q).to(dev) for q in qs]
+    idxs = [P.paris_build_ex(X, 16, 256, bf16_shadow=X.shape[1] <= 256) for X in Xs]
+    torch.cuda.synchronize()
+    out = {"workload": "30Mx128 + 10Mx256 + 2Mx1024 random walks (scaled by %g), 2048 queries in one call" % f,
+           "generate_s": gen_s, "by_k": []}
+    nq = sum(q.shape[0] for q in qs)
+    for k in (1, 10):
+        ms, (res, sts) = timed(lambda: P.paris_exact_knn_multi(idxs, Qs, k, precision=P.PARIS_REFINE_MIXED,
+                                                               want_stats=True), stream, 2)
+        rec = {"k": k, "multi_queries_per_s": nq / (ms * 1e-3), "call_ms": ms,
+               "query_tile": sts[0]["query_tile"], "dense_queries": [s_["dense_queries"] for s_ in sts]}
+        plain = []
+        same = True
+        for c, (idx, Q) in enumerate(zip(idxs, Qs)):
+            pms, (pi, _) = timed(lambda: P.paris_exact_knn_ex(idx, Q[:96], k, mode=P.PARIS_MODE_PLAIN), stream, 1)
+            plain.append(96 / (pms * 1e-3))
+            same = same and bool(torch.equal(pi, res[c][0][:96]))
+        rec["plain_queries_per_s_per_collection"] = plain
+        rec["plain_identical_answers"] = same
+        out["by_k"].append(rec)
+    for idx in idxs:
+        idx.free()
+    del Xs, Qs, hosts
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -489,6 +607,13 @@ def main():
         plan.free()
         idx.free()
 
+    # ---- beside it: the 4096-query batch workload and the three-collection call
+    batch_wl = multi_wl = None
+    if args.batch_n > 0:
+        batch_wl = run_batch_workload(args, P, host, model, dev, stream)
+    if args.multi_scale > 0:
+        multi_wl = run_three_collections(args, P, dev, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -584,6 +709,8 @@ def main():
         "dense_queries_per_step": dense_q / steps,
         "phase_ms_per_step": {kk: v / steps for kk, v in ph.items()},
         "per_sigma": per_sigma,
+        "batch_50m": batch_wl,
+        "three_collections": multi_wl,
         "refine_gbs": refine_gbs,
         "gpu_launches": int(launches),
         "clocks": clk,

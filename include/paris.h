@@ -123,7 +123,13 @@ typedef struct paris_query_opts {
                               that box of iSAX regions) passes the same test as a row; pages that
                               fail hold no row that could pass. 1: scan every summary (Alg. 8 as
                               printed). Same answers either way. */
-  int32_t reserved[2]; /* must be zero */
+  int32_t private_bsf; /* 0 (default): one best-so-far per query, shared through atomics, which
+                          every refining warp re-reads before each distance (ParIS+, Alg. 9);
+                          1: each warp refines against its own best-so-far, started from the
+                          query's threshold when it takes up the query and published only when
+                          it leaves it (the per-worker BSF of nb-ParIS+, Sec. 3.3.2), for the
+                          ablation of BSF sharing. Same answers either way. */
+  int32_t reserved[1]; /* must be zero */
 } paris_query_opts;
 
 typedef struct paris_query_stats {
@@ -142,6 +148,10 @@ typedef struct paris_query_stats {
                           slot and pair of queries; early abandoning skips the rest) */
   int64_t pages_examined; /* leaf pruning: page lower bounds computed (pages x queries) */
   int64_t pages_kept;     /* ... of which passed (their rows were scanned for that query) */
+  int64_t bsf_updates;    /* times refinement lowered a query's shared threshold */
+  int64_t list_rows;      /* BATCHED with leaf pruning: rows tested one query at a time by the
+                             list scan (queries whose kept pages fit a list of 16384 pages; the
+                             others share tile passes, counted in lb_lookups) */
 } paris_query_stats;
 
 /* paris_exact_knn with options (NULL = defaults) and optional host stats (NULL = none). */
@@ -217,6 +227,14 @@ const char* paris_last_error(void);
  * freed blocks cached for later calls; paris_trim_memory returns the cached blocks of the
  * current device to the driver (it synchronises the device first). */
 paris_status paris_trim_memory(void);
+
+/* Bound, in nanoseconds, of every device-side wait of the pipelined kernels (the tensor-core
+ * screening's waits between its copy, MMA and epilogue roles); 0 restores the default of 4 s;
+ * above 60 s: EINVAL. When a wait expires the kernel stops issuing work, waits (at most 0.1 s
+ * more) for its own copies and MMAs in flight, releases its tensor memory and returns; the call
+ * then fails with PARIS_ETIMEOUT and the device stays usable. Process-wide; takes effect at
+ * the next launch. */
+paris_status paris_set_wait_limit(uint64_t ns);
 
 typedef void* (*paris_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*paris_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);

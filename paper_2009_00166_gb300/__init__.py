@@ -37,6 +37,7 @@ from .binding import (  # noqa: F401
     paris_kernel_launches,
     paris_lb_scan,
     paris_leaf_scan,
+    paris_set_wait_limit,
     PARIS_PAGE_ROWS,
     paris_row_buckets,
     paris_last_error,

@@ -35,7 +35,7 @@ class BuildOpts(C.Structure):
 class QueryOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("query_tile", C.c_int32), ("chunk", C.c_int32),
                 ("precision", C.c_int32), ("seed", C.c_int32), ("no_leaf_pruning", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("private_bsf", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class QueryStats(C.Structure):
@@ -44,7 +44,7 @@ class QueryStats(C.Structure):
                 ("ms_descent", C.c_double), ("ms_lbscan", C.c_double), ("ms_refine", C.c_double),
                 ("ms_select", C.c_double), ("ms_dense", C.c_double), ("query_tile", C.c_int32),
                 ("rescreens", C.c_int32), ("lb_lookups", C.c_int64), ("pages_examined", C.c_int64),
-                ("pages_kept", C.c_int64)]
+                ("pages_kept", C.c_int64), ("bsf_updates", C.c_int64), ("list_rows", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +94,7 @@ def lib():
             "paris_kernel_launches": ([], C.c_uint64),
             "paris_set_allocator": ([ALLOC_FN, FREE_FN, VP], I32),
             "paris_trim_memory": ([], I32),
+            "paris_set_wait_limit": ([C.c_uint64], I32),
             "paris_index_describe": ([VP, C.POINTER(IndexView)], I32),
             "paris_breakpoints": ([I32, P], I32),
             "paris_export_sax": ([VP, P, VP], I32),
@@ -129,6 +130,11 @@ def paris_kernel_launches() -> int:
 
 def paris_trim_memory():
     _check(lib().paris_trim_memory())
+
+
+def paris_set_wait_limit(ns: int = 0):
+    """Bound of the device-side waits in ns (0: the default 4 s)."""
+    _check(lib().paris_set_wait_limit(int(ns)))
 
 
 def paris_last_error() -> str:
@@ -205,7 +211,7 @@ def paris_free(index: ParisIndex):
 def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, mode: int = PARIS_MODE_PLAIN,
                        query_tile: int = 0, chunk: int = 0, precision: int = PARIS_REFINE_FP32,
                        seed: int = PARIS_SEED_DESCENT, want_stats: bool = False, stream=None,
-                       leaf_pruning: bool = True):
+                       leaf_pruning: bool = True, private_bsf: bool = False):
     """paris_exact_knn_ex: returns (idx [nq][k] int64, dist [nq][k] float32[, stats dict]).
 
     Outputs are allocated like the queries (same device) when not given.
@@ -218,7 +224,7 @@ def paris_exact_knn_ex(index: ParisIndex, queries, k: int, out_idx=None, out_dis
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
     opts = QueryOpts(mode=mode, query_tile=query_tile, chunk=chunk, precision=precision, seed=seed,
-                     no_leaf_pruning=0 if leaf_pruning else 1)
+                     no_leaf_pruning=0 if leaf_pruning else 1, private_bsf=1 if private_bsf else 0)
     stats = QueryStats()
     _check(lib().paris_exact_knn_ex(index.handle, _ptr(queries), nq, k, _ptr(out_idx), _ptr(out_dist),
                                     C.byref(opts), C.byref(stats) if want_stats else None, _stream(stream)))

@@ -24,9 +24,13 @@ namespace paris {
 namespace {
 thread_local std::string g_err;
 paris_alloc_fn g_alloc = nullptr;
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // 4 s
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
 paris_free_fn g_free = nullptr;
 void* g_ctx = nullptr;
 }  // namespace
+
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 
 paris_status fail(paris_status s, const char* fmt, ...) {
   char buf[512];
@@ -123,12 +127,13 @@ paris_status check_status_word(const uint32_t* dev_status, cudaStream_t st, cons
   uint32_t s = 0;
   PARIS_CUDA(cudaMemcpyAsync(&s, dev_status, sizeof s, cudaMemcpyDeviceToHost, st));
   PARIS_CUDA(cudaStreamSynchronize(st));
+  // an expired wait leaves the later phases without their inputs: it is the error to report
+  if (s & DEV_TIMEOUT) return fail(PARIS_ETIMEOUT, "%s: a device-side wait expired", what);
   if (s & DEV_NONFINITE) return fail(PARIS_EINVAL, "%s: input holds a NaN or infinite value", what);
   if (s & DEV_CONT_OVERFLOW)
     return fail(PARIS_EINTERNAL, "%s: more than %d rows tie with the k-th neighbour within the fp32 bound",
                 what, kContCap);
   if (s & DEV_CAND_OVERFLOW) return fail(PARIS_EINTERNAL, "%s: candidate list overflow", what);
-  if (s & DEV_TIMEOUT) return fail(PARIS_ETIMEOUT, "%s: a device-side wait expired", what);
   return PARIS_OK;
 }
 
@@ -156,7 +161,7 @@ void release_index(paris_index* idx) {
   dev_free(idx->keys_sorted, (size_t)idx->n * 8, st);
   dev_free(idx->rows_sorted, (size_t)idx->n * 4, st);
   dev_free(idx->sax_sorted, (size_t)idx->n * PARIS_SAX_BYTES, st);
-  dev_free(idx->env, (size_t)idx->npages * 32, st);
+  dev_free(idx->env, (size_t)(idx->npages + (idx->npages + 15) / 16) * 32, st);
   dev_free(idx->beta_keys, (size_t)(idx->card - 1) * 8, st);
   dev_free(idx->beta_ext, (size_t)(idx->card + 1) * 8, st);
   release_shadow(idx);
@@ -271,7 +276,11 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
     sub.count = cs.count + offs[j];
     sub.rows = cs.rows + (int64_t)offs[j] * cs.cap;
     sub.lb = cs.lb + (int64_t)offs[j] * cs.cap;
-    if (cs.pagebits) sub.pagebits = cs.pagebits + (int64_t)offs[j] * page_words(idx->n);
+    if (cs.pagebits) {
+      sub.pagebits = cs.pagebits + (int64_t)offs[j] * page_words(idx->n);
+      sub.page_count = cs.page_count + offs[j];
+      sub.page_list = cs.page_list + (int64_t)offs[j] * page_list_cap(idx->n);
+    }
     return sub;
   };
   DevBuf scratch_status;
@@ -315,6 +324,7 @@ paris_status tuned_query_tile(const paris_index* idx, const QueryState& qs, cons
   for (int j = 0; j < nsub; ++j) PARIS_CUDA(cudaMemsetAsync(cs.count + offs[j], 0, (size_t)m * 4, st));
   // the trial scans' lookups are not the call's (tuning runs before any chunk is scanned)
   PARIS_CUDA(cudaMemsetAsync(qs.counters + 4, 0, 8, st));
+  PARIS_CUDA(cudaMemsetAsync(qs.counters + 6, 0, 8, st));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tuned[key] = best;
   *out = best;
@@ -328,6 +338,13 @@ extern "C" {
 const char* paris_last_error(void) { return g_err.c_str(); }
 
 uint64_t paris_kernel_launches(void) { return launch_count(); }
+
+paris_status paris_set_wait_limit(uint64_t ns) {
+  clear_error();
+  if (ns > 60000000000ull) return fail(PARIS_EINVAL, "wait limit above 60 s");
+  g_wait_ns.store(ns ? ns : kDefaultWaitNs);
+  return PARIS_OK;
+}
 
 paris_status paris_trim_memory(void) {
   clear_error();
@@ -619,8 +636,8 @@ static paris_status check_query_args(const paris_index* idx, const float* querie
 }
 
 static paris_status check_query_opts(const paris_index* idx, const paris_query_opts& o) {
-  for (int i = 0; i < 2; ++i)
-    if (o.reserved[i]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.reserved[0]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
+  if (o.private_bsf != 0 && o.private_bsf != 1) return fail(PARIS_EINVAL, "private_bsf must be 0 or 1");
   if (o.no_leaf_pruning != 0 && o.no_leaf_pruning != 1) return fail(PARIS_EINVAL, "no_leaf_pruning must be 0 or 1");
   if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
   if (o.seed == PARIS_SEED_LEARNED && !idx->seed_model)
@@ -686,6 +703,7 @@ struct KnnJob {
     PARIS_TRY(si.out(out_idx, (size_t)nq * k * sizeof(int64_t), st));
     PARIS_TRY(sd.out(out_dist, (size_t)nq * k * sizeof(float), st));
     PARIS_TRY(alloc_query_state(idx, nq, k, (const float*)sq.dev, qs, qblock, st));
+    qs.private_bsf = o.private_bsf;
     if (o.seed == PARIS_SEED_LEARNED) {
       if (!lkeys.alloc((size_t)nq * (idx->seed_r + 1) * 8, st)) return fail(PARIS_ENOMEM, "learned keys");
       qs.keys = lkeys.as<uint64_t>();
@@ -721,8 +739,9 @@ struct KnnJob {
            o_pk = take((size_t)((qc + 1) / 2 + 1) * idx->card * 16 * 4), o_pl = take((size_t)qc * 8), o_pm = take((size_t)qc * 4),
            o_ds = take((size_t)qc * 4), o_dn = take(8), o_no = take(8),
            o_dq = take(dense_query_rows(qc) * idx->len * 2), o_dm = take(dense_query_rows(qc) * 8),
-           o_pb = take((size_t)qc * page_words(idx->n) * 4), o_pls = take((size_t)page_count(idx->n) * 4),
-           o_pc = take(8);
+           o_pb = take((size_t)qc * page_words(idx->n) * 4),
+           o_pls = take((size_t)std::max<int64_t>(qc * page_list_cap(idx->n), page_count(idx->n)) * 4),
+           o_pc = take((size_t)qc * 4), o_ip = take((size_t)(qc + 1) * 4);
     if (!cblock.alloc(off, st)) return fail(PARIS_ENOMEM, "candidate lists (%zu bytes)", off);
     char* b = cblock.as<char>();
     cs.cap = cap;
@@ -753,6 +772,7 @@ struct KnnJob {
     cs.pagebits = prune ? (uint32_t*)(b + o_pb) : nullptr;
     cs.page_list = (uint32_t*)(b + o_pls);
     cs.page_count = (uint32_t*)(b + o_pc);
+    cs.item_prefix = (uint32_t*)(b + o_ip);
     paged_chunk = -1;
     pages_examined = 0;
     qt = o.mode == PARIS_MODE_BATCHED ? o.query_tile : 0;
@@ -763,7 +783,8 @@ struct KnnJob {
   paris_status page_pass(int64_t c) {
     if (!prune || o.mode != PARIS_MODE_BATCHED || paged_chunk == c) return PARIS_OK;
     timer.begin(2);
-    PARIS_TRY(launch_page_lb(idx, qs, cs.q0, cs.qc, cs.pagebits, nullptr, nullptr, st));
+    PARIS_TRY(launch_page_lb(idx, qs, cs.q0, cs.qc, cs.pagebits, cs.page_list, cs.page_count,
+                             page_list_cap(idx->n), st));
     timer.end(2);
     pages_examined += idx->npages * (int64_t)cs.qc;
     paged_chunk = c;
@@ -845,8 +866,7 @@ struct KnnJob {
     } else if (prune) {
       // the paper's one-query pass, over the pages whose envelope may hold a kept row
       for (int j = 0; j < cs.qc; ++j) {
-        PARIS_CUDA(cudaMemsetAsync(cs.page_count, 0, 4, st));
-        PARIS_TRY(launch_page_lb(idx, qs, cs.q0 + j, 1, cs.pagebits, cs.page_list, cs.page_count, st));
+        PARIS_TRY(launch_page_lb(idx, qs, cs.q0 + j, 1, nullptr, cs.page_list, cs.page_count, idx->npages, st));
         PARIS_TRY(launch_lbscan_pages(idx, qs, cs.q0 + j, cs.page_list, cs.page_count, cs.count + j,
                                       cs.rows + (int64_t)j * cs.cap, cs.lb + (int64_t)j * cs.cap, cs.cap, lb_status,
                                       mixed ? 1 : 0, st));
@@ -926,6 +946,8 @@ struct KnnJob {
       stats->lb_lookups = (int64_t)c[4];
       stats->pages_kept = (int64_t)c[5];
       stats->pages_examined = pages_examined;
+      stats->list_rows = (int64_t)c[6];
+      stats->bsf_updates = (int64_t)c[7];
     }
     return PARIS_OK;
   }
@@ -1257,7 +1279,9 @@ paris_status paris_leaf_scan(const paris_index* idx, const float* query, float t
   uint32_t tb = 0;
   std::memcpy(&tb, &threshold_sq, 4);
   PARIS_CUDA(cudaMemcpyAsync(qs.thr, &tb, 4, cudaMemcpyHostToDevice, st));
-  PARIS_TRY(launch_page_lb(idx, qs, 0, 1, out_bits, nullptr, nullptr, st));
+  DevBuf cnt;
+  if (!cnt.alloc(4, st)) return fail(PARIS_ENOMEM, "counter");
+  PARIS_TRY(launch_page_lb(idx, qs, 0, 1, out_bits, nullptr, cnt.as<uint32_t>(), 0, st));
   unsigned long long kept = 0;
   PARIS_CUDA(cudaMemcpyAsync(&kept, qs.counters + 5, 8, cudaMemcpyDeviceToHost, st));
   PARIS_TRY(check_status_word(qs.status, st, "paris_leaf_scan"));

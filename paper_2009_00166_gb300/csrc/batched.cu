@@ -250,6 +250,8 @@ struct ScanColl {
   const uint4* sax;      // index-order summaries (position p rotated by p mod 16)
   const uint32_t* pos_row;  // row of each index-order position
   const uint32_t* pagebits;  // [qc][words] kept pages per chunk query (NULL: every page)
+  const uint32_t* page_count;  // [qc] kept pages per chunk query: those within list_cap take the list scan
+  int64_t list_cap;
   int64_t words;
   int64_t n;
   const uint32_t* packed;
@@ -294,7 +296,6 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
   __shared__ float s_thr[QT];
   __shared__ bool s_active[QT];
   __shared__ int s_qid[QT];  // chunk query of each tile slot
-  __shared__ int s_skip;
   __shared__ uint32_t s_pages[kWinPages];  // kept pages of the current window (any order)
   __shared__ int s_np;
   const ScanColl& C = W.c[coll_of_block(W)];
@@ -316,22 +317,19 @@ __global__ void __launch_bounds__(kBThreads, 1) lbscan_batched_kernel(const __gr
   for (int tile = 0; tile < C.ntiles; ++tile) {
     const int qb = tile * QT;
     __syncthreads();  // the previous tile's tables and flags are no longer read
-    if (threadIdx.x == 0) {
-      int skip = 1;
-      for (int q = 0; q < QT; ++q) {
-        const int qq = qb + q;
-        const int qid = qq < qc ? (C.perm ? C.perm[qq] : qq) : 0;
-        // a list whose count passed its capacity has flagged its overflow (or was handed to the
-        // tensor-core screening beforehand): the query takes no further part in the scan
-        const bool act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qid) > cap);
-        s_active[q] = act;
-        s_qid[q] = qid;
-        if (act) skip = 0;
-      }
-      s_skip = skip;
+    bool act = false;
+    if (threadIdx.x < QT) {  // one thread per tile slot
+      const int q = threadIdx.x, qq = qb + q;
+      const int qid = qq < qc ? (C.perm ? C.perm[qq] : qq) : 0;
+      // a list whose count passed its capacity has flagged its overflow (or was handed to the
+      // tensor-core screening beforehand): the query takes no further part in the scan; with
+      // leaf pruning, a query whose kept pages fit its list is scanned by the list scan instead
+      act = qq < qc && !(stop_on_overflow && (int64_t)__ldcg(count + qid) > cap) &&
+            !(C.pagebits && (int64_t)C.page_count[qid] <= C.list_cap);
+      s_active[q] = act;
+      s_qid[q] = qid;
     }
-    __syncthreads();
-    if (s_skip) continue;
+    if (!__syncthreads_or(act)) continue;
     bool loaded = false;
     __half2 thh[NP];
     uint32_t ovf = 0u;   // bit q: the list of tile slot q passed its capacity
@@ -586,6 +584,8 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     C.sax = reinterpret_cast<const uint4*>(idx->sax_sorted);
     C.pos_row = idx->rows_sorted;
     C.pagebits = cs.pagebits;
+    C.page_count = cs.page_count;
+    C.list_cap = page_list_cap(idx->n);
     C.words = page_words(idx->n);
     C.n = idx->n;
     C.packed = cs.packed;
@@ -643,6 +643,10 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(W);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
+  // the queries that the leaf pruning left with few pages: one work item per few pages each
+  for (int j = 0; j < m; ++j)
+    if (jobs[j].cs->pagebits) PARIS_TRY(launch_lbscan_lists(jobs[j].idx, *jobs[j].qs, *jobs[j].cs, jobs[j].stop,
+                                                            jobs[j].status, st));
   return PARIS_OK;
 }
 

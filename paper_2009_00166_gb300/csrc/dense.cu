@@ -58,9 +58,10 @@ constexpr int MAX_KB = 4;           // len <= 256
 constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
 constexpr size_t DENSE_SMEM = 1024 + STAGES * B_STAGE_BYTES + 256;
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
-constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
+constexpr unsigned long long kDrainNs = 100000000ull;  // extra bound of the drain waits after an abort
 
 struct DenseParams {
+  uint64_t wait_ns;  // bound of every wait of a role on another role (paris_set_wait_limit)
   int64_t n;
   int len, nkb;
   int qtile, nd;         // nd < 0: the count of screened queries is read from nd_dev
@@ -108,12 +109,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase with the given parity; gives up (returning false) after kWaitNs or when
+// Waits for the phase with the given parity; gives up (returning false) at the deadline or when
 // another role has already given up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           uint64_t deadline) {
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
+    if (globaltimer() > deadline) return false;
+  }
+  return true;
+}
+// Drain wait of a role's own asynchronous work (its TMA copies or MMAs) before the CTA releases
+// shared and tensor memory: it ignores the abort flag and only stops at its own deadline.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
     if (globaltimer() > deadline) return false;
   }
   return true;
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   // pass 1 needs the upper ends of any k rows: it visits every SAMPLE-th tile; pass 2 visits all
   const int64_t tstep = (PHASE == 1 ? SAMPLE : 1);
   const int64_t tfirst = (int64_t)blockIdx.x * tstep, tstride = (int64_t)gridDim.x * tstep;
-  const uint64_t deadline = globaltimer() + kWaitNs;
+  const uint64_t deadline = globaltimer() + P.wait_ns;
   const int nkb = P.nkb;
 
   if (warp == 0) {
@@ -271,7 +280,8 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       // drain: the last loads must land before the CTA may exit
       const int issued = i;
       for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
-        mbar_wait(b_full + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), abort_flag, deadline + 100000000ull);
+        if (!mbar_wait_drain(b_full + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), deadline + kDrainNs))
+          *abort_flag = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
@@ -304,8 +314,8 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       }
       if (!ok) *abort_flag = 1;
       // drain: wait for the last MMAs before the TMEM is released
-      if (i > 0) mbar_wait(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), abort_flag,
-                           deadline + 100000000ull);
+      if (i > 0 && !mbar_wait_drain(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), deadline + kDrainNs))
+        *abort_flag = 1;
     }
   } else {  // ---- epilogue: warps 2..17, TMEM lane quadrant = warp % 4
     const int qd = warp & 3;
@@ -356,22 +366,27 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
         const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);  // rows of this chunk inside the series
         const uint32_t row_mask = nrow >= 32 ? 0xffffffffu : (nrow <= 0 ? 0u : ((1u << nrow) - 1u));
         uint32_t hit = 0u;
+        // the tests below are monotone in the dot product (round-toward functions of -2 dot
+        // plus a constant), so the largest of the 32 dots decides whether any row can pass
+        float dmax = __uint_as_float(v[0]);
+#pragma unroll
+        for (int jj = 1; jj < 32; ++jj) dmax = fmaxf(dmax, __uint_as_float(v[jj]));
         if (PHASE == 1) {
           // upper ends from the tile's norm range: ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max))
           const float Cq = __fadd_ru(qn, Mmax);
-          float val[32];
+          if (valid && __fadd_ru(__fmaf_ru(-2.0f, dmax, rng.y), Cq) < kth) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            val[jj] = __fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(v[jj]), rng.y), Cq);
-            hit |= (val[jj] < kth ? 1u : 0u) << jj;
+            for (int jj = 0; jj < 32; ++jj)
+              hit |= (__fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(v[jj]), rng.y), Cq) < kth ? 1u : 0u) << jj;
           }
           hit = valid ? (hit & row_mask) : 0u;
           while (hit) {  // rare: insert into the top-k
             const int jj = __ffs(hit) - 1;
             hit &= hit - 1u;
-            float x = 0.f;
+            uint32_t dv = 0u;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) x = (j == jj) ? val[j] : x;
+            for (int j = 0; j < 32; ++j) dv = (j == jj) ? v[j] : dv;
+            float x = __fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(dv), rng.y), Cq);
             if (x < kth) {
 #pragma unroll
               for (int j = 0; j < KMAX; ++j) {
@@ -389,9 +404,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
         } else {
           // drop unless rd(xn_min - 2 dot) <= ru(thr + M_max - |q|^2)
           const float R = __fsub_ru(__fadd_ru(thr_q, Mmax), qn);
+          if (valid && __fmaf_rd(-2.0f, dmax, rng.x) <= R) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
+            for (int jj = 0; jj < 32; ++jj)
+              hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
+          }
           hit = valid ? (hit & row_mask) : 0u;
           while (hit) {  // rare: the row's own interval, then emit
             const int jj = __ffs(hit) - 1;
@@ -687,6 +704,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
   PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
   DenseParams P;
+  P.wait_ns = wait_limit_ns();
   P.n = idx->n;
   P.len = idx->len;
   P.nkb = idx->len / BKE;

@@ -100,6 +100,9 @@ paris_status launch_unrotate_sax(const uint8_t* sax_rot, int64_t n, int w, uint8
                                  cudaStream_t st);
 paris_status radix_sort_index(uint64_t* keys, uint32_t* rows, int64_t n, cudaStream_t st);
 
+// Bound of the device-side waits of the pipelined kernels (paris_set_wait_limit), in ns.
+uint64_t wait_limit_ns();
+
 // Number of kernels this library has launched since it was loaded (all threads).
 void note_launches(int count);
 uint64_t launch_count();

@@ -16,6 +16,8 @@
 // page's; the fp32 sum of the page's entries is then at most the fp32 sum of the row's in the
 // same order (round-to-nearest addition is monotone), and a page that fails the row test
 // (LB^2 * (1 - 2^-16) > threshold) holds no row that passes it.
+#include <algorithm>
+
 #include "query.cuh"
 
 namespace paris {
@@ -87,70 +89,251 @@ __global__ void page_env_kernel(const uint4* __restrict__ sax_sorted, int64_t n,
   }
 }
 
-// Page lower bounds of one query per blockIdx.y against every page. Lane l of a warp takes page
-// 32 t + l, whose envelope is rotated by l mod 16; the query's symbols are rotated the same way
-// once, so the clamped word is formed with byte-wise SIMD min/max and looked up in the query's
-// fp32 table exactly like a row's summary (two copies of the table, one per half-warp, so the
-// 32 lookups of a step fall in 32 different banks). Writes one bit per page (kept) to
-// bits[q][words], and, when `list` is given (one query), appends the kept pages to it.
-__global__ void __launch_bounds__(kPageThreads) page_lb_kernel(
-    const uint4* __restrict__ env, int64_t npages, int64_t words, const float* __restrict__ qtable,
-    const uint8_t* __restrict__ qsym, const uint32_t* __restrict__ thr, int card, uint32_t* __restrict__ bits,
-    uint32_t* __restrict__ list, uint32_t* __restrict__ list_count, unsigned long long* __restrict__ pages_kept) {
-  extern __shared__ __align__(16) float s_tab[];
-  const int64_t q = blockIdx.y;
-  const float* table = qtable + q * (int64_t)card * 16;
-  for (int e = threadIdx.x; e < card * 16; e += blockDim.x) {
-    const float v = table[e];
-    const int c = e >> 4, i = e & 15;
-    s_tab[c * 64 + i] = v;
-    s_tab[c * 64 + 16 + i] = v;
+// Page lower bounds of one query per blockIdx.y, in two levels: super pages of 16 pages first
+// (their envelopes cover their pages'), then the 32 pages of every word whose super pages
+// passed. Lane l of a warp takes envelope 32 t + l, rotated by l mod 16; the query's symbols
+// are rotated the same way once, so the clamped word is formed with byte-wise SIMD min/max and
+// looked up in the query's fp32 table exactly like a row's summary (two copies of the table, one
+// per half-warp, so the 32 lookups of a step fall in 32 different banks).
+// Writes bit p of bits[q][words] for each kept page (the caller zeroes bits), counts the kept
+// pages of each query in list_count[q] and lists the first list_cap of them in lists[q][].
+__device__ __forceinline__ float box_lb(uint4 lo, uint4 hi, const uint4& sq, const uint32_t (&offp)[8], uint32_t tab) {
+  const uint32_t wv[4] = {__vmaxu4(__vminu4(sq.x, hi.x), lo.x), __vmaxu4(__vminu4(sq.y, hi.y), lo.y),
+                          __vmaxu4(__vminu4(sq.z, hi.z), lo.z), __vmaxu4(__vminu4(sq.w, hi.w), lo.w)};
+  float lb = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) {
+    const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
+    const uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
+    float v;
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    lb += v;
   }
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint4 sq = rot_bytes(*reinterpret_cast<const uint4*>(qsym + q * 16), lane & 15);
-  const float t = __uint_as_float(thr[q]);
-  uint32_t offp[8];
+  return lb;
+}
+
+__device__ __forceinline__ void fp32_table_offsets(int lane, uint32_t (&offp)[8]) {
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const uint32_t o0 = 4u * (16u * (lane >> 4) + ((2 * m + lane) & 15));
     const uint32_t o1 = 4u * (16u * (lane >> 4) + ((2 * m + 1 + lane) & 15));
     offp[m] = o0 | (o1 << 16);
   }
+}
+
+__device__ __forceinline__ void load_fp32_table(const float* __restrict__ table, int card, float* s_tab) {
+  for (int e = threadIdx.x; e < card * 16; e += blockDim.x) {
+    const float v = table[e];
+    const int c = e >> 4, i = e & 15;
+    s_tab[c * 64 + i] = v;
+    s_tab[c * 64 + 16 + i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kPageThreads) page_lb_kernel(
+    const uint4* __restrict__ senv, int64_t nsuper, const uint4* __restrict__ env, int64_t npages, int64_t words,
+    const float* __restrict__ qtable, const uint8_t* __restrict__ qsym, const uint32_t* __restrict__ thr, int card,
+    uint32_t* __restrict__ bits, uint32_t* __restrict__ lists, uint32_t* __restrict__ list_count, int64_t list_cap,
+    unsigned long long* __restrict__ pages_kept) {
+  extern __shared__ __align__(16) float s_tab[];
+  const int64_t q = blockIdx.y;
+  load_fp32_table(qtable + q * (int64_t)card * 16, card, s_tab);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint4 sq = rot_bytes(*reinterpret_cast<const uint4*>(qsym + q * 16), lane & 15);
+  const float t = __uint_as_float(thr[q]);
+  uint32_t offp[8];
+  fp32_table_offsets(lane, offp);
   __syncthreads();
   const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
   unsigned long long kept = 0;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t wd = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; wd < words; wd += nw) {
-    const int64_t pg = wd * 32 + lane;
-    const bool valid = pg < npages;
-    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-    if (valid) {
-      lo = __ldg(env + 2 * pg);
-      hi = __ldg(env + 2 * pg + 1);
-    }
-    const uint32_t wv[4] = {__vmaxu4(__vminu4(sq.x, hi.x), lo.x), __vmaxu4(__vminu4(sq.y, hi.y), lo.y),
-                            __vmaxu4(__vminu4(sq.z, hi.z), lo.z), __vmaxu4(__vminu4(sq.w, hi.w), lo.w)};
-    float lb = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
-      const uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
-      float v;
-      asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-      lb += v;
-    }
-    const bool keep = valid && lb * kPageKeepScale <= t;
-    const uint32_t m = __ballot_sync(PARIS_FULL_MASK, keep);
-    if (lane == 0) bits[q * words + wd] = m;
-    kept += __popc(m);
-    if (list && m) {
+  for (int64_t sw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; sw * 32 < nsuper; sw += nw) {
+    const int64_t sp = sw * 32 + lane;
+    const bool sval = sp < nsuper;
+    const uint4 slo = sval ? __ldg(senv + 2 * sp) : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 shi = sval ? __ldg(senv + 2 * sp + 1) : make_uint4(0u, 0u, 0u, 0u);
+    const float slb = box_lb(slo, shi, sq, offp, tab);
+    const uint32_t ks = __ballot_sync(PARIS_FULL_MASK, sval && slb * kPageKeepScale <= t);
+    // words of the 32 super pages: word 16 sw + j holds super pages 32 sw + 2j and 2j + 1
+    uint32_t pw = (ks | (ks >> 1)) & 0x55555555u;
+    while (pw) {
+      const int b = __ffs(pw) - 1;  // even: super page pair (b, b + 1)
+      pw &= pw - 1u;
+      const int64_t wd = sw * 16 + (b >> 1);
+      const int64_t pg = wd * 32 + lane;
+      const bool in_super = (ks >> (b + (lane >> 4))) & 1u;
+      const bool valid = in_super && pg < npages;
+      const uint4 lo = valid ? __ldg(env + 2 * pg) : make_uint4(0u, 0u, 0u, 0u);
+      const uint4 hi = valid ? __ldg(env + 2 * pg + 1) : make_uint4(0u, 0u, 0u, 0u);
+      const float lb = box_lb(lo, hi, sq, offp, tab);
+      const bool keep = valid && lb * kPageKeepScale <= t;
+      const uint32_t m = __ballot_sync(PARIS_FULL_MASK, keep);
+      if (!m) continue;
+      if (lane == 0 && bits) bits[q * words + wd] = m;
+      kept += __popc(m);
       uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(list_count, (uint32_t)__popc(m));
+      if (lane == 0) base = atomicAdd(list_count + q, (uint32_t)__popc(m));
       base = __shfl_sync(PARIS_FULL_MASK, base, 0);
-      if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)pg;
+      const uint32_t at = base + __popc(m & ((1u << lane) - 1u));
+      if (lists && keep && (int64_t)at < list_cap) lists[q * list_cap + at] = (uint32_t)pg;
     }
   }
   if (lane == 0 && kept && pages_kept) atomicAdd(pages_kept, kept);
+}
+
+// Super-page envelopes: the per-segment min and max over 16 consecutive pages' envelopes.
+__global__ void super_env_kernel(const uint4* __restrict__ env, int64_t npages, int64_t nsuper, uint4* __restrict__ senv) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += (int64_t)gridDim.x * blockDim.x) {
+    uint4 lo = make_uint4(~0u, ~0u, ~0u, ~0u), hi = make_uint4(0u, 0u, 0u, 0u);
+    for (int j = 0; j < 16; ++j) {
+      const int64_t pg = s * 16 + j;
+      if (pg >= npages) break;
+      const uint4 a = rot_bytes(env[2 * pg], 16 - (int)(pg & 15));  // to segment order
+      const uint4 b = rot_bytes(env[2 * pg + 1], 16 - (int)(pg & 15));
+      lo = make_uint4(__vminu4(lo.x, a.x), __vminu4(lo.y, a.y), __vminu4(lo.z, a.z), __vminu4(lo.w, a.w));
+      hi = make_uint4(__vmaxu4(hi.x, b.x), __vmaxu4(hi.y, b.y), __vmaxu4(hi.z, b.z), __vmaxu4(hi.w, b.w));
+    }
+    senv[2 * s] = rot_bytes(lo, (int)(s & 15));
+    senv[2 * s + 1] = rot_bytes(hi, (int)(s & 15));
+  }
+}
+
+// Work items of the list scan: per chunk query, ceil(min(kept, list_cap) / kItemPages) items
+// when its kept pages fit its list (the others go through the tile scan); prefix[qc] = total.
+constexpr int kItemPages = 64;
+__global__ void item_prefix_kernel(const uint32_t* __restrict__ list_count, int qc, int64_t list_cap,
+                                   uint32_t* __restrict__ prefix) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t acc = 0;
+  for (int j = 0; j < qc; ++j) {
+    prefix[j] = acc;
+    const uint32_t c = list_count[j];
+    if ((int64_t)c <= list_cap) acc += (c + kItemPages - 1) / kItemPages;
+  }
+  prefix[qc] = acc;
+}
+
+constexpr int kListThreads = 512;
+constexpr int kListStage = 64;
+
+__device__ __forceinline__ void list_flush(uint32_t* s_row, float* s_lb, int nflush, int lane, uint32_t* count,
+                                           uint32_t* out_rows, float* out_lb, int64_t cap, uint32_t* status) {
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, (uint32_t)nflush);
+  base = __shfl_sync(PARIS_FULL_MASK, base, 0);
+  for (int i = lane; i < nflush; i += 32) {
+    const uint32_t p = base + i;
+    if ((int64_t)p < cap) {
+      out_rows[p] = s_row[i];
+      out_lb[p] = s_lb[i];
+    } else {
+      atomicOr(status, DEV_CAND_OVERFLOW);
+    }
+  }
+}
+
+// The lower-bound scan of the chunk's queries whose kept pages fit their lists: work items of
+// kItemPages kept pages of one query, a contiguous range of items per CTA (so consecutive items
+// mostly share the query and its table); rows are tested exactly as in the one-query scan (fp32
+// table, LB^2 * (1 - 2^-16) <= threshold) and kept rows appended to the query's candidate list.
+__global__ void __launch_bounds__(kListThreads, 2) lbscan_list_kernel(
+    const uint4* __restrict__ sax, const uint32_t* __restrict__ pos_row, int64_t n, const float* __restrict__ qtable,
+    int card, const uint32_t* __restrict__ thr, const uint32_t* __restrict__ lists,
+    const uint32_t* __restrict__ list_count, int64_t list_cap, const uint32_t* __restrict__ prefix, int qc,
+    uint32_t* __restrict__ count, uint32_t* __restrict__ out_rows, float* __restrict__ out_lb, int64_t cap,
+    uint32_t* __restrict__ status, int stop_on_overflow, unsigned long long* __restrict__ rows_tested) {
+  extern __shared__ __align__(16) float s_tab[];
+  __shared__ uint32_t s_stage_row[kListThreads / 32][kListStage];
+  __shared__ float s_stage_lb[kListThreads / 32][kListStage];
+  __shared__ int s_q, s_skip;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  constexpr int kGpp = kPageRows / 32;
+  uint32_t offp[8];
+  fp32_table_offsets(lane, offp);
+  const uint32_t tab = (uint32_t)__cvta_generic_to_shared(s_tab);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t* st_row = s_stage_row[wib];
+  float* st_lb = s_stage_lb[wib];
+  const int64_t total = prefix[qc];
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(total, i0 + per);
+  int cur = -1;
+  float t = 0.f;
+  unsigned long long tested = 0;
+  int qw = 0;  // thread 0: query of the current item (items of a CTA are consecutive)
+  if (threadIdx.x == 0 && i0 < i1) {  // last j with prefix[j] <= i0
+    int lo = 0, hi = qc;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)prefix[mid] <= i0) lo = mid; else hi = mid;
+    }
+    qw = lo;
+  }
+  for (int64_t item = i0; item < i1; ++item) {
+    __syncthreads();  // the previous item's flags and table are no longer read
+    if (threadIdx.x == 0) {
+      while (qw + 1 < qc && (int64_t)prefix[qw + 1] <= item) ++qw;  // also skips queries without items
+      s_q = qw;
+      s_skip = stop_on_overflow && (int64_t)__ldcg(count + qw) > cap;
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q != cur) {
+      load_fp32_table(qtable + (int64_t)q * card * 16, card, s_tab);
+      t = __uint_as_float(thr[q]);
+      cur = q;
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    const int64_t j = item - prefix[q];
+    const int64_t kept = min((int64_t)list_count[q], list_cap);
+    const int64_t p0 = j * kItemPages, p1 = min(kept, p0 + kItemPages);
+    const int64_t groups = (p1 - p0) * kGpp;
+    const uint32_t* lst = lists + (int64_t)q * list_cap;
+    uint32_t* qrows = out_rows + (int64_t)q * cap;
+    float* qlb = out_lb + (int64_t)q * cap;
+    int fill = 0;
+    for (int64_t g = wib; g < groups; g += blockDim.x >> 5) {
+      const int64_t pos = ((int64_t)lst[p0 + g / kGpp] * kGpp + g % kGpp) * 32 + lane;
+      const uint4 word = pos < n ? __ldcs(sax + pos) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
+      float lb = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
+        const uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
+        float v;
+        asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+        lb += v;
+      }
+      const bool keep = pos < n && lb * kPageKeepScale <= t;
+      tested += pos < n ? 1u : 0u;
+      const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
+      if (mk) {
+        if (keep) {
+          const int p = fill + __popc(mk & lt_mask);
+          st_row[p] = pos_row[pos];
+          st_lb[p] = lb;
+        }
+        fill += __popc(mk);
+        __syncwarp();
+        if (fill >= 32) {
+          list_flush(st_row, st_lb, 32, lane, count + q, qrows, qlb, cap, status);
+          __syncwarp();
+          if (lane < fill - 32) {
+            st_row[lane] = st_row[32 + lane];
+            st_lb[lane] = st_lb[32 + lane];
+          }
+          fill -= 32;
+          __syncwarp();
+        }
+      }
+    }
+    if (fill > 0) list_flush(st_row, st_lb, fill, lane, count + q, qrows, qlb, cap, status);
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) tested += __shfl_xor_sync(PARIS_FULL_MASK, tested, o);
+  if (lane == 0 && tested) atomicAdd(rows_tested, tested);
 }
 
 int sm_count_leaf() {
@@ -164,12 +347,13 @@ int sm_count_leaf() {
 
 int64_t page_count(int64_t n) { return (n + kPageRows - 1) / kPageRows; }
 int64_t page_words(int64_t n) { return (page_count(n) + 31) / 32; }
+int64_t page_list_cap(int64_t n) { return std::min<int64_t>(page_count(n), 16384); }
 
 paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st) {
-  const int64_t n = idx->n, npages = page_count(n);
+  const int64_t n = idx->n, npages = page_count(n), nsuper = (npages + 15) / 16;
   idx->npages = npages;
   idx->sax_sorted = (uint8_t*)dev_alloc((size_t)n * PARIS_SAX_BYTES, st);
-  idx->env = (uint8_t*)dev_alloc((size_t)npages * 32, st);
+  idx->env = (uint8_t*)dev_alloc((size_t)(npages + nsuper) * 32, st);
   if (!idx->sax_sorted || !idx->env) return fail(PARIS_ENOMEM, "index-order summaries and leaf envelopes");
   const int sms = sm_count_leaf();
   const int64_t g1 = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
@@ -178,27 +362,52 @@ paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st) {
   const int64_t g2 = std::min<int64_t>((npages + 7) / 8, (int64_t)sms * 8);
   page_env_kernel<<<(unsigned)std::max<int64_t>(g2, 1), 256, 0, st>>>(
       reinterpret_cast<const uint4*>(idx->sax_sorted), n, npages, reinterpret_cast<uint4*>(idx->env));
-  note_launches(2);
+  uint4* senv = reinterpret_cast<uint4*>(idx->env) + 2 * npages;
+  super_env_kernel<<<(unsigned)std::max<int64_t>((nsuper + 255) / 256, 1), 256, 0, st>>>(
+      reinterpret_cast<const uint4*>(idx->env), npages, nsuper, senv);
+  note_launches(3);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }
 
 paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_t q0, int64_t nq, uint32_t* bits,
-                            uint32_t* list, uint32_t* list_count, cudaStream_t st) {
+                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st) {
   if (nq <= 0) return PARIS_OK;
   if (!qs.qsym) return fail(PARIS_EINTERNAL, "query symbols were not prepared");
-  const int64_t words = page_words(idx->n);
+  const int64_t words = page_words(idx->n), npages = idx->npages, nsuper = (npages + 15) / 16;
+  if (bits) PARIS_CUDA(cudaMemsetAsync(bits, 0, (size_t)nq * words * 4, st));
+  PARIS_CUDA(cudaMemsetAsync(list_count, 0, (size_t)nq * 4, st));
   const size_t smem = (size_t)idx->card * 64 * sizeof(float);
   PARIS_CUDA(cudaFuncSetAttribute(page_lb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // one query: enough blocks to cover the pages once; many queries: one block per query (the
-  // table is loaded once per block and each warp walks many words)
+  // one query: enough blocks to cover the super pages once; many queries: one block per query
+  // (the table is loaded once per block and each warp walks many words)
   const int wpb = kPageThreads / 32;
-  const int64_t bx = nq == 1 ? std::max<int64_t>(1, (words + wpb - 1) / wpb) : 1;
+  const int64_t sw = (nsuper + 31) / 32;
+  const int64_t bx = nq == 1 ? std::max<int64_t>(1, (sw + wpb - 1) / wpb) : 1;
   dim3 grid((unsigned)bx, (unsigned)nq);
-  page_lb_kernel<<<grid, kPageThreads, smem, st>>>(reinterpret_cast<const uint4*>(idx->env), idx->npages, words,
+  const uint4* env = reinterpret_cast<const uint4*>(idx->env);
+  page_lb_kernel<<<grid, kPageThreads, smem, st>>>(env + 2 * npages, nsuper, env, npages, words,
                                                   qs.qtable + q0 * (int64_t)idx->card * 16, qs.qsym + q0 * 16,
-                                                  qs.thr + q0, idx->card, bits, list, list_count, qs.counters + 5);
+                                                  qs.thr + q0, idx->card, bits, lists, list_count, list_cap,
+                                                  qs.counters + 5);
   note_launches(1);
+  PARIS_CUDA(cudaGetLastError());
+  return PARIS_OK;
+}
+
+paris_status launch_lbscan_lists(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                                 int stop_on_overflow, uint32_t* status, cudaStream_t st) {
+  if (cs.qc <= 0) return PARIS_OK;
+  const int64_t list_cap = page_list_cap(idx->n);
+  item_prefix_kernel<<<1, 32, 0, st>>>(cs.page_count, cs.qc, list_cap, cs.item_prefix);
+  const size_t smem = (size_t)idx->card * 64 * sizeof(float);
+  PARIS_CUDA(cudaFuncSetAttribute(lbscan_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = sm_count_leaf() * 2;
+  lbscan_list_kernel<<<grid, kListThreads, smem, st>>>(
+      reinterpret_cast<const uint4*>(idx->sax_sorted), idx->rows_sorted, idx->n,
+      qs.qtable + cs.q0 * (int64_t)idx->card * 16, idx->card, qs.thr + cs.q0, cs.page_list, cs.page_count, list_cap,
+      cs.item_prefix, cs.qc, cs.count, cs.rows, cs.lb, cs.cap, status, stop_on_overflow, qs.counters + 6);
+  note_launches(2);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }

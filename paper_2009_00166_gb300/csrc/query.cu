@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
     int qc, int64_t cap, const uint32_t* __restrict__ prefix, const uint32_t* __restrict__ count,
     const uint32_t* __restrict__ rows, const float* __restrict__ lbs, float* __restrict__ Fout,
     uint32_t* __restrict__ thr, unsigned long long* __restrict__ bsf, int k, float cg,
-    unsigned long long* __restrict__ counters) {
+    unsigned long long* __restrict__ counters, int private_bsf) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -467,9 +467,20 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
   const float* qp = nullptr;
   float best = CUDART_INF_F;  // lane j < have: j-th best completed F of this warp and query
   int have = 0;
-  unsigned long long touched = 0;
+  unsigned long long touched = 0, updates = 0;
+  // private best-so-far (nb-ParIS+ ablation): the warp's own threshold and best (F, row) for the
+  // current query, published to the query's shared ones only when the warp leaves the query
+  float tp = CUDART_INF_F;
+  unsigned long long pbest = ~0ull;
+  uint32_t pthr = 0xffffffffu;
+  auto publish = [&](int64_t qi) {
+    if (!private_bsf || lane != 0) return;
+    if (pbest != ~0ull) atomicMin(bsf + qi, pbest);
+    if (pthr != 0xffffffffu && atomicMin(thr + qi, pthr) > pthr) ++updates;
+  };
   for (int64_t item0 = gw * 32; item0 < total; item0 += W * 32) {
     if (cur < 0 || item0 >= next_bound) {
+      if (cur >= 0) publish(q0 + cur);
       if (cur < 0) {
         int lo = 0, hi = qc;  // last j with prefix[j] <= item0
         while (hi - lo > 1) {
@@ -487,6 +498,9 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
       if (vec) qv.load(qp, len, lane);
       best = CUDART_INF_F;
       have = 0;
+      tp = __uint_as_float(ld_volatile_u32(thr + q0 + cur));  // the seed threshold
+      pbest = ~0ull;
+      pthr = 0xffffffffu;
     }
     const int64_t qi = q0 + cur;
     const int64_t i = item0 - prefix[cur] + lane;
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
     const int64_t slot = (int64_t)cur * cap + i;
     const uint32_t row = valid ? rows[slot] : 0u;
     const float lbv = valid ? lbs[slot] : CUDART_INF_F;
-    float t = __uint_as_float(ld_volatile_u32(thr + qi));
+    float t = private_bsf ? tp : __uint_as_float(ld_volatile_u32(thr + qi));
     uint32_t todo = __ballot_sync(PARIS_FULL_MASK, valid && lbv * kKeepScale <= t);
     float myF = CUDART_INF_F;
     while (todo) {
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
       todo &= todo - 1;
       const uint32_t r = __shfl_sync(PARIS_FULL_MASK, row, b);
       const float lb_b = __shfl_sync(PARIS_FULL_MASK, lbv, b);
-      t = fminf(t, __uint_as_float(ld_volatile_u32(thr + qi)));
+      if (!private_bsf) t = fminf(t, __uint_as_float(ld_volatile_u32(thr + qi)));
       if (lb_b * kKeepScale > t) continue;
       ++touched;
       const float* xr = series + (int64_t)r * len;
@@ -511,9 +525,13 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
       if (F <= t) {
         if (k == 1) {
           const uint32_t nb = up_scaled_bits(F, cg);
-          if (lane == 0) {
-            atomicMin(bsf + qi, ((unsigned long long)__float_as_uint(F) << 32) | r);
-            atomicMin(thr + qi, nb);
+          const unsigned long long packed = ((unsigned long long)__float_as_uint(F) << 32) | r;
+          if (private_bsf) {
+            pbest = min(pbest, packed);
+            pthr = min(pthr, nb);
+          } else if (lane == 0) {
+            atomicMin(bsf + qi, packed);
+            if (atomicMin(thr + qi, nb) > nb) ++updates;
           }
           t = fminf(t, __uint_as_float(nb));
         } else if (k <= 32) {
@@ -527,7 +545,11 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
             if (have == k) {
               float kth = __shfl_sync(PARIS_FULL_MASK, best, k - 1);
               uint32_t nb = up_scaled_bits(kth, cg);
-              if (lane == 0 && nb < __float_as_uint(t)) atomicMin(thr + qi, nb);
+              if (private_bsf) {
+                pthr = min(pthr, nb);
+              } else if (lane == 0 && nb < __float_as_uint(t)) {
+                if (atomicMin(thr + qi, nb) > nb) ++updates;
+              }
               t = fminf(t, __uint_as_float(nb));
             }
           }
@@ -535,8 +557,11 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(
       }
     }
     if (valid) Fout[slot] = myF;
+    if (private_bsf) tp = t;
   }
+  if (cur >= 0) publish(q0 + cur);
   if (lane == 0 && touched) atomicAdd(&counters[1], touched);
+  if (lane == 0 && updates) atomicAdd(&counters[7], updates);
 }
 
 // Candidate order for refinement: 32 buckets of LB / (seed threshold), lowest first, so that
@@ -983,7 +1008,7 @@ paris_status launch_refine(const paris_index* idx, const QueryState& qs, const C
 #define REF(IT)                                                                                   \
   refine_kernel<IT><<<grid, kRefineThreads, 0, st>>>(idx->series, idx->len, vec, qs.queries, cs.q0, cs.qc, \
                                                      cs.cap, cs.prefix, cs.count, cs.rows2, cs.lb2, cs.F, qs.thr, \
-                                                     qs.bsf, qs.k, qs.cg, qs.counters)
+                                                     qs.bsf, qs.k, qs.cg, qs.counters, qs.private_bsf)
   switch (it) {
     case 1: REF(1); break;
     case 2: REF(2); break;

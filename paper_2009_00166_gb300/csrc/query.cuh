@@ -25,10 +25,12 @@ struct QueryState {
   float* seed = nullptr;           // [nq]
   uint32_t* status = nullptr;      // [1]
   unsigned long long* counters = nullptr;  // [8]: candidates, refined, contenders, leaf rows, batched-scan
-                                           // lookups, pages kept by the leaf pruning, (2 unused)
+                                           // lookups, pages kept by the leaf pruning, list-scan rows,
+                                           // shared best-so-far updates
   float cg = 1.f;                  // (1+gamma)/(1-gamma), rounded up, gamma = gamma_{len+2}
   const uint64_t* keys = nullptr;  // [nq][nk] approximate-search keys (NULL: qkey only)
   int nk = 1;
+  int private_bsf = 0;             // refinement keeps a per-warp best-so-far (nb-ParIS+ ablation)
 };
 
 // Candidate lists of a chunk of queries [q0, q0 + qc).
@@ -61,8 +63,9 @@ struct ChunkState {
   int64_t dq_rows = 0;             // qc rounded up to whole query tiles
   // leaf pruning (NULL pagebits: every page is scanned)
   uint32_t* pagebits = nullptr;    // [qc][page words]: bit p of query j = page p may hold a kept row
-  uint32_t* page_list = nullptr;   // [npages] kept pages of the query being scanned (PLAIN)
-  uint32_t* page_count = nullptr;  // [1]
+  uint32_t* page_list = nullptr;   // BATCHED: [qc][page list cap] kept pages per query; PLAIN: [npages]
+  uint32_t* page_count = nullptr;  // [qc] kept pages per query (may exceed the list cap)
+  uint32_t* item_prefix = nullptr; // [qc + 1] work items of the list scan
 };
 
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
@@ -76,11 +79,16 @@ paris_status launch_lbscan_threshold(const paris_index* idx, const float* table,
 // Leaf pruning (leaf.cu): index-order summaries and page envelopes (build), page lower bounds.
 int64_t page_count(int64_t n);
 int64_t page_words(int64_t n);
+int64_t page_list_cap(int64_t n);  // kept pages a BATCHED query may list (more: tile scan)
 paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st);
-// Page bits of chunk queries [q0, q0 + nq) into bits ([nq][words]); with one query, `list` and
-// `list_count` (zeroed by the caller) also receive the kept pages.
+// Page bits of chunk queries [q0, q0 + nq) into bits ([nq][words], may be NULL), kept page counts into
+// list_count [nq] and the first list_cap kept pages of each into lists [nq][list_cap] (may be
+// NULL); bits and counts are zeroed first.
 paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_t q0, int64_t nq, uint32_t* bits,
-                            uint32_t* list, uint32_t* list_count, cudaStream_t st);
+                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st);
+// The scan of the chunk's queries whose kept pages fit their lists (the others: tile scan).
+paris_status launch_lbscan_lists(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
+                                 int stop_on_overflow, uint32_t* status, cudaStream_t st);
 // The lower-bound scan of query q over the index-order pages in page_list (count on the device).
 paris_status launch_lbscan_pages(const paris_index* idx, const QueryState& qs, int64_t q, const uint32_t* page_list,
                                  const uint32_t* page_count, uint32_t* count, uint32_t* rows, float* lb, int64_t cap,

@@ -38,29 +38,33 @@ def _walk_chunk(seed: int, chunk: int, rows: int, length: int) -> np.ndarray:
 
 
 def random_walk(n_rows: int, length: int, seed: int, out: np.ndarray | None = None,
-                threads: int | None = None) -> np.ndarray:
+                threads: int | None = None, start_row: int = 0) -> np.ndarray:
     """Rows [0, n_rows) of the z-normalised random-walk dataset ``seed``; float32 [n_rows][length].
 
     ``out`` may be any writable float32 C-contiguous array of that shape (e.g. a numpy view of a
-    pinned host tensor); chunks are filled by a thread pool (numpy releases the GIL).
+    pinned host tensor); chunks are filled by a thread pool (numpy releases the GIL). With
+    ``start_row`` only rows [start_row, n_rows) of ``out`` are written (the rows before it are
+    left as they are, e.g. already copied from a smaller collection of the same seed).
     """
     if out is None:
         out = np.empty((n_rows, length), dtype=np.float32)
     assert out.shape == (n_rows, length) and out.dtype == np.float32
     n_chunks = (n_rows + CHUNK - 1) // CHUNK
+    first = start_row // CHUNK
 
     def fill(c: int) -> None:
         r0 = c * CHUNK
         r1 = min(n_rows, r0 + CHUNK)
-        out[r0:r1] = _walk_chunk(seed, c, r1 - r0, length)
+        lo = max(r0, start_row)
+        out[lo:r1] = _walk_chunk(seed, c, r1 - r0, length)[lo - r0:]
 
     threads = threads or min(32, os.cpu_count() or 1)
-    if n_chunks == 1 or threads == 1:
-        for c in range(n_chunks):
+    if n_chunks - first <= 1 or threads == 1:
+        for c in range(first, n_chunks):
             fill(c)
     else:
         with ThreadPoolExecutor(threads) as ex:
-            list(ex.map(fill, range(n_chunks)))
+            list(ex.map(fill, range(first, n_chunks)))
     return out
 
 

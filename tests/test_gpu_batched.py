@@ -39,14 +39,21 @@ def run(P, idx, q, k, **kw):
 def test_batched_equals_oracle(setup, qt, k):
     P, idx, q, want = setup
     for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
-        gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=prec)
-        assert st["query_tile"] in (2, 4, 8, 12, 16, 24) and (qt == 0 or st["query_tile"] == qt)
-        # at most 16 slots per row group and query pair (a CTA's range end may add a few
-        # partial unrolled steps)
-        full = 16 * (st["query_tile"] // 2) * 32 * ((x_rows(idx) + 31) // 32) * (-(-len(q) // st["query_tile"]))
-        assert 0 < st["lb_lookups"] <= 1.05 * full
-        assert np.array_equal(gi, want[k][0])
-        assert np.allclose(gd, want[k][1], rtol=1e-5, atol=0)
+        for prune in (False, True):
+            gi, gd, st = run(P, idx, q, k, mode=P.PARIS_MODE_BATCHED, query_tile=qt, precision=prec,
+                             leaf_pruning=prune)
+            assert st["query_tile"] in (2, 4, 8, 12, 16, 24) and (qt == 0 or st["query_tile"] == qt)
+            # at most 16 slots per row group and query pair (a CTA's range end may add a few
+            # partial unrolled steps); with leaf pruning, queries that keep few pages take the
+            # list scan (no tile lookups) and the tiles visit only kept pages
+            full = 16 * (st["query_tile"] // 2) * 32 * ((x_rows(idx) + 31) // 32) * (-(-len(q) // st["query_tile"]))
+            assert (0 <= st["lb_lookups"] if prune else 0 < st["lb_lookups"]) and st["lb_lookups"] <= 1.05 * full
+            if prune:
+                assert st["list_rows"] <= st["pages_kept"] * 256
+            else:
+                assert st["list_rows"] == 0
+            assert np.array_equal(gi, want[k][0])
+            assert np.allclose(gd, want[k][1], rtol=1e-5, atol=0)
 
 
 def test_batched_equals_plain_and_small_chunks(setup):
