@@ -56,6 +56,13 @@ def parse():
                    help="rows of the 4096-query batch workload reported beside (0: skip it)")
     p.add_argument("--multi-scale", type=float, default=1.0,
                    help="size factor of the three-collection workload reported beside (0: skip it)")
+    p.add_argument("--learned-study", action="store_true",
+                   help="instead of the headline: train the learned seed on 2M labelled pairs over 50M x 256 and "
+                        "compare it with the descent seed on 10K held-out queries (one JSON line)")
+    p.add_argument("--study-n", type=int, default=50_000_000)
+    p.add_argument("--study-pairs", type=int, default=2_000_000)
+    p.add_argument("--study-heldout", type=int, default=10_000)
+    p.add_argument("--study-epochs", type=int, default=4)
     return p.parse_args()
 
 
@@ -309,6 +316,88 @@ def run_three_collections(args, P, dev, stream):
     return out
 
 
+def run_learned_study(args):
+    """The learned best-so-far proposal at full size: 50M x 256 random walks (seed 1); 2M training
+    pairs (query PAA, 12-bit bucket of its exact nearest neighbour) from queries with sigma ~
+    U[0.1, 1.0] (seed 20), labelled by the exact search itself; 10K held-out queries, half at
+    sigma 0.1 and half at 1.0 (seeds 30, 31). Per sigma: seed looseness (seed / exact squared
+    distance), kept pages and candidates per query and queries/s of the batched mixed form with
+    the descent seed and with the learned seed, and of the plain method on 500 queries each."""
+    import numpy as np
+    import torch
+
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n = args.study_n
+    t0 = time.perf_counter()
+    host = torch.empty((n, 256), dtype=torch.float32, pin_memory=True)
+    synth.random_walk(n, 256, seed=1, out=host.numpy())
+    X = host.to(dev)
+    gen_s = time.perf_counter() - t0
+    idx = P.paris_build_ex(X, 16, 256, bf16_shadow=True)
+    torch.cuda.synchronize()
+    # labels from the exact search, in batches
+    t0 = time.perf_counter()
+    m = args.study_pairs
+    tq, _, _ = synth.mixed_sigma_queries(host.numpy(), n, 256, m, 0.1, 1.0, seed=20)
+    labels = np.empty(m, np.int32)
+    paa = torch.empty((m, 16), dtype=torch.float64, device=dev)
+    B = 65536
+    for b0 in range(0, m, B):
+        Qb = torch.from_numpy(tq[b0:b0 + B]).to(dev)
+        rows, _ = P.paris_exact_knn_ex(idx, Qb, 1, mode=P.PARIS_MODE_BATCHED, precision=P.PARIS_REFINE_MIXED)
+        labels[b0:b0 + B] = P.paris_row_buckets(idx, rows.cpu().numpy()[:, 0])
+        paa[b0:b0 + B] = P.paris_encode(Qb, 16, 256, want_paa=True)[2]
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    del tq
+    t0 = time.perf_counter()
+    md = P.SeedModel(1)
+    losses = md.train(paa, torch.from_numpy(labels).to(dev), batch=1024, epochs=args.study_epochs, lr=2e-3,
+                      order_seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    P.paris_attach_seed_model(idx, md, 3)
+    groups = []
+    half = args.study_heldout // 2
+    for gi, (sigma, seed) in enumerate(((0.1, 30), (1.0, 31))):
+        q, _, _ = synth.mixed_sigma_queries(host.numpy(), n, 256, half, sigma, sigma, seed=seed)
+        Q = torch.from_numpy(q).to(dev)
+        rec = {"sigma": sigma, "queries": half}
+        ref = None
+        for name, sd in (("descent", P.PARIS_SEED_DESCENT), ("learned", P.PARIS_SEED_LEARNED)):
+            _, seeds = P.paris_approx_search(idx, Q, 1, sd)
+            ms, (ri, rd, st) = timed(lambda: P.paris_exact_knn_ex(idx, Q, 1, mode=P.PARIS_MODE_BATCHED,
+                                                                    precision=P.PARIS_REFINE_MIXED, seed=sd,
+                                                                    want_stats=True), stream, 2)
+            if ref is None:
+                ref = (ri, rd)
+            true_sq = rd.double()[:, 0] ** 2
+            pms, (pi, _, pst) = timed(lambda: P.paris_exact_knn_ex(idx, Q[:500], 1, mode=P.PARIS_MODE_PLAIN, seed=sd,
+                                                                     want_stats=True), stream, 1)
+            rec[name] = {"seed_looseness_mean": float((seeds.double() / true_sq.clamp_min(1e-30)).mean()),
+                         "batched_mixed_queries_per_s": half / (ms * 1e-3),
+                         "pages_kept_per_query": st["pages_kept"] / half,
+                         "candidates_per_query": st["candidates"] / half,
+                         "pruning_ratio": 1.0 - st["candidates"] / half / n,
+                         "dense_queries": st["dense_queries"],
+                         "plain_queries_per_s": 500 / (pms * 1e-3),
+                         "plain_candidates_per_query": pst["candidates"] / 500,
+                         "identical_answers": bool(torch.equal(ri, ref[0]))}
+        groups.append(rec)
+    line = {"metric": "learned seed vs descent seed, exact 1-NN at %dx256" % n, "data": "synthetic",
+            "config": {"workload": f"{n}x256 random walks; {m} training pairs sigma ~ U[0.1, 1.0]; "
+                                   f"{args.study_heldout} held-out queries at sigma 0.1 and 1.0"},
+            "generate_s": gen_s, "label_s": label_s, "train_s": train_s, "epochs": args.study_epochs,
+            "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "by_sigma": groups}
+    md.free()
+    idx.free()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -378,6 +467,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.learned_study:
+        run_learned_study(args)
         return
     import numpy as np
     import torch

@@ -17,16 +17,16 @@
 // that survive get the exact interval above. Pass 1 ranks the looser upper ends
 // ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max), which still bound the distance from above.
 //
-// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries in tensor memory
-// (lane = query, K-major BF16 pairs per column, written once with tcgen05.st); warp 0 streams
-// 64-row tiles of the BF16 shadow of the series into a 7-stage shared-memory ring with TMA
-// (128-byte swizzle), warp 1 issues the tensor-core MMAs (one thread; A from tensor memory, B
-// from shared memory) of both query tiles against each row tile into double-buffered TMEM
-// accumulators (2 x 2 x 128 x 64 fp32), and warps 2-17 read the accumulators back (tcgen05.ld)
-// and run the screening epilogue: one query per thread and 32 rows of the tile per warp. The
-// epilogue reads each tile's norm range from global memory two tiles ahead, and a row's own
-// norms only for the rare pairs that pass the range test. Each row tile read from HBM serves
-// 256 queries.
+// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries in shared memory
+// (BF16, K-major, 128-byte swizzle, written once per launch); warp 0 streams the row tiles of
+// the BF16 shadow of the series (128 rows x 64 K elements per stage) into a 6-stage ring with
+// TMA, warp 1 issues the tensor-core MMAs (one thread; 128 x 128 x 16 per instruction, both
+// operands from shared memory) of both query tiles against each row tile into double-buffered
+// TMEM accumulators (2 x 2 x 128 x 128 fp32, all 512 columns), and warps 2-17 read the
+// accumulators back (tcgen05.ld) and run the screening epilogue: one query per thread and 64
+// rows of the tile per warp, 32 at a time. The epilogue reads each 64-row norm range from global
+// memory two tiles ahead, and a row's own norms only for the rare pairs that pass the range
+// test. Each row tile read from HBM serves 256 queries.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -43,20 +43,22 @@ namespace paris {
 namespace {
 
 constexpr int BM = 128;             // queries per tile (MMA M)
-constexpr int BN = 64;              // series rows per tile (MMA N)
+constexpr int BN = 128;             // series rows per tile (MMA N)
+constexpr int RT = 64;              // rows per norm-range tile (xtile) and per norm block
 constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
 constexpr int QTILES = 2;           // query tiles sharing each row tile
-constexpr int STAGES = 7;           // shared-memory ring depth for row tiles
+constexpr int STAGES = 6;           // shared-memory ring depth: one (row tile, K block) per stage
 constexpr int DENSE_THREADS = 576;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-17: epilogue
-constexpr int EPI_WARPS = 16;       // per TMEM lane quadrant: one per (query tile, 32-row half)
+constexpr int EPI_WARPS = 16;       // per TMEM lane quadrant: one per (query tile, 64-row half)
 constexpr int SAMPLE = 16;          // pass 1 visits one row tile in SAMPLE
 constexpr int KMAX = 16;            // largest k the screening supports
-constexpr uint32_t TMEM_COLS = 512;  // accumulators (2 buffers x 2 query tiles x 64) then the query tiles
-constexpr uint32_t A_COL0 = 2 * QTILES * BN;  // first TMEM column of the query tiles (K/2 columns each)
+constexpr uint32_t TMEM_COLS = 512;  // accumulators: 2 buffers x 2 query tiles x 128 columns
 constexpr int MAX_KB = 4;           // len <= 256
 
-constexpr size_t B_STAGE_BYTES = (size_t)MAX_KB * BN * 128;
-constexpr size_t DENSE_SMEM = 1024 + STAGES * B_STAGE_BYTES + 256;
+constexpr size_t KBLK_BYTES = (size_t)BN * 128;      // one K block of a row tile (= of a query tile)
+constexpr size_t A_BYTES = (size_t)QTILES * MAX_KB * BM * 128;
+constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * KBLK_BYTES + 256;
+static_assert(BM * 128 == KBLK_BYTES, "query and row tiles share the K-block shape");
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
 constexpr unsigned long long kDrainNs = 100000000ull;  // extra bound of the drain waits after an abort
 
@@ -147,25 +149,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// BF16 MMA with FP32 accumulation into tensor memory: A (the query tile, K-major) read from
-// tensor memory, B (a row tile) from shared memory through its descriptor.
-__device__ __forceinline__ void umma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                                 uint32_t accumulate) {
+// BF16 MMA with FP32 accumulation into tensor memory: A (a query tile) and B (a row tile), both
+// K-major in shared memory, through their descriptors.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           d_tmem),
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -197,8 +188,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   if (P.qtile * BM >= nd) return;
   const int nq_tiles = (P.qtile + 1) * BM < nd ? 2 : 1;  // query tiles of this launch that hold queries
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* smB = base;
-  uint64_t* bars = (uint64_t*)(smB + STAGES * B_STAGE_BYTES);
+  uint8_t* smA = base;            // [QTILES][MAX_KB] query K blocks, 128-byte swizzle
+  uint8_t* smB = base + A_BYTES;  // [STAGES] row-tile K blocks, 128-byte swizzle (written by TMA)
+  uint64_t* bars = (uint64_t*)(smB + STAGES * KBLK_BYTES);
   // bars: full[STAGES] | empty[STAGES] | acc_full[2] | acc_empty[2]
   uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
@@ -223,39 +215,26 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // the query tiles go to shared memory once, in the layout the 128-byte-swizzle descriptors read:
+  // K block kb of tile c holds row r's 16-byte chunk j (elements 64 kb + 8 j ...) at
+  // r * 128 + 16 * (j ^ (r mod 8))
+  {
+    const int nkb = P.nkb;
+    const int chunks = nq_tiles * nkb * BM * 8;
+    for (int e = threadIdx.x; e < chunks; e += blockDim.x) {
+      const int j = e & 7, r = (e >> 3) & (BM - 1), kb = (e >> 10) % nkb, c = (e >> 10) / nkb;
+      const int64_t grow = (int64_t)(P.qtile + c) * BM + r;
+      const uint4 v = *reinterpret_cast<const uint4*>(P.qbf + grow * (P.len / 2) + kb * (BKE / 2) + j * 4);
+      *reinterpret_cast<uint4*>(smA + ((size_t)(c * MAX_KB + kb) * KBLK_BYTES) + r * 128 + ((j ^ (r & 7)) << 4)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
-  {
-    // the query tiles go to tensor memory once (lane = query row, column j = elements 2j, 2j+1):
-    // warp (quadrant qd, tile c, half h) writes its 32 rows' columns [64h, 64h + 64) of tile c
-    const int w = threadIdx.x >> 5;
-    if (w >= 2) {
-      const int qd = w & 3, c = ((w - 2) >> 2) & 1, h = (w - 2) >> 3;
-      if (c < nq_tiles) {
-        const int64_t grow = (int64_t)(P.qtile + c) * BM + qd * 32 + (threadIdx.x & 31);
-        const uint32_t* src = P.qbf + grow * (P.len / 2);
-        for (int j0 = h * 64; j0 < h * 64 + 64 && j0 < P.len / 2; j0 += 32) {
-          uint32_t v[32];
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const uint4 q4 = *reinterpret_cast<const uint4*>(src + j0 + j);
-            v[j] = q4.x;
-            v[j + 1] = q4.y;
-            v[j + 2] = q4.z;
-            v[j + 3] = q4.w;
-          }
-          tmem_st32(tmem_base + ((uint32_t)(qd * 32) << 16) + A_COL0 + (uint32_t)(c * (MAX_KB * 32) + j0), v);
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-  }
   const int64_t ntiles = (P.n + BN - 1) / BN;
+  const int64_t nranges = (P.n + RT - 1) / RT;
   // pass 1 needs the upper ends of any k rows: it visits every SAMPLE-th tile; pass 2 visits all
   const int64_t tstep = (PHASE == 1 ? SAMPLE : 1);
   const int64_t tfirst = (int64_t)blockIdx.x * tstep, tstride = (int64_t)gridDim.x * tstep;
@@ -263,19 +242,19 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   const int nkb = P.nkb;
 
   if (warp == 0) {
-    if (lane == 0) {  // ---- TMA producer
+    if (lane == 0) {  // ---- TMA producer: one stage per (row tile, K block)
       int i = 0;
-      for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
-        const int s = i % STAGES;
-        const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-        if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
-          *abort_flag = 1;
-          break;
+      for (int64_t t = tfirst; t < ntiles && !*abort_flag; t += tstride) {
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % STAGES;
+          const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+          if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(b_full + 8 * s, (uint32_t)KBLK_BYTES);
+          tma_load_2d(smem_u32(smB + (size_t)s * KBLK_BYTES), &tmB, kb * BKE, (int)(t * BN), b_full + 8 * s);
         }
-        mbar_expect_tx(b_full + 8 * s, (uint32_t)(nkb * BN * 128));
-        for (int kb = 0; kb < nkb; ++kb)
-          tma_load_2d(smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128), &tmB, kb * BKE,
-                      (int)(t * BN), b_full + 8 * s);
       }
       // drain: the last loads must land before the CTA may exit
       const int issued = i;
@@ -287,40 +266,47 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     if (lane == 0) {  // ---- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
       bool ok = true;
-      int i = 0;
-      for (int64_t t = tfirst; ok && t < ntiles; t += tstride, ++i) {
-        const int s = i % STAGES;
-        const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-        const int ab = i & 1;
-        const uint32_t aph = (uint32_t)((i >> 1) & 1);
-        if (!mbar_wait(b_full + 8 * s, ph, abort_flag, deadline) ||
-            !mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag, deadline)) {
+      int i = 0, j = 0;  // stages consumed, row tiles finished
+      for (int64_t t = tfirst; ok && t < ntiles; t += tstride, ++j) {
+        const int ab = j & 1;
+        const uint32_t aph = (uint32_t)((j >> 1) & 1);
+        if (!mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag, deadline)) {
           ok = false;
           break;
         }
-        tc_fence_after();
-        for (int qt = 0; qt < nq_tiles; ++qt) {
-          const uint32_t d_tmem = tmem_base + (uint32_t)((ab * QTILES + qt) * BN);
-          for (int kb = 0; kb < nkb; ++kb) {
-            const uint32_t a0 = tmem_base + A_COL0 + (uint32_t)(qt * (MAX_KB * 32) + kb * 32);
-            const uint32_t b0 = smem_u32(smB + (size_t)s * B_STAGE_BYTES + (size_t)kb * BN * 128);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)  // 16 BF16 per MMA step along K: 8 columns of A, 32 bytes of B
-              umma_bf16_tmem_a(d_tmem, a0 + 8 * ks, smem_desc_sw128(b0 + 32 * ks), idesc, (kb | ks) ? 1u : 0u);
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % STAGES;
+          const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+          if (!mbar_wait(b_full + 8 * s, ph, abort_flag, deadline)) {
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t b0 = smem_u32(smB + (size_t)s * KBLK_BYTES);
+          for (int qt = 0; qt < nq_tiles; ++qt) {
+            const uint32_t d_tmem = tmem_base + (uint32_t)((ab * QTILES + qt) * BN);
+            const uint32_t a0 = smem_u32(smA + (size_t)(qt * MAX_KB + kb) * KBLK_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)  // 16 BF16 per MMA step along K: 32 bytes of each row
+              umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
+                        (kb | ks) ? 1u : 0u);
+          }
+          umma_commit(b_empty + 8 * s);
         }
-        umma_commit(b_empty + 8 * s);
+        if (!ok) break;
         umma_commit(b_accf + 8 * ab);
       }
       if (!ok) *abort_flag = 1;
-      // drain: wait for the last MMAs before the TMEM is released
-      if (i > 0 && !mbar_wait_drain(b_accf + 8 * ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), deadline + kDrainNs))
+      // drain: wait for the last MMAs before the TMEM is released (the commit of the last stage
+      // covers every MMA this thread issued before it)
+      if (i > 0 && !mbar_wait_drain(b_empty + 8 * ((i - 1) % STAGES), (uint32_t)(((i - 1) / STAGES) & 1),
+                                    deadline + kDrainNs))
         *abort_flag = 1;
     }
   } else {  // ---- epilogue: warps 2..17, TMEM lane quadrant = warp % 4
     const int qd = warp & 3;
     const int c = ((warp - 2) >> 2) & 1;  // query tile
-    const int h = (warp - 2) >> 3;        // 32-row half of each row tile
+    const int h = (warp - 2) >> 3;        // 64-row half of each row tile
     const bool tile_on = c < nq_tiles;  // warp-uniform: this warp's query tile holds queries
     const int m = qd * 32 + lane;
     const int d = (P.qtile + c) * BM + m;
@@ -339,94 +325,100 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     const float c1q = __fmul_ru(P.c1, qrt);
     float best[KMAX];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) best[j] = CUDART_INF_F;
+    for (int jj = 0; jj < KMAX; ++jj) best[jj] = CUDART_INF_F;
     float kth = CUDART_INF_F;
-    // norm range of the row tiles, loaded two tiles ahead (one address per warp)
-    auto load_range = [&](int64_t t) { return t < ntiles ? P.xtile[t] : make_float4(0.f, 0.f, 0.f, 0.f); };
+    // norm range of this warp's 64 rows of a row tile, loaded two tiles ahead (one address per warp)
+    auto load_range = [&](int64_t t) {
+      const int64_t r = 2 * t + h;
+      return (t < ntiles && r < nranges) ? P.xtile[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
     float4 rng1 = load_range(tfirst), rng2 = load_range(tfirst + tstride);
-    int i = 0;
-    for (int64_t t = tfirst; t < ntiles; t += tstride, ++i) {
+    int j = 0;
+    for (int64_t t = tfirst; t < ntiles; t += tstride, ++j) {
       const float4 rng = rng1;
       rng1 = rng2;
       rng2 = load_range(t + 2 * tstride);
-      const int ab = i & 1;
-      const uint32_t aph = (uint32_t)((i >> 1) & 1);
+      const int ab = j & 1;
+      const uint32_t aph = (uint32_t)((j >> 1) & 1);
       if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
       if (tile_on) {
-        // largest margin over the tile's rows, rounded up
+        // largest margin over the rows of the range, rounded up
         const float Mmax = __fmaf_ru(c1q, rng.z, __fmul_ru(P.c2, __fadd_ru(qn, rng.y)));
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)((ab * QTILES + c) * BN + h * 32), v);
-        const int64_t row0 = t * BN + h * 32;
-        const int64_t left = P.n - row0;
-        const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);  // rows of this chunk inside the series
-        const uint32_t row_mask = nrow >= 32 ? 0xffffffffu : (nrow <= 0 ? 0u : ((1u << nrow) - 1u));
-        uint32_t hit = 0u;
-        // the tests below are monotone in the dot product (round-toward functions of -2 dot
-        // plus a constant), so the largest of the 32 dots decides whether any row can pass
-        float dmax = __uint_as_float(v[0]);
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)((ab * QTILES + c) * BN + h * 64 + ch * 32), v);
+          const int64_t row0 = t * BN + h * 64 + ch * 32;
+          const int64_t left = P.n - row0;
+          const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);  // rows of this chunk inside the series
+          const uint32_t row_mask = nrow >= 32 ? 0xffffffffu : (nrow <= 0 ? 0u : ((1u << nrow) - 1u));
+          uint32_t hit = 0u;
+          // the tests below are monotone in the dot product (round-toward functions of -2 dot
+          // plus a constant), so the largest of the 32 dots decides whether any row can pass
+          float dmax = __uint_as_float(v[0]);
 #pragma unroll
-        for (int jj = 1; jj < 32; ++jj) dmax = fmaxf(dmax, __uint_as_float(v[jj]));
-        if (PHASE == 1) {
-          // upper ends from the tile's norm range: ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max))
-          const float Cq = __fadd_ru(qn, Mmax);
-          if (valid && __fadd_ru(__fmaf_ru(-2.0f, dmax, rng.y), Cq) < kth) {
+          for (int jj = 1; jj < 32; ++jj) dmax = fmaxf(dmax, __uint_as_float(v[jj]));
+          if (PHASE == 1) {
+            // upper ends from the range's norms: ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max))
+            const float Cq = __fadd_ru(qn, Mmax);
+            if (valid && __fadd_ru(__fmaf_ru(-2.0f, dmax, rng.y), Cq) < kth) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              hit |= (__fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(v[jj]), rng.y), Cq) < kth ? 1u : 0u) << jj;
-          }
-          hit = valid ? (hit & row_mask) : 0u;
-          while (hit) {  // rare: insert into the top-k
-            const int jj = __ffs(hit) - 1;
-            hit &= hit - 1u;
-            uint32_t dv = 0u;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dv = (j == jj) ? v[j] : dv;
-            float x = __fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(dv), rng.y), Cq);
-            if (x < kth) {
-#pragma unroll
-              for (int j = 0; j < KMAX; ++j) {
-                if (j < P.k) {
-                  const float lo = fminf(best[j], x);
-                  x = fmaxf(best[j], x);
-                  best[j] = lo;
-                }
-              }
-#pragma unroll
-              for (int j = 0; j < KMAX; ++j)
-                if (j == P.k - 1) kth = best[j];
+              for (int jj = 0; jj < 32; ++jj)
+                hit |= (__fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(v[jj]), rng.y), Cq) < kth ? 1u : 0u) << jj;
             }
-          }
-        } else {
-          // drop unless rd(xn_min - 2 dot) <= ru(thr + M_max - |q|^2)
-          const float R = __fsub_ru(__fadd_ru(thr_q, Mmax), qn);
-          if (valid && __fmaf_rd(-2.0f, dmax, rng.x) <= R) {
+            hit = valid ? (hit & row_mask) : 0u;
+            while (hit) {  // rare: insert into the top-k
+              const int jj = __ffs(hit) - 1;
+              hit &= hit - 1u;
+              uint32_t dv = 0u;
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
-          }
-          hit = valid ? (hit & row_mask) : 0u;
-          while (hit) {  // rare: the row's own interval, then emit
-            const int jj = __ffs(hit) - 1;
-            hit &= hit - 1u;
-            uint32_t dv = 0u;
+              for (int q2 = 0; q2 < 32; ++q2) dv = (q2 == jj) ? v[q2] : dv;
+              float x = __fadd_ru(__fmaf_ru(-2.0f, __uint_as_float(dv), rng.y), Cq);
+              if (x < kth) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) dv = (j == jj) ? v[j] : dv;
-            const float2 xx = P.xnorm[row0 + jj];
-            const float d2 = fmaf(-2.0f, __uint_as_float(dv), qn + xx.x);
-            const float M = __fmaf_ru(c1q, xx.y, __fmul_ru(P.c2, __fadd_ru(qn, xx.x)));
-            const float x = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
-            if (x <= thr_q) {
-              const uint32_t p = atomicAdd(P.count + slot, 1u);
-              if ((int64_t)p < P.cap) {
-                P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
-                P.lb[(int64_t)slot * P.cap + p] = x;
-              } else {
-                atomicOr(P.overflow, DEV_CAND_OVERFLOW);
+                for (int q2 = 0; q2 < KMAX; ++q2) {
+                  if (q2 < P.k) {
+                    const float lo = fminf(best[q2], x);
+                    x = fmaxf(best[q2], x);
+                    best[q2] = lo;
+                  }
+                }
+#pragma unroll
+                for (int q2 = 0; q2 < KMAX; ++q2)
+                  if (q2 == P.k - 1) kth = best[q2];
+              }
+            }
+          } else {
+            // drop unless rd(xn_min - 2 dot) <= ru(thr + M_max - |q|^2)
+            const float R = __fsub_ru(__fadd_ru(thr_q, Mmax), qn);
+            if (valid && __fmaf_rd(-2.0f, dmax, rng.x) <= R) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
+            }
+            hit = valid ? (hit & row_mask) : 0u;
+            while (hit) {  // rare: the row's own interval, then emit
+              const int jj = __ffs(hit) - 1;
+              hit &= hit - 1u;
+              uint32_t dv = 0u;
+#pragma unroll
+              for (int q2 = 0; q2 < 32; ++q2) dv = (q2 == jj) ? v[q2] : dv;
+              const float2 xx = P.xnorm[row0 + jj];
+              const float d2 = fmaf(-2.0f, __uint_as_float(dv), qn + xx.x);
+              const float M = __fmaf_ru(c1q, xx.y, __fmul_ru(P.c2, __fadd_ru(qn, xx.x)));
+              const float x = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
+              if (x <= thr_q) {
+                const uint32_t p = atomicAdd(P.count + slot, 1u);
+                if ((int64_t)p < P.cap) {
+                  P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
+                  P.lb[(int64_t)slot * P.cap + p] = x;
+                } else {
+                  atomicOr(P.overflow, DEV_CAND_OVERFLOW);
+                }
               }
             }
           }
@@ -560,12 +552,12 @@ void dense_margins(int len, float* c1, float* c2) {
 // Norm range of each 64-row tile over its rows inside the series; one warp per tile.
 __global__ void tile_range_kernel(const float2* __restrict__ nm, int64_t n, float4* __restrict__ out) {
   const int lane = threadIdx.x & 31;
-  const int64_t tiles = (n + BN - 1) / BN;
+  const int64_t tiles = (n + RT - 1) / RT;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += warps) {
     float lo = CUDART_INF_F, hi = -CUDART_INF_F, rt = -CUDART_INF_F;
-    for (int j = lane; j < BN; j += 32) {
-      const int64_t r = t * BN + j;
+    for (int j = lane; j < RT; j += 32) {
+      const int64_t r = t * RT + j;
       if (r < n) {
         const float2 v = nm[r];
         lo = fminf(lo, v.x);
@@ -584,8 +576,8 @@ __global__ void tile_range_kernel(const float2* __restrict__ nm, int64_t n, floa
 }
 
 // Row norms are stored for whole row tiles, so a tile's norms are one bulk copy.
-size_t norm_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN * BN) * sizeof(float2); }
-size_t range_bytes(int64_t n) { return (size_t)((n + BN - 1) / BN) * sizeof(float4); }
+size_t norm_bytes(int64_t n) { return (size_t)((n + RT - 1) / RT * RT) * sizeof(float2); }
+size_t range_bytes(int64_t n) { return (size_t)((n + RT - 1) / RT) * sizeof(float4); }
 
 bool dense_shape_ok(int len) { return len % BKE == 0 && len <= MAX_KB * BKE; }
 
