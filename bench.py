@@ -706,6 +706,52 @@ def main():
     if args.multi_scale > 0:
         multi_wl = run_three_collections(args, P, dev, stream)
 
+    # ---- beside it: best-so-far sharing ablation (nb-ParIS+ keeps one BSF per worker): the plain
+    # method on 300 sigma = 0.1 queries and 100 independent random walks (the hard queries), with
+    # the shared BSF and with a private BSF per refining warp
+    if args.plain_steps > 0:
+        import synth as _synth
+        nbq = {"sigma_0.1": Q[args.per_sigma:args.per_sigma + min(300, args.per_sigma)],
+               "random_walks": torch.from_numpy(_synth.random_walk(100, length, seed=2)).to(dev)}
+        nidx = P.paris_build(X, 16, 256)
+        abl = {}
+        for gname, gq in nbq.items():
+            rec = {}
+            ans = {}
+            for priv in (False, True):
+                _, (gi_, _, st_) = timed(lambda: P.paris_exact_knn_ex(nidx, gq, k, mode=P.PARIS_MODE_PLAIN,
+                                                                        want_stats=True, private_bsf=priv), stream, 1)
+                rec["private" if priv else "shared"] = {
+                    "refined_rows_per_query": st_["refined"] / gq.shape[0],
+                    "bsf_updates_per_query": st_["bsf_updates"] / gq.shape[0],
+                    "refine_ms": st_["ms_refine"], "queries": int(gq.shape[0])}
+                ans[priv] = gi_
+            rec["identical_answers"] = bool(torch.equal(ans[False], ans[True]))
+            abl[gname] = rec
+        beside["nb_ablation"] = abl
+        nidx.free()
+
+    # ---- beside it: the same collection kept in host memory (series_on_host): built through two
+    # device staging buffers, raw rows read from host memory by the searches; queries only
+    if args.graph_steps > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hidx = P.paris_build_ex(host, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED, series_on_host=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hb_ms = e0.elapsed_time(e1)
+        ref_i = P.paris_exact_knn_ex(hidx, Q, k, mode=mode, precision=precision)[0]
+        hq_ms, (hi_, _) = timed(lambda: P.paris_exact_knn_ex(hidx, Q, k, mode=mode, precision=precision), stream, 2)
+        didx = P.paris_build_ex(X, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
+        dq_ms, (di_, _) = timed(lambda: P.paris_exact_knn_ex(didx, Q, k, mode=mode, precision=precision), stream, 2)
+        beside["host_resident_series"] = {
+            "form": "series kept in host memory, read over the CPU-GPU link (index built once; queries only)",
+            "build_ms": hb_ms, "value": nq / (hq_ms * 1e-3), "unit": "queries/s",
+            "device_series_value": nq / (dq_ms * 1e-3),
+            "identical_answers": bool(torch.equal(hi_, di_)) and bool(torch.equal(ref_i, di_))}
+        hidx.free()
+        didx.free()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

@@ -66,7 +66,17 @@ typedef struct paris_build_opts {
                             row norms that PARIS_REFINE_MIXED screens with (otherwise they are
                             built by the first MIXED query); no effect for shapes the screening
                             does not support (len not a multiple of 64 or above 256) */
-  int32_t reserved[6];   /* must be zero */
+  int32_t series_on_host; /* 1 (host series only): keep the series in host memory instead of copying
+                             it to the device -- the collection may exceed HBM. The build streams
+                             it through two 512 MB device staging buffers (a copy of one chunk
+                             overlaps the encode of the other, the double-buffered loading of
+                             Sec. 3.1-3.2); the summaries, keys, leaf envelopes and the optional
+                             BF16 copy stay in device memory, while the approximate search,
+                             refinement and exact re-rank read raw rows from host memory over the
+                             CPU-GPU link. The series is BORROWED: keep it alive and unchanged
+                             until paris_free. Pageable memory is registered with the driver for
+                             the index's lifetime (pinned memory is used as it is). */
+  int32_t reserved[5];   /* must be zero */
 } paris_build_opts;
 
 /* paris_build with options (opts may be NULL = defaults). */
@@ -247,7 +257,8 @@ paris_status paris_set_allocator(paris_alloc_fn alloc, paris_free_fn free_fn, vo
 typedef struct paris_index_view {
   int64_t n;
   int32_t len, w, card, leaf_capacity;
-  const float* series;          /* device [n][len] */
+  const float* series;          /* device-accessible [n][len] (device memory, or mapped host
+                                   memory with series_on_host) */
   const uint64_t* keys_sorted;  /* device [n]: top 64 key bits in index order */
   const uint32_t* rows_sorted;  /* device [n]: rows in index order (key, row) */
 } paris_index_view;

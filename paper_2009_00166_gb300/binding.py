@@ -29,7 +29,8 @@ class ParisError(RuntimeError):
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("leaf_capacity", C.c_int32), ("bf16_shadow", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("leaf_capacity", C.c_int32), ("bf16_shadow", C.c_int32), ("series_on_host", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class QueryOpts(C.Structure):
@@ -191,10 +192,12 @@ class ParisIndex:
 
 
 def paris_build_ex(series, w: int = 16, card: int = 256, leaf_capacity: int = 0, bf16_shadow: bool = False,
-                   stream=None) -> ParisIndex:
-    """paris_build_ex: series is a contiguous [n][len] float32 tensor (device: borrowed; host: copied)."""
+                   stream=None, series_on_host: bool = False) -> ParisIndex:
+    """paris_build_ex: series is a contiguous [n][len] float32 tensor (device: borrowed; host: copied,
+    or borrowed and read in place with series_on_host)."""
     n, length = int(series.shape[0]), int(series.shape[1])
-    opts = BuildOpts(leaf_capacity=leaf_capacity, bf16_shadow=1 if bf16_shadow else 0)
+    opts = BuildOpts(leaf_capacity=leaf_capacity, bf16_shadow=1 if bf16_shadow else 0,
+                     series_on_host=1 if series_on_host else 0)
     out = C.c_void_p()
     _check(lib().paris_build_ex(_ptr(series), n, length, w, card, C.byref(opts), _stream(stream), C.byref(out)))
     return ParisIndex(out.value, n, length, w, card, series)

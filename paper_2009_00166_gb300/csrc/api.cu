@@ -157,6 +157,7 @@ void release_index(paris_index* idx) {
   if (!idx) return;
   cudaStream_t st = nullptr;
   dev_free(idx->series_owned, idx->series_owned_bytes, st);
+  if (idx->host_registered) cudaHostUnregister(const_cast<void*>(idx->host_registered));
   dev_free(idx->sax, (size_t)idx->n * PARIS_SAX_BYTES, st);
   dev_free(idx->keys_sorted, (size_t)idx->n * 8, st);
   dev_free(idx->rows_sorted, (size_t)idx->n * 4, st);
@@ -407,11 +408,14 @@ paris_status copy_streams(cudaStream_t* out) {
 // A host series is copied to the device in chunks on two copy streams while the encode pass
 // works through the chunks already copied. Chunks start at multiples of 16 rows (the rotation
 // of the summary slots follows the row number).
+// With `staging` (two buffers of `rows` rows each; the series stays on the host), chunk j is copied
+// into staging[j % 2] once the encode of chunk j - 2 has read that buffer.
 static paris_status copy_and_encode(paris_index* idx, const float* host, const RowShape& sh, ShadowBufs& shb,
-                                    uint32_t* status, cudaStream_t st) {
+                                    uint32_t* status, cudaStream_t st, float* const* staging = nullptr,
+                                    int64_t staging_rows = 0) {
   const int64_t n = idx->n, len = idx->len;
   const size_t row_bytes = (size_t)len * sizeof(float);
-  int64_t rows = (int64_t)((size_t)(512u << 20) / row_bytes);  // about 512 MB per chunk
+  int64_t rows = staging ? staging_rows : (int64_t)((size_t)(512u << 20) / row_bytes);  // about 512 MB per chunk
   rows = std::max<int64_t>(16, rows / 16 * 16);
   cudaStream_t cs[2];
   PARIS_TRY(copy_streams(cs));
@@ -425,18 +429,25 @@ static paris_status copy_and_encode(paris_index* idx, const float* host, const R
   int j = 0;
   for (int64_t r0 = 0; r0 < n && s == PARIS_OK; r0 += rows, ++j) {
     const int64_t m = std::min(rows, n - r0);
-    cudaEvent_t done = nullptr;
-    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMemcpyAsync(dst + r0 * len, host + r0 * len, (size_t)m * row_bytes, cudaMemcpyHostToDevice, cs[j & 1]) !=
-            cudaSuccess ||
-        cudaEventRecord(done, cs[j & 1]) != cudaSuccess || cudaStreamWaitEvent(st, done, 0) != cudaSuccess) {
+    float* chunk = staging ? staging[j & 1] : dst + r0 * len;
+    cudaEvent_t done = nullptr, freed = nullptr;
+    bool ok = cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && staging && j >= 2) {  // the buffer's previous chunk must have been encoded
+      ok = cudaEventCreateWithFlags(&freed, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventRecord(freed, st) == cudaSuccess && cudaStreamWaitEvent(cs[j & 1], freed, 0) == cudaSuccess;
+    }
+    ok = ok &&
+         cudaMemcpyAsync(chunk, host + r0 * len, (size_t)m * row_bytes, cudaMemcpyHostToDevice, cs[j & 1]) ==
+             cudaSuccess &&
+         cudaEventRecord(done, cs[j & 1]) == cudaSuccess && cudaStreamWaitEvent(st, done, 0) == cudaSuccess;
+    if (done) cudaEventDestroy(done);
+    if (freed) cudaEventDestroy(freed);
+    if (!ok) {
       cudaGetLastError();
-      if (done) cudaEventDestroy(done);
       s = fail(PARIS_ECUDA, "copying the series to the device");
       break;
     }
-    cudaEventDestroy(done);
-    s = launch_encode(dst + r0 * len, m, sh, idx->card, idx->bits, idx->beta_keys, idx->sax + r0 * PARIS_SAX_BYTES,
+    s = launch_encode(chunk, m, sh, idx->card, idx->bits, idx->beta_keys, idx->sax + r0 * PARIS_SAX_BYTES,
                       nullptr, idx->keys_sorted + r0, nullptr, status, st,
                       shb.shadow ? (void*)((uint16_t*)shb.shadow + r0 * len) : nullptr,
                       shb.xnorm ? shb.xnorm + r0 : nullptr);
@@ -457,10 +468,13 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   int leaf = opts && opts->leaf_capacity ? opts->leaf_capacity : 2048;
   if (leaf < 1 || leaf > kMaxLeaf) return fail(PARIS_EINVAL, "leaf_capacity must be in [1, %d]", kMaxLeaf);
   if (opts) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (opts->reserved[i]) return fail(PARIS_EINVAL, "paris_build_opts.reserved must be zero");
     if (opts->bf16_shadow != 0 && opts->bf16_shadow != 1) return fail(PARIS_EINVAL, "bf16_shadow must be 0 or 1");
+    if (opts->series_on_host != 0 && opts->series_on_host != 1)
+      return fail(PARIS_EINVAL, "series_on_host must be 0 or 1");
   }
+  const bool on_host = opts && opts->series_on_host;
   cudaStream_t st = (cudaStream_t)stream;
   paris_index* idx = new (std::nothrow) paris_index();
   if (!idx) return fail(PARIS_ENOMEM, "index object");
@@ -478,8 +492,37 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
   };
   const size_t series_bytes = (size_t)n * len * sizeof(float);
   const float* host_src = nullptr;  // a host series, copied in while the encode pass runs
+  DevBuf stage[2];
+  float* staging[2] = {nullptr, nullptr};
+  int64_t staging_rows = 0;
   if (is_device_ptr(series)) {
     idx->series = series;
+  } else if (on_host) {
+    // the series stays where it is: the kernels read it through its device mapping
+    cudaPointerAttributes a;
+    void* mapped = nullptr;
+    if (cudaPointerGetAttributes(&a, series) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+      mapped = a.devicePointer;
+    } else {
+      cudaGetLastError();
+      if (cudaHostRegister(const_cast<float*>(series), series_bytes, cudaHostRegisterMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PARIS_ECUDA, "registering the host series (%zu bytes)", series_bytes));
+      }
+      idx->host_registered = series;
+      if (cudaHostGetDevicePointer(&mapped, const_cast<float*>(series), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PARIS_ECUDA, "device mapping of the host series"));
+      }
+    }
+    idx->series = (const float*)mapped;
+    staging_rows = std::max<int64_t>(16, (int64_t)((size_t)(512u << 20) / ((size_t)len * 4)) / 16 * 16);
+    staging_rows = std::min<int64_t>(staging_rows, (n + 15) / 16 * 16);
+    for (int i = 0; i < 2; ++i) {
+      if (!stage[i].alloc((size_t)staging_rows * len * 4, st)) return bail(fail(PARIS_ENOMEM, "staging buffers"));
+      staging[i] = stage[i].as<float>();
+    }
+    host_src = series;
   } else {
     idx->series_owned = dev_alloc(series_bytes, st);
     if (!idx->series_owned) return bail(fail(PARIS_ENOMEM, "device copy of the series (%zu bytes)", series_bytes));
@@ -504,7 +547,8 @@ paris_status paris_build_ex(const float* series, int64_t n, int32_t len, int32_t
     s = alloc_shadow(idx, &shb, st);
     if (s != PARIS_OK) return bail(s);
   }
-  s = host_src ? copy_and_encode(idx, host_src, sh, shb, status.as<uint32_t>(), st)
+  s = host_src ? copy_and_encode(idx, host_src, sh, shb, status.as<uint32_t>(), st, on_host ? staging : nullptr,
+                                 staging_rows)
                : launch_encode(idx->series, n, sh, card, idx->bits, idx->beta_keys, idx->sax, nullptr,
                                idx->keys_sorted, nullptr, status.as<uint32_t>(), st, shb.shadow, shb.xnorm);
   if (s == PARIS_OK && fused) s = finish_shadow(idx, &shb, st);

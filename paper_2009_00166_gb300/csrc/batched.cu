@@ -427,10 +427,18 @@ __global__ void __launch_bounds__(kBThreads, 1) pilot_kernel(const __grid_consta
   const int64_t per = (samples + C.ncta - 1) / C.ncta;
   const int64_t s0 = (int64_t)(blockIdx.x - C.cta0) * per, s1 = min(samples, s0 + per);
   const int64_t entries = (int64_t)W.card * 16;
-  if (threadIdx.x < QT) s_active[threadIdx.x] = true;
   for (int tile = 0; tile < C.ntiles; ++tile) {
     const int qb = tile * QT;
     __syncthreads();
+    // queries that the leaf pruning sends to the list scan need no pilot count (they are neither
+    // routed nor placed in tiles): a tile of such queries only is skipped
+    bool act = false;
+    if (threadIdx.x < QT) {
+      const int qq = qb + threadIdx.x;
+      act = qq < qc && !(C.pagebits && (int64_t)C.page_count[qq] <= C.list_cap);
+      s_active[threadIdx.x] = act;
+    }
+    if (!__syncthreads_or(act)) continue;
     load_tile<NP>(C.packed, entries, qb, qc, C.thr, C.q0, nullptr, s_active, s_tab, s_thr);
     if (threadIdx.x < 2 * QT) s_cnt[threadIdx.x] = 0u;
     __syncthreads();

@@ -188,14 +188,28 @@ __device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
   return (int64_t)__shfl_sync(PARIS_FULL_MASK, (long long)v, src);
 }
 
-// Number of breakpoints <= v (upper region on ties). An FP32 estimate floor(card * Phi(v)) is
-// moved to the exact answer by comparing order keys of the FP64 values (a few steps at most);
-// the binary search below is the fallback.
+// Starting points of the symbol search: bucket b of [-8, 8) (width 1/256, narrower than any gap
+// between consecutive breakpoints of up to 256 symbols) holds the number of breakpoints <= the
+// bucket's lower end; the symbol of a value in the bucket is that count or one more.
+constexpr int kSymBuckets = 4096;
 __device__ __forceinline__ int symbol_search(uint64_t key, const uint64_t* beta_keys, int card);
-__device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, int card) {
+// Fills the bucket table (shared memory) from the order keys of the breakpoints (shared memory);
+// the caller synchronises before use.
+__device__ __forceinline__ void build_symbol_table(const uint64_t* beta_keys, int card, uint8_t* tab) {
+  for (int b = threadIdx.x; b < kSymBuckets; b += blockDim.x)
+    tab[b] = (uint8_t)symbol_search(double_order_key(-8.0 + (double)b * (1.0 / 256.0)), beta_keys, card);
+}
+
+// Number of breakpoints <= v (upper region on ties): the bucket table's estimate, moved to the
+// exact answer by comparing order keys of the FP64 values (one step at most, up to 8 tried); the
+// binary search below is the fallback.
+__device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, const uint8_t* tab, int card) {
   const uint64_t key = double_order_key(v);
-  int sym = (int)(normcdff(__double2float_rn(v)) * (float)card);
-  sym = sym < 0 ? 0 : (sym > card - 1 ? card - 1 : sym);
+  const float f = fminf(fmaxf(__double2float_rn(v), -8.0f), 7.99f);
+  int b = (int)((f + 8.0f) * 256.0f);
+  b = b < 0 ? 0 : (b > kSymBuckets - 1 ? kSymBuckets - 1 : b);
+  int sym = tab[b];
+  sym = sym > card - 1 ? card - 1 : sym;
   // answer: beta_keys[sym-1] <= key < beta_keys[sym] (missing ends are -inf / +inf)
   for (int it = 0; it < 8; ++it) {
     if (sym > 0 && beta_keys[sym - 1] > key) {
@@ -350,7 +364,9 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
 __device__ __forceinline__ uint64_t warp_pair_key64(int sym, int lane, int w, int bits) {
   uint64_t hi = 0, lo = 0;
   int filled = 0;
-  for (int j = 0; j < bits; ++j) {
+  // only the planes that reach the top 64 bits: ceil(64 / w) of them (4 at w = 16)
+  const int planes = min(bits, (64 + w - 1) / w);
+  for (int j = 0; j < planes; ++j) {
     const int b = bits - 1 - j;
     const uint32_t m = __brev(__ballot_sync(PARIS_FULL_MASK, (sym >> b) & 1));
     // row 0's lanes 0..15 are now bits 31..16, row 1's lanes 16..31 are bits 15..0

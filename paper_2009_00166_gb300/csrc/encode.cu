@@ -18,7 +18,10 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     uint8_t* __restrict__ sax_plain, uint64_t* __restrict__ key64, double* __restrict__ paa_out,
     uint32_t* __restrict__ status, __nv_bfloat16* __restrict__ shadow, float2* __restrict__ xnorm) {
   __shared__ uint64_t beta_keys[255];
+  __shared__ uint8_t sym_tab[kSymBuckets];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
+  __syncthreads();
+  build_symbol_table(beta_keys, card, sym_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4, seg = lane & 15;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
     if (!lane_segment_paa<SEGV>(row0, row1, sh, lane, paa)) nonfinite = true;
     const int64_t r = r0 + half;
     const bool rv = half == 0 || has1;
-    const int sym = (rv && seg < sh.w) ? symbol_of(paa, beta_keys, card) : 0;
+    const int sym = (rv && seg < sh.w) ? symbol_of(paa, beta_keys, sym_tab, card) : 0;
     const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     // rotated summary slot: slot j holds segment (j + r) mod 16 (0 when that segment >= w)
     const int src = (seg + (int)(r & 15)) & 15;

@@ -16,6 +16,7 @@ struct paris_index {
   const float* series = nullptr;  // device [n][len]; borrowed unless series_owned
   void* series_owned = nullptr;
   size_t series_owned_bytes = 0;
+  const void* host_registered = nullptr;  // host series registered by the build (series_on_host)
   uint8_t* sax = nullptr;           // device [n][16], slot j of row r = segment (j + r) % 16
   uint64_t* keys_sorted = nullptr;  // device [n]
   uint32_t* rows_sorted = nullptr;  // device [n]

@@ -102,7 +102,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
                                                    uint64_t* __restrict__ qkey, float* __restrict__ qtable,
                                                    uint8_t* __restrict__ qsym, uint32_t* __restrict__ status) {
   __shared__ uint64_t beta_keys[255];
+  __shared__ uint8_t sym_tab[kSymBuckets];
   for (int i = threadIdx.x; i < card - 1; i += blockDim.x) beta_keys[i] = beta_keys_g[i];
+  __syncthreads();
+  build_symbol_table(beta_keys, card, sym_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4, seg = lane & 15;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
     if (!lane_segment_paa<SEGV>(row0, has1 ? row0 + sh.len : nullptr, sh, lane, paa)) atomicOr(status, DEV_NONFINITE);
     const int64_t q = q0 + half;
     const bool qv = half == 0 || has1;
-    const int sym = (qv && seg < sh.w) ? symbol_of(paa, beta_keys, card) : 0;
+    const int sym = (qv && seg < sh.w) ? symbol_of(paa, beta_keys, sym_tab, card) : 0;
     const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     if (!qv) continue;
     qpaa[q * 16 + seg] = seg < sh.w ? paa : 0.0;
