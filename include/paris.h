@@ -219,6 +219,18 @@ paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k
  * work on `stream` waits for it; it returns once the outputs are written. */
 paris_status paris_knn_plan_run(paris_knn_plan* plan, const float* queries, int64_t* out_idx,
                                 float* out_dist, void* stream);
+/* A captured plan over several collections: the multi-collection search of
+ * paris_exact_knn_multi (Sec. 3.3 per collection; one batched scan launch per chunk round over
+ * every collection, BATCHED mode only) recorded once as one CUDA graph for batches of exactly
+ * nq[c] queries against idx[c] (1 <= nidx <= 4, nq[c] >= 0 with at least one query, equal
+ * cardinalities). Runs take queries[c] ([nq[c]][len of idx[c]]) and write out_idx[c] /
+ * out_dist[c] ([nq[c]][k]; out_dist or out_dist[c] may be NULL), device or host, with the
+ * results and ordering guarantees of paris_exact_knn_multi. paris_knn_plan_run rejects such a
+ * plan; paris_knn_plan_run_multi also runs single-collection plans (arrays of one). */
+paris_status paris_knn_plan_create_multi(const paris_index* const* idx, int32_t nidx, const int64_t* nq,
+                                         int32_t k, const paris_query_opts* opts, paris_knn_plan** out);
+paris_status paris_knn_plan_run_multi(paris_knn_plan* plan, const float* const* queries,
+                                      int64_t* const* out_idx, float* const* out_dist, void* stream);
 paris_status paris_knn_plan_info(const paris_knn_plan* plan, paris_knn_plan_stats* out);
 void paris_knn_plan_free(paris_knn_plan* plan); /* NULL-safe */
 

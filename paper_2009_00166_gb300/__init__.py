@@ -30,6 +30,7 @@ from .binding import (  # noqa: F401
     paris_exact_knn_ex,
     paris_exact_knn_multi,
     KnnPlan,
+    KnnPlanMulti,
     paris_export_order,
     paris_export_sax,
     paris_free,

@@ -89,6 +89,9 @@ def lib():
             "paris_knn_plan_run": ([VP, P, P, P, VP], I32),
             "paris_knn_plan_info": ([VP, C.POINTER(PlanStats)], I32),
             "paris_knn_plan_free": ([VP], None),
+            "paris_knn_plan_create_multi": ([C.POINTER(VP), I32, C.POINTER(C.c_int64), I32, C.POINTER(QueryOpts),
+                                             C.POINTER(VP)], I32),
+            "paris_knn_plan_run_multi": ([VP, C.POINTER(VP), C.POINTER(VP), C.POINTER(VP), VP], I32),
             "paris_exact_knn_multi": ([C.POINTER(VP), I32, C.POINTER(VP), C.POINTER(C.c_int64), I32, C.POINTER(VP),
                                        C.POINTER(VP), C.POINTER(QueryOpts), C.POINTER(QueryStats), VP], I32),
             "paris_last_error": ([], C.c_char_p),
@@ -303,6 +306,37 @@ class KnnPlan:
             self.free()
         except Exception:
             pass
+
+
+class KnnPlanMulti(KnnPlan):
+    """paris_knn_plan_create_multi: batches of nqs[c] queries per collection, one CUDA graph."""
+
+    def __init__(self, indexes, nqs, k: int, query_tile: int = 0, chunk: int = 0,
+                 precision: int = PARIS_REFINE_FP32, leaf_pruning: bool = True):
+        m = len(indexes)
+        self.indexes, self.nqs, self.k = list(indexes), [int(v) for v in nqs], int(k)
+        opts = QueryOpts(mode=PARIS_MODE_BATCHED, query_tile=query_tile, chunk=chunk, precision=precision,
+                         no_leaf_pruning=0 if leaf_pruning else 1)
+        VPA = C.c_void_p * m
+        h = C.c_void_p()
+        _check(lib().paris_knn_plan_create_multi(VPA(*[ix.handle for ix in indexes]), m,
+                                                 (C.c_int64 * m)(*self.nqs), self.k, C.byref(opts), C.byref(h)))
+        self.handle = h
+
+    def run(self, queries, stream=None):
+        """queries: one [nq_c][len_c] tensor per collection; returns [(idx, dist)] per collection."""
+        import torch
+        m = len(self.indexes)
+        outs = []
+        for q, nq in zip(queries, self.nqs):
+            dev = q.device if hasattr(q, "device") else torch.device("cpu")
+            outs.append((torch.empty((nq, self.k), dtype=torch.int64, device=dev),
+                         torch.empty((nq, self.k), dtype=torch.float32, device=dev)))
+        VPA = C.c_void_p * m
+        _check(lib().paris_knn_plan_run_multi(self.handle, VPA(*[_ptr(q) for q in queries]),
+                                              VPA(*[_ptr(o[0]) for o in outs]), VPA(*[_ptr(o[1]) for o in outs]),
+                                              _stream(stream)))
+        return outs
 
 
 def paris_exact_knn(index: ParisIndex, queries, k: int, out_idx=None, out_dist=None, stream=None):

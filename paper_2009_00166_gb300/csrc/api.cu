@@ -1013,39 +1013,155 @@ paris_status paris_exact_knn_ex(const paris_index* idx, const float* queries, in
   return job.run_eager("paris_exact_knn");
 }
 
-// A captured query pipeline: the plan owns its query and output buffers and one KnnJob; the
-// first run executes eagerly (choosing the query tile) and then records the whole call as one
-// CUDA graph that later runs replay.
+namespace {
+
+// The query tile of a multi-collection scan launch: the tuned tile of the collection with the
+// most work (rows x chunk queries) in this round.
+int multi_round_tile(KnnJob* jobs, int nidx, int64_t r) {
+  int qt = 0;
+  double most = -1.0;
+  for (int c = 0; c < nidx; ++c) {
+    if (r >= jobs[c].chunks()) continue;
+    const double work = (double)jobs[c].idx->n * jobs[c].cs.qc;
+    if (work > most) {
+      most = work;
+      qt = jobs[c].qt;
+    }
+  }
+  return qt;
+}
+
+// Several collections with host decisions (tuning, screening tile counts, repeated screenings):
+// per chunk round, one batched scan launch over every collection's chunk.
+paris_status multi_run_eager(KnnJob* jobs, int nidx, const char* what) {
+  const paris_query_opts& o = jobs[0].o;
+  int64_t rounds = 0;
+  for (int c = 0; c < nidx; ++c) {
+    if (jobs[c].nq > 0) {
+      PARIS_CUDA(cudaMemsetAsync(jobs[c].qs.status, 0, 4, jobs[c].st));
+      PARIS_CUDA(cudaMemsetAsync(jobs[c].qs.counters, 0, 64, jobs[c].st));
+    }
+    jobs[c].dense_total = 0;
+    jobs[c].rescreens = 0;
+    jobs[c].paged_chunk = -1;
+    jobs[c].pages_examined = 0;
+    PARIS_TRY(jobs[c].front());
+    rounds = std::max(rounds, jobs[c].chunks());
+  }
+  for (int64_t r = 0; r < rounds; ++r) {
+    ScanJob sj[kMaxScanJobs];
+    int m = 0;
+    for (int c = 0; c < nidx; ++c) {
+      if (r >= jobs[c].chunks()) continue;
+      PARIS_TRY(jobs[c].begin_chunk(r));
+      if (o.mode == PARIS_MODE_BATCHED)
+        sj[m++] = ScanJob{jobs[c].idx, &jobs[c].qs, &jobs[c].cs, jobs[c].mixed ? 1 : 0, jobs[c].lb_status};
+      else
+        PARIS_TRY(jobs[c].scan_chunk());
+    }
+    if (m > 0) {
+      // one launch scans every collection's chunk; its time is charged to each collection
+      for (int c = 0; c < nidx; ++c)
+        if (r < jobs[c].chunks()) jobs[c].timer.begin(2);
+      PARIS_TRY(launch_lbscan_batched_multi(sj, m, multi_round_tile(jobs, nidx, r), jobs[0].st));
+      for (int c = 0; c < nidx; ++c)
+        if (r < jobs[c].chunks()) jobs[c].timer.end(2);
+    }
+    for (int c = 0; c < nidx; ++c)
+      if (r < jobs[c].chunks()) PARIS_TRY(jobs[c].finish_chunk());
+  }
+  for (int c = 0; c < nidx; ++c) PARIS_TRY(jobs[c].finish(what));
+  return PARIS_OK;
+}
+
+// The same call as one stream of launches without host synchronisation (for graph capture):
+// every collection's query tile must be known; overflowed screened lists are only counted.
+paris_status multi_record(KnnJob* jobs, int nidx) {
+  const paris_query_opts& o = jobs[0].o;
+  int64_t rounds = 0;
+  for (int c = 0; c < nidx; ++c) {
+    KnnJob& J = jobs[c];
+    if (J.nq == 0) continue;
+    if (o.mode == PARIS_MODE_BATCHED && J.qt == 0) return fail(PARIS_EINTERNAL, "query tile unknown at capture");
+    PARIS_CUDA(cudaMemsetAsync(J.qs.status, 0, 4, J.st));
+    PARIS_CUDA(cudaMemsetAsync(J.qs.counters, 0, 64, J.st));
+    PARIS_CUDA(cudaMemsetAsync(J.cs.nover, 0, 4, J.st));
+    J.paged_chunk = -1;
+    J.pages_examined = 0;
+    PARIS_TRY(J.front());
+    rounds = std::max(rounds, J.chunks());
+  }
+  for (int64_t r = 0; r < rounds; ++r) {
+    ScanJob sj[kMaxScanJobs];
+    int m = 0;
+    for (int c = 0; c < nidx; ++c) {
+      KnnJob& J = jobs[c];
+      if (r >= J.chunks()) continue;
+      J.cs.q0 = r * J.qc;
+      J.cs.qc = (int)std::min<int64_t>(J.qc, J.nq - J.cs.q0);
+      PARIS_CUDA(cudaMemsetAsync(J.cs.count, 0, (size_t)J.cs.qc * 4, J.st));
+      PARIS_TRY(J.page_pass(r));
+      if (o.mode == PARIS_MODE_BATCHED)
+        sj[m++] = ScanJob{J.idx, &J.qs, &J.cs, J.mixed ? 1 : 0, J.lb_status};
+      else
+        PARIS_TRY(J.scan_chunk());
+    }
+    if (m > 0) PARIS_TRY(launch_lbscan_batched_multi(sj, m, multi_round_tile(jobs, nidx, r), jobs[0].st));
+    for (int c = 0; c < nidx; ++c) {
+      KnnJob& J = jobs[c];
+      if (r >= J.chunks()) continue;
+      if (J.mixed) PARIS_TRY(launch_dense(const_cast<paris_index*>(J.idx), J.qs, J.cs, J.lb_status, nullptr, J.st));
+      PARIS_TRY(launch_refine(J.idx, J.qs, J.cs, J.st));
+      PARIS_TRY(launch_select(J.idx, J.qs, J.cs, (int64_t*)J.si.dev, (float*)J.sd.dev, J.st));
+      if (J.mixed) PARIS_TRY(launch_tighten(J.qs, J.cs, J.st));
+    }
+  }
+  return PARIS_OK;
+}
+
+}  // namespace
+
+// A captured query pipeline: the plan owns the query and output buffers of each of its
+// collections (one, or up to kMaxScanJobs for a multi-collection batch) and one KnnJob per
+// collection; the first run executes eagerly (choosing the query tiles) and then records the
+// whole call as one CUDA graph that later runs replay.
 struct paris_knn_plan {
-  const paris_index* idx = nullptr;
-  int64_t nq = 0;
+  int nj = 0;
+  const paris_index* idx[kMaxScanJobs] = {};
+  int64_t nq[kMaxScanJobs] = {};
   int k = 1;
   paris_query_opts o{};
   cudaStream_t pst = nullptr;
   cudaEvent_t ev = nullptr;
-  DevBuf qbuf, obi, obd;
-  KnnJob* job = nullptr;
+  DevBuf qbuf[kMaxScanJobs], obi[kMaxScanJobs], obd[kMaxScanJobs];
+  KnnJob* job = nullptr;  // [nj]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0, replays = 0, eager_runs = 0;
   bool capture_failed = false;
 };
 
-paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k, const paris_query_opts* opts,
-                                   paris_knn_plan** out) {
-  clear_error();
+namespace {
+paris_status plan_create(const paris_index* const* idx, int nidx, const int64_t* nq, int32_t k,
+                         const paris_query_opts* opts, paris_knn_plan** out) {
   if (!out) return fail(PARIS_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nq < 1) return fail(PARIS_EINVAL, "a plan needs nq >= 1");
-  PARIS_TRY(check_query_args(idx, (const float*)1, nq, k));
+  if (nidx < 1 || nidx > kMaxScanJobs) return fail(PARIS_EINVAL, "between 1 and %d collections per plan", kMaxScanJobs);
   paris_query_opts o{};
   if (opts) o = *opts;
-  PARIS_TRY(check_query_opts(idx, o));
+  int64_t total_q = 0;
+  for (int c = 0; c < nidx; ++c) {
+    if (nq[c] < 0) return fail(PARIS_EINVAL, "nq must be >= 0");
+    total_q += nq[c];
+    PARIS_TRY(check_query_args(idx[c], (const float*)1, std::max<int64_t>(nq[c], 1), k));
+    PARIS_TRY(check_query_opts(idx[c], o));
+    if (idx[c]->card != idx[0]->card) return fail(PARIS_EINVAL, "the collections must share the cardinality");
+  }
+  if (total_q < 1) return fail(PARIS_EINVAL, "a plan needs nq >= 1");
   if (o.seed == PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "captured plans use the descent seed only");
   auto* pl = new (std::nothrow) paris_knn_plan;
   if (!pl) return fail(PARIS_ENOMEM, "plan");
-  pl->idx = idx;
-  pl->nq = nq;
+  pl->nj = nidx;
   pl->k = k;
   pl->o = o;
   auto bail = [&](paris_status s) {
@@ -1057,47 +1173,37 @@ paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k
     cudaGetLastError();
     return bail(fail(PARIS_ECUDA, "plan stream"));
   }
-  if (!pl->qbuf.alloc((size_t)nq * idx->len * 4, pl->pst) || !pl->obi.alloc((size_t)nq * k * 8, pl->pst) ||
-      !pl->obd.alloc((size_t)nq * k * 4, pl->pst))
-    return bail(fail(PARIS_ENOMEM, "plan buffers"));
-  pl->job = new (std::nothrow) KnnJob;
+  pl->job = new (std::nothrow) KnnJob[nidx];
   if (!pl->job) return bail(fail(PARIS_ENOMEM, "plan"));
-  paris_status st = pl->job->setup(idx, pl->qbuf.as<float>(), nq, k, pl->obi.as<int64_t>(), pl->obd.as<float>(), o,
-                                   nullptr, pl->pst, 1.0);
-  if (st != PARIS_OK) return bail(st);
-  if (pl->job->mixed) {
-    st = ensure_shadow(const_cast<paris_index*>(idx), pl->pst);
+  double rows = 0.0;
+  for (int c = 0; c < nidx; ++c) rows += (double)idx[c]->n;
+  for (int c = 0; c < nidx; ++c) {
+    pl->idx[c] = idx[c];
+    pl->nq[c] = nq[c];
+    const int64_t m = std::max<int64_t>(nq[c], 1);
+    if (!pl->qbuf[c].alloc((size_t)m * idx[c]->len * 4, pl->pst) || !pl->obi[c].alloc((size_t)m * k * 8, pl->pst) ||
+        !pl->obd[c].alloc((size_t)m * k * 4, pl->pst))
+      return bail(fail(PARIS_ENOMEM, "plan buffers"));
+    paris_status st = pl->job[c].setup(idx[c], pl->qbuf[c].as<float>(), nq[c], k, pl->obi[c].as<int64_t>(),
+                                       pl->obd[c].as<float>(), o, nullptr, pl->pst, (double)idx[c]->n / rows);
     if (st != PARIS_OK) return bail(st);
+    if (pl->job[c].mixed) {
+      st = ensure_shadow(const_cast<paris_index*>(idx[c]), pl->pst);
+      if (st != PARIS_OK) return bail(st);
+    }
   }
   if (cudaStreamSynchronize(pl->pst) != cudaSuccess) return bail(fail(PARIS_ECUDA, "plan setup"));
   *out = pl;
   return PARIS_OK;
 }
 
-void paris_knn_plan_free(paris_knn_plan* pl) {
-  if (!pl) return;
-  if (pl->exec) cudaGraphExecDestroy(pl->exec);
-  if (pl->graph) cudaGraphDestroy(pl->graph);
-  delete pl->job;
-  pl->qbuf.release();
-  pl->obi.release();
-  pl->obd.release();
-  if (pl->pst) {
-    cudaStreamSynchronize(pl->pst);
-    cudaStreamDestroy(pl->pst);
-  }
-  if (pl->ev) cudaEventDestroy(pl->ev);
-  delete pl;
-}
-
-namespace {
 paris_status plan_capture(paris_knn_plan* pl) {
   const uint64_t before = launch_count();
   if (cudaStreamBeginCapture(pl->pst, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return fail(PARIS_ECUDA, "stream capture could not start");
   }
-  paris_status s = pl->job->record_all();
+  paris_status s = pl->nj == 1 ? pl->job[0].record_all() : multi_record(pl->job, pl->nj);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(pl->pst, &g);
   if (s != PARIS_OK || e != cudaSuccess || !g) {
@@ -1116,48 +1222,117 @@ paris_status plan_capture(paris_knn_plan* pl) {
   note_launches(-(int)pl->kernels);
   return PARIS_OK;
 }
-}  // namespace
 
-paris_status paris_knn_plan_run(paris_knn_plan* pl, const float* queries, int64_t* out_idx, float* out_dist,
-                                void* stream) {
-  clear_error();
-  if (!pl || !queries || !out_idx) return fail(PARIS_EINVAL, "NULL argument");
+paris_status plan_run(paris_knn_plan* pl, const float* const* queries, int64_t* const* out_idx,
+                      float* const* out_dist, void* stream) {
+  for (int c = 0; c < pl->nj; ++c)
+    if (pl->nq[c] > 0 && (!queries[c] || !out_idx[c])) return fail(PARIS_EINVAL, "NULL argument");
   cudaStream_t cst = (cudaStream_t)stream;
-  KnnJob& job = *pl->job;
   PARIS_CUDA(cudaEventRecord(pl->ev, cst));
   PARIS_CUDA(cudaStreamWaitEvent(pl->pst, pl->ev, 0));
-  PARIS_CUDA(cudaMemcpyAsync(pl->qbuf.p, queries, (size_t)pl->nq * pl->idx->len * 4, cudaMemcpyDefault, pl->pst));
+  for (int c = 0; c < pl->nj; ++c)
+    if (pl->nq[c] > 0)
+      PARIS_CUDA(cudaMemcpyAsync(pl->qbuf[c].p, queries[c], (size_t)pl->nq[c] * pl->idx[c]->len * 4,
+                                 cudaMemcpyDefault, pl->pst));
   bool eager = true;
   if (pl->exec) {
     PARIS_CUDA(cudaGraphLaunch(pl->exec, pl->pst));
     note_launches((int)pl->kernels);
     ++pl->replays;
-    uint32_t word[2] = {0u, 0u};
-    PARIS_CUDA(cudaMemcpyAsync(&word[0], job.qs.status, 4, cudaMemcpyDeviceToHost, pl->pst));
-    PARIS_CUDA(cudaMemcpyAsync(&word[1], job.cs.nover, 4, cudaMemcpyDeviceToHost, pl->pst));
+    uint32_t nover[kMaxScanJobs] = {};
+    for (int c = 0; c < pl->nj; ++c)
+      if (pl->nq[c] > 0)
+        PARIS_CUDA(cudaMemcpyAsync(&nover[c], pl->job[c].cs.nover, 4, cudaMemcpyDeviceToHost, pl->pst));
     PARIS_CUDA(cudaStreamSynchronize(pl->pst));
     // a screened list that overflowed needs the host-driven repeats: run the batch eagerly
-    eager = word[1] != 0u;
-    if (!eager) PARIS_TRY(check_status_word(job.qs.status, pl->pst, "paris_knn_plan_run"));
+    eager = false;
+    for (int c = 0; c < pl->nj; ++c) eager = eager || nover[c] != 0u;
+    if (!eager)
+      for (int c = 0; c < pl->nj; ++c)
+        if (pl->nq[c] > 0) PARIS_TRY(check_status_word(pl->job[c].qs.status, pl->pst, "paris_knn_plan_run"));
   }
   if (eager) {
-    PARIS_TRY(job.run_eager("paris_knn_plan_run"));
+    if (pl->nj == 1)
+      PARIS_TRY(pl->job[0].run_eager("paris_knn_plan_run"));
+    else
+      PARIS_TRY(multi_run_eager(pl->job, pl->nj, "paris_knn_plan_run_multi"));
     ++pl->eager_runs;
     if (!pl->exec && !pl->capture_failed) {
-      // the query tile is settled now; later runs replay the recorded call
+      // the query tiles are settled now; later runs replay the recorded call
       if (plan_capture(pl) != PARIS_OK) {
         pl->capture_failed = true;  // keep running eagerly
         clear_error();
       }
     }
   }
-  PARIS_CUDA(cudaMemcpyAsync(out_idx, pl->obi.p, (size_t)pl->nq * pl->k * 8, cudaMemcpyDefault, pl->pst));
-  if (out_dist)
-    PARIS_CUDA(cudaMemcpyAsync(out_dist, pl->obd.p, (size_t)pl->nq * pl->k * 4, cudaMemcpyDefault, pl->pst));
+  for (int c = 0; c < pl->nj; ++c) {
+    if (pl->nq[c] == 0) continue;
+    PARIS_CUDA(cudaMemcpyAsync(out_idx[c], pl->obi[c].p, (size_t)pl->nq[c] * pl->k * 8, cudaMemcpyDefault, pl->pst));
+    if (out_dist && out_dist[c])
+      PARIS_CUDA(cudaMemcpyAsync(out_dist[c], pl->obd[c].p, (size_t)pl->nq[c] * pl->k * 4, cudaMemcpyDefault,
+                                 pl->pst));
+  }
   PARIS_CUDA(cudaEventRecord(pl->ev, pl->pst));
   PARIS_CUDA(cudaStreamWaitEvent(cst, pl->ev, 0));
   PARIS_CUDA(cudaStreamSynchronize(pl->pst));
   return PARIS_OK;
+}
+}  // namespace
+
+paris_status paris_knn_plan_create(const paris_index* idx, int64_t nq, int32_t k, const paris_query_opts* opts,
+                                   paris_knn_plan** out) {
+  clear_error();
+  if (out) *out = nullptr;
+  if (nq < 1) return fail(PARIS_EINVAL, "a plan needs nq >= 1");
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  return plan_create(&idx, 1, &nq, k, opts, out);
+}
+
+paris_status paris_knn_plan_create_multi(const paris_index* const* idx, int32_t nidx, const int64_t* nq, int32_t k,
+                                         const paris_query_opts* opts, paris_knn_plan** out) {
+  clear_error();
+  if (out) *out = nullptr;
+  if (!idx || !nq) return fail(PARIS_EINVAL, "NULL argument array");
+  for (int c = 0; c < nidx && c < kMaxScanJobs; ++c)
+    if (!idx[c]) return fail(PARIS_EINVAL, "index %d is NULL", c);
+  paris_query_opts o{};
+  if (opts) o = *opts;
+  if (o.mode != PARIS_MODE_BATCHED) return fail(PARIS_EINVAL, "multi-collection plans use BATCHED mode");
+  return plan_create(idx, nidx, nq, k, &o, out);
+}
+
+void paris_knn_plan_free(paris_knn_plan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  delete[] pl->job;
+  for (int c = 0; c < kMaxScanJobs; ++c) {
+    pl->qbuf[c].release();
+    pl->obi[c].release();
+    pl->obd[c].release();
+  }
+  if (pl->pst) {
+    cudaStreamSynchronize(pl->pst);
+    cudaStreamDestroy(pl->pst);
+  }
+  if (pl->ev) cudaEventDestroy(pl->ev);
+  delete pl;
+}
+
+paris_status paris_knn_plan_run(paris_knn_plan* pl, const float* queries, int64_t* out_idx, float* out_dist,
+                                void* stream) {
+  clear_error();
+  if (!pl || !queries || !out_idx) return fail(PARIS_EINVAL, "NULL argument");
+  if (pl->nj != 1) return fail(PARIS_EINVAL, "a multi-collection plan runs with paris_knn_plan_run_multi");
+  float* const od[1] = {out_dist};
+  return plan_run(pl, &queries, &out_idx, out_dist ? od : nullptr, stream);
+}
+
+paris_status paris_knn_plan_run_multi(paris_knn_plan* pl, const float* const* queries, int64_t* const* out_idx,
+                                      float* const* out_dist, void* stream) {
+  clear_error();
+  if (!pl || !queries || !out_idx) return fail(PARIS_EINVAL, "NULL argument");
+  return plan_run(pl, queries, out_idx, out_dist, stream);
 }
 
 paris_status paris_knn_plan_info(const paris_knn_plan* pl, paris_knn_plan_stats* out) {
@@ -1168,7 +1343,7 @@ paris_status paris_knn_plan_info(const paris_knn_plan* pl, paris_knn_plan_stats*
   out->replays = pl->replays;
   out->eager_runs = pl->eager_runs;
   out->captured = pl->exec != nullptr;
-  out->query_tile = pl->job ? pl->job->qt : 0;
+  out->query_tile = pl->job ? pl->job[0].qt : 0;
   return PARIS_OK;
 }
 
@@ -1190,48 +1365,16 @@ paris_status paris_exact_knn_multi(const paris_index* const* idx, int32_t nidx, 
   }
   cudaStream_t st = (cudaStream_t)stream;
   KnnJob jobs[kMaxScanJobs];
-  int64_t rounds = 0;
   double total = 0.0;
   for (int c = 0; c < nidx; ++c) total += (double)idx[c]->n;
   for (int c = 0; c < nidx; ++c) {
     // candidate-list memory is shared in proportion to collection size
     PARIS_TRY(jobs[c].setup(idx[c], queries[c], nq[c], k, out_idx[c], out_dist ? out_dist[c] : nullptr, o,
                             stats ? &stats[c] : nullptr, st, (double)idx[c]->n / total));
-    PARIS_TRY(jobs[c].front());
-    rounds = std::max(rounds, jobs[c].chunks());
   }
-  for (int64_t r = 0; r < rounds; ++r) {
-    ScanJob sj[kMaxScanJobs];
-    int m = 0, qt = 0;
-    double most = -1.0;
-    for (int c = 0; c < nidx; ++c) {
-      if (r >= jobs[c].chunks()) continue;
-      PARIS_TRY(jobs[c].begin_chunk(r));
-      if (o.mode == PARIS_MODE_BATCHED) {
-        sj[m++] = ScanJob{idx[c], &jobs[c].qs, &jobs[c].cs, jobs[c].mixed ? 1 : 0, jobs[c].lb_status};
-        const double work = (double)idx[c]->n * jobs[c].cs.qc;
-        if (work > most) {  // one query tile per launch: the tuned tile of the largest share
-          most = work;
-          qt = jobs[c].qt;
-        }
-      } else {
-        PARIS_TRY(jobs[c].scan_chunk());
-      }
-    }
-    if (m > 0) {
-      // one launch scans every collection's chunk; its time is charged to each collection
-      for (int c = 0; c < nidx; ++c)
-        if (r < jobs[c].chunks()) jobs[c].timer.begin(2);
-      PARIS_TRY(launch_lbscan_batched_multi(sj, m, qt, st));
-      for (int c = 0; c < nidx; ++c)
-        if (r < jobs[c].chunks()) jobs[c].timer.end(2);
-    }
-    for (int c = 0; c < nidx; ++c)
-      if (r < jobs[c].chunks()) PARIS_TRY(jobs[c].finish_chunk());
-  }
-  for (int c = 0; c < nidx; ++c) PARIS_TRY(jobs[c].finish("paris_exact_knn_multi"));
-  return PARIS_OK;
+  return multi_run_eager(jobs, nidx, "paris_exact_knn_multi");
 }
+
 paris_status paris_exact_knn(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
                              int64_t* out_idx, float* out_dist, void* stream) {
   return paris_exact_knn_ex(idx, queries, nq, k, out_idx, out_dist, nullptr, nullptr, stream);

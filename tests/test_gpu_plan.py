@@ -95,3 +95,39 @@ def test_plan_rejects_bad_arguments(setup):
         P.KnnPlan(idx, 0, 1)
     with pytest.raises(P.ParisError):
         P.KnnPlan(idx, 4, 0)
+
+
+def test_multi_collection_plan_replays_match_oracle():
+    """Three collections of lengths 128, 256 and 1024 (uneven query counts, one collection with
+    no queries in the second plan) recorded as one graph: every replay equals the oracle and the
+    eager multi-collection call."""
+    import paper_2009_00166_gb300 as P
+    import synth
+    dev = require_gpu()
+    shapes = [(60_000, 128, 41), (40_000, 256, 42), (6_000, 1024, 43)]
+    xs = [synth.random_walk(n, length, seed=s) for n, length, s in shapes]
+    idxs = [P.paris_build_ex(torch.from_numpy(x).to(dev), bf16_shadow=x.shape[1] <= 256) for x in xs]
+    for nqs in ([9, 14, 5], [12, 0, 7]):
+        for prec in (P.PARIS_REFINE_FP32, P.PARIS_REFINE_MIXED):
+            plan = P.KnnPlanMulti(idxs, nqs, 3, precision=prec)
+            for rep in range(3):
+                qs = [synth.mixed_sigma_queries(x, x.shape[0], x.shape[1], m, 0.01, 2.0, seed=70 + 10 * rep + c)[0]
+                      if m else np.zeros((0, x.shape[1]), np.float32) for c, (x, m) in enumerate(zip(xs, nqs))]
+                Qs = [torch.from_numpy(np.ascontiguousarray(q)).to(dev) for q in qs]
+                outs = plan.run(Qs)
+                eager = P.paris_exact_knn_multi(idxs, Qs, 3, precision=prec)
+                for c, (x, q) in enumerate(zip(xs, qs)):
+                    if not len(q):
+                        continue
+                    wi, wd = oknn.knn(x, q, 3)
+                    gi, gd = outs[c][0].cpu().numpy(), outs[c][1].cpu().numpy()
+                    assert np.array_equal(gi, wi), (nqs, prec, rep, c)
+                    assert np.allclose(gd, wd, rtol=1e-5, atol=0)
+                    assert np.array_equal(gi, eager[c][0].cpu().numpy())
+            info = plan.info()
+            assert info["captured"] == 1 and info["replays"] + info["eager_runs"] == 3 and info["replays"] >= 1
+            plan.free()
+    with pytest.raises(P.ParisError):
+        P.KnnPlanMulti(idxs, [0, 0, 0], 3)
+    for ix in idxs:
+        ix.free()
