@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--clocks-csv", default="", help="keep the raw nvidia-smi clock samples of the timed region here")
+    p.add_argument("--leaf-capacity", type=int, default=0, help="rows per approximate-search leaf (0: 2048)")
     p.add_argument("--batch-n", type=int, default=50_000_000,
                    help="rows of the 4096-query batch workload reported beside (0: skip it)")
     p.add_argument("--multi-scale", type=float, default=1.0,
@@ -531,7 +532,7 @@ def main():
         """Build, then answer every query: one call for the whole batch, or one per sigma group."""
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        idx = P.paris_build_ex(X, 16, 256, bf16_shadow=prec == P.PARIS_REFINE_MIXED)
+        idx = P.paris_build_ex(X, 16, 256, bf16_shadow=prec == P.PARIS_REFINE_MIXED, leaf_capacity=args.leaf_capacity)
         e1.record(stream)
         if sd == P.PARIS_SEED_LEARNED:
             P.paris_attach_seed_model(idx, model, 3)

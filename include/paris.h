@@ -160,7 +160,7 @@ typedef struct paris_query_stats {
   int64_t pages_kept;     /* ... of which passed (their rows were scanned for that query) */
   int64_t bsf_updates;    /* times refinement lowered a query's shared threshold */
   int64_t list_rows;      /* BATCHED with leaf pruning: rows tested one query at a time by the
-                             list scan (queries whose kept pages fit a list of 16384 pages; the
+                             list scan (queries whose kept pages fit a list of 32768 pages; the
                              others share tile passes, counted in lb_lookups) */
 } paris_query_stats;
 

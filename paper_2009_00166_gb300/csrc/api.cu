@@ -765,6 +765,7 @@ struct KnnJob {
       cudaMemGetInfo(&freeb, &totalb);
       double budget = std::min((double)freeb * 0.3, 24.0e9) * budget_share;
       qc = (int64_t)(budget / ((double)cap * 20.0 + (double)kContCap * (4 * kLimbs + 4) + 16384.0 +
+                               (double)page_list_cap(idx->n) * 4.0 + (double)page_words(idx->n) * 4.0 +
                                (double)idx->card * 32.0));
       qc = std::max<int64_t>(1, std::min<int64_t>(qc, 4096));
     }

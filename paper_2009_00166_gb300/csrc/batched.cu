@@ -513,6 +513,13 @@ __global__ void __launch_bounds__(1024) order_kernel(const uint32_t* __restrict_
   }
 }
 
+// Marks the queries whose kept pages exceed the list capacity as overflowed (count = cap + 1).
+__global__ void page_route_kernel(const uint32_t* __restrict__ page_count, int qc, int64_t list_cap, int64_t cap,
+                                  uint32_t* __restrict__ count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < qc && (int64_t)page_count[q] > list_cap) count[q] = (uint32_t)(cap + 1);
+}
+
 // Marks the queries whose scaled pilot count reaches `limit` as overflowed (count = cap + 1).
 __global__ void pilot_route_kernel(const uint32_t* __restrict__ pilot, int qc, int64_t stride, double limit,
                                    int64_t cap, uint32_t* __restrict__ count) {
@@ -610,7 +617,14 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     C.lookups = qs.counters + 4;
     pack(qs, cs, nullptr);
     const bool route = C.stop && cs.cap < idx->n;
-    if (groups >= 64 * kPilotStride && (route || C.ntiles > 1)) {
+    if (route && cs.pagebits) {
+      // with leaf pruning in MIXED refinement, every query whose kept pages do not fit its list
+      // goes to the tensor-core screening (one pass of 2 len flops per row and query costs less
+      // than scanning a fifth or more of the summaries and refining what it keeps); the others
+      // take the list scan, so neither the pilot pass nor the tile scan has work
+      page_route_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.page_count, cs.qc, C.list_cap, cs.cap, cs.count);
+      note_launches(1);
+    } else if (groups >= 64 * kPilotStride && (route || C.ntiles > 1)) {
       // the pilot pass: route lists that would overflow anyway (MIXED) and order the tiles
       C.pilot = cs.pilot;
       PARIS_CUDA(cudaMemsetAsync(cs.pilot, 0, (size_t)cs.qc * 8, st));

@@ -203,9 +203,10 @@ __device__ __forceinline__ void build_symbol_table(const uint64_t* beta_keys, in
 // Number of breakpoints <= v (upper region on ties): the bucket table's estimate, moved to the
 // exact answer by comparing order keys of the FP64 values (one step at most, up to 8 tried); the
 // binary search below is the fallback.
-__device__ __forceinline__ int symbol_of(double v, const uint64_t* beta_keys, const uint8_t* tab, int card) {
+__device__ __forceinline__ int symbol_of(double v, float fest, const uint64_t* beta_keys, const uint8_t* tab,
+                                         int card) {
   const uint64_t key = double_order_key(v);
-  const float f = fminf(fmaxf(__double2float_rn(v), -8.0f), 7.99f);
+  const float f = fminf(fmaxf(fest, -8.0f), 7.99f);
   int b = (int)((f + 8.0f) * 256.0f);
   b = b < 0 ? 0 : (b > kSymBuckets - 1 ? kSymBuckets - 1 : b);
   int sym = tab[b];
@@ -249,14 +250,19 @@ struct RowShape {
 // segment's largest exponent so that the sum fits in 63 bits; they are summed exactly in int64
 // and rounded once. Segments holding values finer than 2^lambda (or subnormals) take the
 // 320-bit exact accumulator instead. Returns false if the lane's segment holds a NaN or infinity.
-template <int SEGV>
+// With PRE (fast path, SEGV <= 4 only), `pre` already holds the lane's segment values (zeros
+// for an inactive lane), so a caller can load the next rows while this one is summed. `fest`
+// receives an fp32 estimate of PAA_i (for the symbol search's starting point).
+template <int SEGV, bool PRE = false>
 __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0, const float* __restrict__ row1,
-                                                 const RowShape& sh, int lane, double& paa_out) {
+                                                 const RowShape& sh, int lane, double& paa_out, float& fest,
+                                                 const float4 (&pre)[SEGV <= 4 ? SEGV : 1]) {
   const int seg = lane & 15;
   const float* row = (lane >> 4) ? row1 : row0;
   const bool active = row != nullptr && seg < sh.w;
   const int s = sh.s;
   paa_out = 0.0;
+  fest = 0.f;
   bool finite = true;
   bool done = false;
   if (sh.fast) {
@@ -268,7 +274,7 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
     uint32_t mb = 0u, mn = 0xffffffffu;
 #pragma unroll
     for (int v = 0; v < SEGV; ++v) {
-      float4 x = active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 x = (PRE && kCache) ? pre[kCache ? v : 0] : (active ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f));
       if (kCache) cache[kCache ? v : 0] = x;
       const uint32_t u0 = __float_as_uint(x.x) & 0x7fffffffu, u1 = __float_as_uint(x.y) & 0x7fffffffu;
       const uint32_t u2 = __float_as_uint(x.z) & 0x7fffffffu, u3 = __float_as_uint(x.w) & 0x7fffffffu;
@@ -307,7 +313,12 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
           lo = __fadd_rn(lo, err);
         }
       }
-      paa_out = __dadd_rn((double)hi, (double)lo) * exp2_int(-sh.log2s);  // s is a power of two here
+      // divide by s = 2^L by the exponent field (the sum, if nonzero, is a normal FP64 value far
+      // above 2^(L-1022): it is a multiple of a normal fp32 value's ulp)
+      const double S = __dadd_rn((double)hi, (double)lo);
+      const uint64_t sb = (uint64_t)__double_as_longlong(S);
+      paa_out = (sb << 1) == 0ull ? 0.0 : __longlong_as_double((long long)(sb - ((uint64_t)sh.log2s << 52)));
+      fest = hi * __uint_as_float((uint32_t)(127 - sh.log2s) << 23);
       done = true;
     } else if ((mb >> 23) != 0u) {
       // values are integer multiples of 2^lambda when no nonzero magnitude is below 2^(lambda+23);
@@ -355,7 +366,16 @@ __device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0,
     double S = wide_to_double(acc);
     paa_out = sh.log2s >= 0 ? S * (1.0 / (double)(1 << sh.log2s)) : __ddiv_rn(S, (double)s);
   }
+  if (done && fest == 0.f && paa_out != 0.0) fest = __double2float_rn(paa_out);
+  if (!done) fest = __double2float_rn(paa_out);
   return finite;
+}
+
+template <int SEGV>
+__device__ __forceinline__ bool lane_segment_paa(const float* __restrict__ row0, const float* __restrict__ row1,
+                                                 const RowShape& sh, int lane, double& paa_out, float& fest) {
+  const float4 none[SEGV <= 4 ? SEGV : 1] = {};
+  return lane_segment_paa<SEGV, false>(row0, row1, sh, lane, paa_out, fest, none);
 }
 
 // Top 64 bits of the bit-plane interleaved key of both rows of a warp (lanes 0-15: row 0,

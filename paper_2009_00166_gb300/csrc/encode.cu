@@ -27,29 +27,50 @@ __global__ void __launch_bounds__(kEncodeThreads) encode_kernel(
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t pairs = (n + 1) >> 1;
   bool nonfinite = false;
-  for (int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pr < pairs; pr += warps) {
+  // fast path with the segment in registers: the next row pair's values are loaded while this
+  // pair is summed, encoded and converted (the loads are the kernel's bound)
+  constexpr bool kPre = SEGV <= 4;
+  constexpr int PN = SEGV <= 4 ? SEGV : 1;
+  const bool pre = kPre && sh.fast;
+  auto load_pair = [&](int64_t pr, float4 (&x)[PN]) {
+    const int64_t r = 2 * pr + half;
+    const bool act = pr < pairs && r < n && seg < sh.w;
+    const float4* p = reinterpret_cast<const float4*>(series + r * (int64_t)sh.len + (act ? seg * sh.s : 0));
+#pragma unroll
+    for (int v = 0; v < PN; ++v) x[v] = act ? __ldcs(p + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float4 nxt[PN];
+  if (pre) load_pair(pr, nxt);
+  for (; pr < pairs; pr += warps) {
+    float4 cur[PN];
+#pragma unroll
+    for (int v = 0; v < PN; ++v) cur[v] = nxt[v];
+    if (pre) load_pair(pr + warps, nxt);
     const int64_t r0 = 2 * pr;
     const bool has1 = r0 + 1 < n;
     const float* row0 = series + r0 * (int64_t)sh.len;
     const float* row1 = has1 ? row0 + sh.len : nullptr;
     double paa = 0.0;
-    if (!lane_segment_paa<SEGV>(row0, row1, sh, lane, paa)) nonfinite = true;
+    float fest = 0.f;
+    const bool fin = pre ? lane_segment_paa<SEGV, true>(row0, row1, sh, lane, paa, fest, cur)
+                         : lane_segment_paa<SEGV>(row0, row1, sh, lane, paa, fest);
+    if (!fin) nonfinite = true;
     const int64_t r = r0 + half;
     const bool rv = half == 0 || has1;
-    const int sym = (rv && seg < sh.w) ? symbol_of(paa, beta_keys, sym_tab, card) : 0;
+    const int sym = (rv && seg < sh.w) ? symbol_of(paa, fest, beta_keys, sym_tab, card) : 0;
     const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     // rotated summary slot: slot j holds segment (j + r) mod 16 (0 when that segment >= w)
     const int src = (seg + (int)(r & 15)) & 15;
     const int b = __shfl_sync(PARIS_FULL_MASK, sym, (half << 4) | src);
     if (SEGV <= 4 && shadow) {
       // BF16 copy of the lane's segment and the row's fp32 squared norm (the mixed-precision
-      // screening's inputs), from the values this warp has just read
+      // screening's inputs), from the values this warp holds (zeros for an inactive lane)
       const bool act = rv && seg < sh.w;
-      const float4* p = reinterpret_cast<const float4*>(series + r * (int64_t)sh.len + (act ? seg * sh.s : 0));
       float acc = 0.f;
 #pragma unroll
-      for (int v = 0; v < (SEGV <= 4 ? SEGV : 1); ++v) {
-        const float4 x = act ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int v = 0; v < PN; ++v) {
+        const float4 x = cur[v];
         acc = fmaf(x.x, x.x, acc);
         acc = fmaf(x.y, x.y, acc);
         acc = fmaf(x.z, x.z, acc);

@@ -347,7 +347,7 @@ int sm_count_leaf() {
 
 int64_t page_count(int64_t n) { return (n + kPageRows - 1) / kPageRows; }
 int64_t page_words(int64_t n) { return (page_count(n) + 31) / 32; }
-int64_t page_list_cap(int64_t n) { return std::min<int64_t>(page_count(n), 16384); }
+int64_t page_list_cap(int64_t n) { return std::min<int64_t>(page_count(n), 32768); }
 
 paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st) {
   const int64_t n = idx->n, npages = page_count(n), nsuper = (npages + 15) / 16;

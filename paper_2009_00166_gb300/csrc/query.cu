@@ -109,38 +109,45 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4, seg = lane & 15;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const double scale = (double)(sh.len / sh.w);
   const int64_t pairs = (nq + 1) >> 1;
   for (int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pr < pairs; pr += warps) {
     const int64_t q0 = 2 * pr;
     const bool has1 = q0 + 1 < nq;
     const float* row0 = queries + q0 * (int64_t)sh.len;
     double paa = 0.0;
-    if (!lane_segment_paa<SEGV>(row0, has1 ? row0 + sh.len : nullptr, sh, lane, paa)) atomicOr(status, DEV_NONFINITE);
+    float fest = 0.f;
+    if (!lane_segment_paa<SEGV>(row0, has1 ? row0 + sh.len : nullptr, sh, lane, paa, fest))
+      atomicOr(status, DEV_NONFINITE);
     const int64_t q = q0 + half;
     const bool qv = half == 0 || has1;
-    const int sym = (qv && seg < sh.w) ? symbol_of(paa, beta_keys, sym_tab, card) : 0;
+    const int sym = (qv && seg < sh.w) ? symbol_of(paa, fest, beta_keys, sym_tab, card) : 0;
     const uint64_t key = warp_pair_key64(sym, lane, sh.w, bits);
     if (!qv) continue;
     qpaa[q * 16 + seg] = seg < sh.w ? paa : 0.0;
     if (qsym) qsym[q * 16 + seg] = (uint8_t)sym;  // 0 past w, like the summaries' unused slots
     if (seg == 0) qkey[q] = key;
-    const double P = paa;
-    float* T = qtable + q * (int64_t)card * 16;
-    for (int c = 0; c < card; ++c) {
-      float val = 0.f;
-      if (seg < sh.w) {
-        const double lo = beta_ext[c], hi = beta_ext[c + 1];
-        double d = 0.0;
-        if (P < lo) d = lo - P;
-        else if (P > hi) d = P - hi;
-        const double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
-        d = fmax(0.0, d - mag * 0x1p-50);
-        val = __double2float_rd(scale * d * d);
-      }
-      T[c * 16 + seg] = val;
-    }
   }
+}
+
+// The lower-bound table, one entry per thread: T[c][i] for query blockIdx.y.
+__global__ void __launch_bounds__(256) qtable_kernel(const double* __restrict__ qpaa, int card, int w, double scale,
+                                                     const double* __restrict__ beta_ext, float* __restrict__ qtable) {
+  const int64_t q = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= card * 16) return;
+  const int c = e >> 4, seg = e & 15;
+  float val = 0.f;
+  if (seg < w) {
+    const double P = qpaa[q * 16 + seg];
+    const double lo = beta_ext[c], hi = beta_ext[c + 1];
+    double d = 0.0;
+    if (P < lo) d = lo - P;
+    else if (P > hi) d = P - hi;
+    const double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
+    d = fmax(0.0, d - mag * 0x1p-50);
+    val = __double2float_rd(scale * d * d);
+  }
+  qtable[q * (int64_t)card * 16 + e] = val;
 }
 
 // --------------------------------------------------------------------- approximate search
@@ -900,7 +907,10 @@ paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cud
     default: PREP(32); break;
   }
 #undef PREP
-  note_launches(1);
+  dim3 tg((unsigned)((idx->card * 16 + 255) / 256), (unsigned)qs.nq);
+  qtable_kernel<<<tg, 256, 0, st>>>(qs.qpaa, idx->card, idx->w, (double)(idx->len / idx->w), idx->beta_ext,
+                                    qs.qtable);
+  note_launches(2);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }

@@ -15,23 +15,24 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_IPT = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
 
+// Per-block digit counts (one private histogram per warp, summed at the end).
 __global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                          int shift, uint32_t* __restrict__ hist, int nblocks) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  __shared__ uint32_t h[RS_WARPS][256];
+  for (int w = 0; w < RS_WARPS; ++w) h[w][threadIdx.x] = 0;
   __syncthreads();
+  const int warp = threadIdx.x >> 5;
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
 #pragma unroll 4
   for (int j = 0; j < RS_IPT; ++j) {
     int64_t i = base + j * RS_THREADS + threadIdx.x;
-    if (i < n) {
-      uint32_t d = (uint32_t)(keys[i] >> shift) & 255u;
-      uint32_t peers = __match_any_sync(__activemask(), d);
-      if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
+    if (i < n) atomicAdd(&h[warp][(uint32_t)(__ldcs(keys + i) >> shift) & 255u], 1u);
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) c += h[w][threadIdx.x];
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = c;
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024); returns the total.
