@@ -585,6 +585,7 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
   double work[kMaxColl], pwork[kMaxColl];
   int pilot_of[kMaxColl];  // scan collection of each pilot collection
   int64_t groups_total = 0, pilot_samples = 0;
+  bool any_tiles = false;
   auto pack = [&](const QueryState& qs, const ChunkState& cs, const int* perm) {
     pack_pairs_kernel<<<(unsigned)std::min<int64_t>(((cs.qc + 1) / 2 * entries + 255) / 256, 4096), 256, 0, st>>>(
         qs.qtable + cs.q0 * entries, cs.qc, entries, perm, cs.packed);
@@ -615,8 +616,8 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     C.stop = jobs[j].stop;
     C.status = jobs[j].status;
     C.lookups = qs.counters + 4;
-    pack(qs, cs, nullptr);
     const bool route = C.stop && cs.cap < idx->n;
+    if (!(route && cs.pagebits)) pack(qs, cs, nullptr);  // FP16 tables of the tile scan
     if (route && cs.pagebits) {
       // with leaf pruning in MIXED refinement, every query whose kept pages do not fit its list
       // goes to the tensor-core screening (one pass of 2 len flops per row and query costs less
@@ -624,6 +625,7 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
       // take the list scan, so neither the pilot pass nor the tile scan has work
       page_route_kernel<<<(cs.qc + 255) / 256, 256, 0, st>>>(cs.page_count, cs.qc, C.list_cap, cs.cap, cs.count);
       note_launches(1);
+      C.ntiles = 0;  // no query of this collection is left for the tile scan
     } else if (groups >= 64 * kPilotStride && (route || C.ntiles > 1)) {
       // the pilot pass: route lists that would overflow anyway (MIXED) and order the tiles
       C.pilot = cs.pilot;
@@ -637,6 +639,7 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     W.c[W.ncoll] = C;
     work[W.ncoll++] = (double)groups * C.ntiles;
     groups_total += groups;
+    any_tiles = any_tiles || C.ntiles > 0;
   }
   if (PW.ncoll > 0) {
     const int pgrid = (int)std::max<int64_t>(PW.ncoll, std::min<int64_t>(sms, pilot_samples / 64));
@@ -661,10 +664,12 @@ paris_status launch_np(const ScanJob* jobs, int m, cudaStream_t st) {
     PARIS_CUDA(cudaGetLastError());
   }
   const int grid = (int)std::max<int64_t>(W.ncoll, std::min<int64_t>(sms, (groups_total + 63) / 64));
-  split_ctas(W, work, grid);
-  lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(W);
-  note_launches(1);
-  PARIS_CUDA(cudaGetLastError());
+  if (any_tiles) {
+    split_ctas(W, work, grid);
+    lbscan_batched_kernel<NP><<<grid, kBThreads, smem, st>>>(W);
+    note_launches(1);
+    PARIS_CUDA(cudaGetLastError());
+  }
   // the queries that the leaf pruning left with few pages: one work item per few pages each
   for (int j = 0; j < m; ++j)
     if (jobs[j].cs->pagebits) PARIS_TRY(launch_lbscan_lists(jobs[j].idx, *jobs[j].qs, *jobs[j].cs, jobs[j].stop,

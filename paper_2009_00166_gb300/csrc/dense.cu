@@ -46,7 +46,8 @@ constexpr int BM = 128;             // queries per tile (MMA M)
 constexpr int BN = 128;             // series rows per tile (MMA N)
 constexpr int RT = 64;              // rows per norm-range tile (xtile) and per norm block
 constexpr int BKE = 64;             // K elements per TMA box: 128 bytes of BF16
-constexpr int QTILES = 2;           // query tiles sharing each row tile
+constexpr int QTILES = 2;           // query tiles sharing each row tile (one query group)
+constexpr int GROUPS = 8;           // query groups per launch, each on its own share of the CTAs
 constexpr int STAGES = 6;           // shared-memory ring depth: one (row tile, K block) per stage
 constexpr int DENSE_THREADS = 576;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-17: epilogue
 constexpr int EPI_WARPS = 16;       // per TMEM lane quadrant: one per (query tile, 64-row half)
@@ -60,13 +61,20 @@ constexpr size_t A_BYTES = (size_t)QTILES * MAX_KB * BM * 128;
 constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * KBLK_BYTES + 256;
 static_assert(BM * 128 == KBLK_BYTES, "query and row tiles share the K-block shape");
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
+// pass 2 (emit_kernel): a query group of QG queries is the MMA N side
+constexpr int QG = QTILES * BM;                          // queries per group
+constexpr int E_STAGES = 5;                              // its ring depth
+constexpr size_t Q_BYTES = (size_t)MAX_KB * QG * 128;   // the group's K blocks
+constexpr size_t EMIT_SMEM = 1024 + Q_BYTES + E_STAGES * KBLK_BYTES + EPI_WARPS * 64 * 4 + QG * 16 + 256;
+static_assert(EMIT_SMEM <= 232448, "dynamic shared memory of one CTA");
+static_assert(2 * QG <= (int)TMEM_COLS, "two accumulators of QG columns");
 constexpr unsigned long long kDrainNs = 100000000ull;  // extra bound of the drain waits after an abort
 
 struct DenseParams {
   uint64_t wait_ns;  // bound of every wait of a role on another role (paris_set_wait_limit)
   int64_t n;
   int len, nkb;
-  int qtile, nd;         // nd < 0: the count of screened queries is read from nd_dev
+  int group0, nd;        // first query group of the launch; nd < 0: read from nd_dev
   const int* nd_dev;
   const float2* xnorm;  // [n]: (|x|^2, |x|)
   const uint32_t* qbf;  // BF16 query rows, [rows][len] (pairs of elements per word)
@@ -179,14 +187,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int PHASE>
+// Pass 1: the k smallest upper ends per query over every SAMPLE-th row tile (queries on the MMA
+// M side, 128 x 128 x 16 MMAs: one thread per query in the epilogue keeps its own top k).
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
-    dense_kernel(const __grid_constant__ CUtensorMap tmB, DenseParams P) {
+    bound_kernel(const __grid_constant__ CUtensorMap tmB, DenseParams P) {
   extern __shared__ uint8_t dsm_raw[];
-  // a launch for a query tile past the screened queries has nothing to do (uniform per grid)
+  // The launch's query groups (QTILES query tiles each) split the CTAs; the CTAs of every group
+  // visit the row tiles in the same order at about the same time, so a row tile read from HBM by
+  // one group is served from L2 to the others. Uniform per CTA: a CTA without a group returns.
   const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
-  if (P.qtile * BM >= nd) return;
-  const int nq_tiles = (P.qtile + 1) * BM < nd ? 2 : 1;  // query tiles of this launch that hold queries
+  const int groups = (nd + QTILES * BM - 1) / (QTILES * BM) - P.group0;
+  if (groups <= 0) return;
+  const int G = groups < GROUPS ? groups : GROUPS;
+  const int cpg = (int)gridDim.x / G;  // CTAs per group (the grid holds at least GROUPS CTAs)
+  const int grp = (int)blockIdx.x % G, rank = (int)blockIdx.x / G;
+  if (rank >= cpg) return;
+  const int qtile = (P.group0 + grp) * QTILES;
+  const int nq_tiles = (qtile + 1) * BM < nd ? 2 : 1;  // query tiles of this group that hold queries
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* smA = base;            // [QTILES][MAX_KB] query K blocks, 128-byte swizzle
   uint8_t* smB = base + A_BYTES;  // [STAGES] row-tile K blocks, 128-byte swizzle (written by TMA)
@@ -223,7 +240,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     const int chunks = nq_tiles * nkb * BM * 8;
     for (int e = threadIdx.x; e < chunks; e += blockDim.x) {
       const int j = e & 7, r = (e >> 3) & (BM - 1), kb = (e >> 10) % nkb, c = (e >> 10) / nkb;
-      const int64_t grow = (int64_t)(P.qtile + c) * BM + r;
+      const int64_t grow = (int64_t)(qtile + c) * BM + r;
       const uint4 v = *reinterpret_cast<const uint4*>(P.qbf + grow * (P.len / 2) + kb * (BKE / 2) + j * 4);
       *reinterpret_cast<uint4*>(smA + ((size_t)(c * MAX_KB + kb) * KBLK_BYTES) + r * 128 + ((j ^ (r & 7)) << 4)) = v;
     }
@@ -235,9 +252,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   const uint32_t tmem_base = *tmem_holder;
   const int64_t ntiles = (P.n + BN - 1) / BN;
   const int64_t nranges = (P.n + RT - 1) / RT;
-  // pass 1 needs the upper ends of any k rows: it visits every SAMPLE-th tile; pass 2 visits all
-  const int64_t tstep = (PHASE == 1 ? SAMPLE : 1);
-  const int64_t tfirst = (int64_t)blockIdx.x * tstep, tstride = (int64_t)gridDim.x * tstep;
+  // the upper ends of any k rows bound the k-th distance: every SAMPLE-th tile is enough
+  const int64_t tstep = SAMPLE;
+  const int64_t tfirst = (int64_t)rank * tstep, tstride = (int64_t)cpg * tstep;
   const uint64_t deadline = globaltimer() + P.wait_ns;
   const int nkb = P.nkb;
 
@@ -309,18 +326,15 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     const int h = (warp - 2) >> 3;        // 64-row half of each row tile
     const bool tile_on = c < nq_tiles;  // warp-uniform: this warp's query tile holds queries
     const int m = qd * 32 + lane;
-    const int d = (P.qtile + c) * BM + m;
+    const int d = (qtile + c) * BM + m;
     const bool valid = d < nd;
-    float qn = 0.f, qrt = 0.f, thr_q = 0.f;
-    int slot = 0;
+    float qn = 0.f, qrt = 0.f;
     uint32_t* thr_ptr = nullptr;
     if (valid) {
       const float2 qq = P.qnorm[d];
       qn = qq.x;
       qrt = qq.y;
-      slot = P.qslot[d];
-      thr_ptr = P.thr + P.q0 + slot;
-      thr_q = __uint_as_float(*(volatile uint32_t*)thr_ptr);
+      thr_ptr = P.thr + P.q0 + P.qslot[d];
     }
     const float c1q = __fmul_ru(P.c1, qrt);
     float best[KMAX];
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
           float dmax = __uint_as_float(v[0]);
 #pragma unroll
           for (int jj = 1; jj < 32; ++jj) dmax = fmaxf(dmax, __uint_as_float(v[jj]));
-          if (PHASE == 1) {
+          {
             // upper ends from the range's norms: ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max))
             const float Cq = __fadd_ru(qn, Mmax);
             if (valid && __fadd_ru(__fmaf_ru(-2.0f, dmax, rng.y), Cq) < kth) {
@@ -392,29 +406,261 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
                   if (q2 == P.k - 1) kth = best[q2];
               }
             }
-          } else {
-            // drop unless rd(xn_min - 2 dot) <= ru(thr + M_max - |q|^2)
-            const float R = __fsub_ru(__fadd_ru(thr_q, Mmax), qn);
-            if (valid && __fmaf_rd(-2.0f, dmax, rng.x) <= R) {
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+    }
+    if (valid && kth < CUDART_INF_F) atomicMin(thr_ptr, __float_as_uint(__fmul_ru(kth, P.cg)));
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, DEV_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// R+ of a float: the next float above it (the test rd(y) <= R holds exactly when y < R+).
+__device__ __forceinline__ float next_up(float r) {
+  if (r == 0.f) return __uint_as_float(1u);
+  if (isinf(r) && r > 0.f) return r;
+  const uint32_t b = __float_as_uint(r);
+  return __uint_as_float(r > 0.f ? b + 1u : b - 1u);
+}
+
+// Pass 2: every row whose interval's lower end does not exceed the query's threshold becomes a
+// candidate. Rows on the MMA M side and up to 256 queries on the N side: one 128 x N x 16 MMA
+// per K step reads a row tile once for every query of the group (the tensor cores run at their
+// full rate with N = 256; 128 x 128 shapes with both operands in shared memory run at about
+// half of it). The accumulator of a row tile is 128 lanes (rows) x N columns (queries).
+//
+// Epilogue: a thread owns one row and 64 queries (two chunks of 32 columns). Per chunk and query
+// the range test rd(xn_min - 2 dot) <= R, R = ru(ru(thr + M_max) - |q|^2), is applied in the
+// equivalent-or-looser form dot >= L with L = rd(rd(xn_min - R+) / 2): rd(xn_min - 2 dot) <= R
+// means xn_min - 2 dot < R+, that is dot > (xn_min - R+) / 2 >= L. L depends on the query and
+// the row's 64-row norm range only, so each warp writes its 64 values per tile to shared memory
+// and every lane reads them back (one address per warp). A pair that passes gets the row's own
+// interval and is emitted when d~ - M <= thr.
+__global__ void __launch_bounds__(DENSE_THREADS, 1)
+    emit_kernel(const __grid_constant__ CUtensorMap tmX, DenseParams P) {
+  extern __shared__ uint8_t dsm_raw[];
+  const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
+  const int groups = (nd + QG - 1) / QG - P.group0;
+  if (groups <= 0) return;
+  const int G = groups < GROUPS ? groups : GROUPS;
+  const int cpg = (int)gridDim.x / G;
+  const int grp = (int)blockIdx.x % G, rank = (int)blockIdx.x / G;
+  if (rank >= cpg) return;
+  const int gq0 = (P.group0 + grp) * QG;        // first screened query of the group
+  const int nq = min(QG, nd - gq0);              // its queries
+  const int ncols = (nq + 31) & ~31;             // MMA N (a multiple of 16, at most 256)
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smQ = base;                                   // [MAX_KB][QG rows] query K blocks
+  uint8_t* smX = base + Q_BYTES;                         // [E_STAGES] row-tile K blocks (TMA)
+  float* smL = (float*)(smX + E_STAGES * KBLK_BYTES);    // [EPI_WARPS][64] range thresholds L
+  float4* smC = (float4*)(smL + EPI_WARPS * 64);         // [QG]: |q|^2, ru(c1 |q|), thr, slot
+  uint64_t* bars = (uint64_t*)(smC + QG);
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * E_STAGES + 4);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + E_STAGES),
+                 b_accf = smem_u32(bars + 2 * E_STAGES), b_acce = smem_u32(bars + 2 * E_STAGES + 2);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < E_STAGES; ++s) {
+      mbar_init(b_full + 8 * s, 1);
+      mbar_init(b_empty + 8 * s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(b_accf + 8 * a, 1);
+      mbar_init(b_acce + 8 * a, EPI_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the group's queries, K block kb holding query r's 16-byte chunk j at
+  // kb * QG * 128 + r * 128 + 16 * (j ^ (r mod 8)) (the 128-byte swizzle of the descriptors)
+  {
+    const int nkb = P.nkb;
+    for (int e = threadIdx.x; e < nkb * QG * 8; e += blockDim.x) {
+      const int j = e & 7, r = (e >> 3) & (QG - 1), kb = e >> 11;
+      if (r >= ncols) continue;
+      const uint4 v = *reinterpret_cast<const uint4*>(P.qbf + (int64_t)(gq0 + r) * (P.len / 2) + kb * (BKE / 2) + j * 4);
+      *reinterpret_cast<uint4*>(smQ + (size_t)kb * QG * 128 + r * 128 + ((j ^ (r & 7)) << 4)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+    for (int q = threadIdx.x; q < QG; q += blockDim.x) {
+      float4 c = make_float4(0.f, 0.f, -1.f, 0.f);  // no row passes thr = -1
+      if (q < nq) {
+        const float2 qq = P.qnorm[gq0 + q];
+        const int slot = P.qslot[gq0 + q];
+        c = make_float4(qq.x, __fmul_ru(P.c1, qq.y), __uint_as_float(*(volatile uint32_t*)(P.thr + P.q0 + slot)),
+                        __int_as_float(slot));
+      }
+      smC[q] = c;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const int64_t ntiles = (P.n + BN - 1) / BN;
+  const int64_t nranges = (P.n + RT - 1) / RT;
+  const int64_t tfirst = rank, tstride = cpg;
+  const uint64_t deadline = globaltimer() + P.wait_ns;
+  const int nkb = P.nkb;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer: one stage per (row tile, K block)
+      int i = 0;
+      for (int64_t t = tfirst; t < ntiles && !*abort_flag; t += tstride) {
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % E_STAGES;
+          const uint32_t ph = (uint32_t)((i / E_STAGES) & 1);
+          if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, deadline)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(b_full + 8 * s, (uint32_t)KBLK_BYTES);
+          tma_load_2d(smem_u32(smX + (size_t)s * KBLK_BYTES), &tmX, kb * BKE, (int)(t * BN), b_full + 8 * s);
+        }
+      }
+      const int issued = i;
+      for (int j = (issued > E_STAGES ? issued - E_STAGES : 0); j < issued; ++j)
+        if (!mbar_wait_drain(b_full + 8 * (j % E_STAGES), (uint32_t)((j / E_STAGES) & 1), deadline + kDrainNs))
+          *abort_flag = 1;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer: per stage, 4 MMAs of 128 rows x ncols queries x 16
+      const uint32_t idesc = idesc_bf16(BN, ncols);
+      bool ok = true;
+      int i = 0, j = 0;
+      for (int64_t t = tfirst; ok && t < ntiles; t += tstride, ++j) {
+        const int ab = j & 1;
+        const uint32_t aph = (uint32_t)((j >> 1) & 1);
+        if (!mbar_wait(b_acce + 8 * ab, aph ^ 1u, abort_flag, deadline)) {
+          ok = false;
+          break;
+        }
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * QG);
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % E_STAGES;
+          const uint32_t ph = (uint32_t)((i / E_STAGES) & 1);
+          if (!mbar_wait(b_full + 8 * s, ph, abort_flag, deadline)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smX + (size_t)s * KBLK_BYTES);
+          const uint32_t b0 = smem_u32(smQ + (size_t)kb * QG * 128);
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                hit |= (__fmaf_rd(-2.0f, __uint_as_float(v[jj]), rng.x) <= R ? 1u : 0u) << jj;
+          for (int ks = 0; ks < 4; ++ks)
+            umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
+                      (kb | ks) ? 1u : 0u);
+          umma_commit(b_empty + 8 * s);
+        }
+        if (!ok) break;
+        umma_commit(b_accf + 8 * ab);
+      }
+      if (!ok) *abort_flag = 1;
+      if (i > 0 && !mbar_wait_drain(b_empty + 8 * ((i - 1) % E_STAGES), (uint32_t)(((i - 1) / E_STAGES) & 1),
+                                    deadline + kDrainNs))
+        *abort_flag = 1;
+    }
+  } else {  // ---- epilogue: warps 2..17; TMEM lane quadrant warp % 4, query quarter (warp - 2) / 4
+    const int qd = warp & 3;
+    const int we = warp - 2;
+    const int cq = we >> 2;
+    const bool on = cq * 64 < ncols;  // warp-uniform: this quarter holds queries
+    float* Lw = smL + we * 64;
+    // this lane's two queries for the range thresholds
+    const float4 ca = smC[cq * 64 + lane], cb = smC[cq * 64 + 32 + lane];
+    const bool va = cq * 64 + lane < nq, vb = cq * 64 + 32 + lane < nq;
+    auto range_l = [&](const float4& c, const float4& rng) {
+      const float Mmax = __fmaf_ru(c.y, rng.z, __fmul_ru(P.c2, __fadd_ru(c.x, rng.y)));
+      const float R = __fsub_ru(__fadd_ru(c.z, Mmax), c.x);
+      return __fmul_rd(__fsub_rd(rng.x, next_up(R)), 0.5f);
+    };
+    auto load_range = [&](int64_t t) {
+      const int64_t r = 2 * t + (qd >> 1);
+      return (t < ntiles && r < nranges) ? P.xtile[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto load_norm = [&](int64_t t) {
+      const int64_t row = t * BN + qd * 32 + lane;
+      return (t < ntiles && row < P.n) ? P.xnorm[row] : make_float2(0.f, 0.f);
+    };
+    float4 rng1 = load_range(tfirst), rng2 = load_range(tfirst + tstride);
+    float2 xn1 = load_norm(tfirst);
+    int j = 0;
+    for (int64_t t = tfirst; t < ntiles; t += tstride, ++j) {
+      const float4 rng = rng1;
+      rng1 = rng2;
+      rng2 = load_range(t + 2 * tstride);
+      const float2 xx = xn1;
+      xn1 = load_norm(t + tstride);
+      const int64_t row = t * BN + qd * 32 + lane;
+      const bool row_ok = row < P.n;
+      if (on) {
+        __syncwarp();
+        Lw[lane] = va ? range_l(ca, rng) : CUDART_INF_F;
+        Lw[32 + lane] = vb ? range_l(cb, rng) : CUDART_INF_F;
+        __syncwarp();
+      }
+      const int ab = j & 1;
+      const uint32_t aph = (uint32_t)((j >> 1) & 1);
+      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (on) {
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          const int col0 = cq * 64 + ch * 32;
+          if (col0 >= ncols) break;
+          uint32_t v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * QG + col0), v);
+          const float4* L4 = reinterpret_cast<const float4*>(Lw + ch * 32);
+          bool any = false;
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 l = L4[c4];
+            any |= (__uint_as_float(v[4 * c4]) >= l.x) | (__uint_as_float(v[4 * c4 + 1]) >= l.y) |
+                   (__uint_as_float(v[4 * c4 + 2]) >= l.z) | (__uint_as_float(v[4 * c4 + 3]) >= l.w);
+          }
+          if (any && row_ok) {  // rare: the pairs that pass, each with the row's own interval
+            uint32_t hit = 0u;
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4) {
+              const float4 l = L4[c4];
+              hit |= (__uint_as_float(v[4 * c4]) >= l.x ? 1u : 0u) << (4 * c4);
+              hit |= (__uint_as_float(v[4 * c4 + 1]) >= l.y ? 1u : 0u) << (4 * c4 + 1);
+              hit |= (__uint_as_float(v[4 * c4 + 2]) >= l.z ? 1u : 0u) << (4 * c4 + 2);
+              hit |= (__uint_as_float(v[4 * c4 + 3]) >= l.w ? 1u : 0u) << (4 * c4 + 3);
             }
-            hit = valid ? (hit & row_mask) : 0u;
-            while (hit) {  // rare: the row's own interval, then emit
+            while (hit) {
               const int jj = __ffs(hit) - 1;
               hit &= hit - 1u;
               uint32_t dv = 0u;
 #pragma unroll
               for (int q2 = 0; q2 < 32; ++q2) dv = (q2 == jj) ? v[q2] : dv;
-              const float2 xx = P.xnorm[row0 + jj];
-              const float d2 = fmaf(-2.0f, __uint_as_float(dv), qn + xx.x);
-              const float M = __fmaf_ru(c1q, xx.y, __fmul_ru(P.c2, __fadd_ru(qn, xx.x)));
+              const float4 qc = smC[col0 + jj];
+              const float d2 = fmaf(-2.0f, __uint_as_float(dv), qc.x + xx.x);
+              const float M = __fmaf_ru(qc.y, xx.y, __fmul_ru(P.c2, __fadd_ru(qc.x, xx.x)));
               const float x = fmaxf(__fsub_rd(d2, M), 0.f);  // lower end
-              if (x <= thr_q) {
+              if (x <= qc.z) {
+                const int slot = __float_as_int(qc.w);
                 const uint32_t p = atomicAdd(P.count + slot, 1u);
                 if ((int64_t)p < P.cap) {
-                  P.rows[(int64_t)slot * P.cap + p] = (uint32_t)(row0 + jj);
+                  P.rows[(int64_t)slot * P.cap + p] = (uint32_t)row;
                   P.lb[(int64_t)slot * P.cap + p] = x;
                 } else {
                   atomicOr(P.overflow, DEV_CAND_OVERFLOW);
@@ -428,7 +674,6 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(b_acce + 8 * ab);
     }
-    if (PHASE == 1 && valid && kth < CUDART_INF_F) atomicMin(thr_ptr, __float_as_uint(__fmul_ru(kth, P.cg)));
   }
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) atomicOr(P.status, DEV_TIMEOUT);
@@ -693,8 +938,8 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   note_launches(2);
   PARIS_CUDA(cudaGetLastError());
   // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
-  PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
-  PARIS_CUDA(cudaFuncSetAttribute(dense_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
+  PARIS_CUDA(cudaFuncSetAttribute(bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
+  PARIS_CUDA(cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMIT_SMEM));
   DenseParams P;
   P.wait_ns = wait_limit_ns();
   P.n = idx->n;
@@ -719,15 +964,16 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   P.status = qs.status;
   P.overflow = overflow;
   const int64_t ntiles = (idx->n + BN - 1) / BN;
-  const int grid = (int)std::min<int64_t>(ntiles, sm_count_dense());
+  const int grid = (int)std::max<int64_t>(std::min<int64_t>(ntiles, sm_count_dense()), GROUPS);
   const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;
+  const int groups = (int)((tiles + QTILES - 1) / QTILES);
   for (int phase = 1; phase <= 2; ++phase) {
-    for (int t = 0; t < (int)tiles; t += QTILES) {
-      P.qtile = t;
+    for (int g0 = 0; g0 < groups; g0 += GROUPS) {
+      P.group0 = g0;
       if (phase == 1)
-        dense_kernel<1><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
+        bound_kernel<<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
       else
-        dense_kernel<2><<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
+        emit_kernel<<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);
       note_launches(1);
       PARIS_CUDA(cudaGetLastError());
     }

@@ -733,14 +733,16 @@ __global__ void kth_from_bsf_kernel(const unsigned long long* __restrict__ bsf, 
   if (j < qc) kth[j] = (uint32_t)(bsf[q0 + j] >> 32);
 }
 
-// Rows whose fp32 distance cannot be separated from the k-th best by the fp32 error bound.
+// Rows whose fp32 distance cannot be separated from the k-th best by the fp32 error bound. An
+// overflowed list holds an arbitrary subset of its candidates (possibly fewer than k finite
+// distances): its query is screened and selected again, so it names no contenders here.
 __global__ void contenders_kernel(const float* __restrict__ F, const uint32_t* __restrict__ rows,
                                   const uint32_t* __restrict__ count, int64_t cap,
                                   const uint32_t* __restrict__ kth, float cg, uint32_t* __restrict__ cont_count,
                                   uint32_t* __restrict__ cont_rows, uint32_t* __restrict__ status) {
   const int j = blockIdx.y;
-  int64_t m = count[j];
-  if (m > cap) m = cap;
+  const int64_t m = count[j];
+  if (m > cap) return;
   const float Tc = __fmul_ru(__uint_as_float(kth[j]), cg);
   const float* f = F + (int64_t)j * cap;
   const uint32_t* r = rows + (int64_t)j * cap;
