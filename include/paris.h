@@ -118,6 +118,7 @@ enum {
 enum {
   PARIS_SEED_DESCENT = 0, /* the approximate search visits the query key's leaf (Sec. 3.3) */
   PARIS_SEED_LEARNED = 1, /* ... and the leaves of the attached model's top-r key buckets */
+  PARIS_SEED_ADAPTIVE = 2, /* the query's leaf of the adaptive-split tree (paris_build_adaptive_leaves) */
 };
 
 typedef struct paris_query_opts {
@@ -298,6 +299,34 @@ paris_status paris_encode(const float* series, int64_t n, int32_t len, int32_t w
  * (out_leaf still reports the query key's own leaf). */
 paris_status paris_approx_search_ex(const paris_index* idx, const float* queries, int64_t nq, int32_t k,
                                     int32_t seed_mode, int64_t* out_leaf, float* out_seed_sq, void* stream);
+
+/* Adaptive-split leaves (Sec. 2.2, ADS+): the tree in which a leaf holding more than the
+ * index's leaf capacity splits into two children by adding one bit to the segment whose next
+ * bit divides its series most evenly (smallest |n0 - n1|, lowest segment on ties; a split that
+ * leaves one side empty is still made; a node whose segments all have every bit stays a leaf of
+ * any size). Root children are the words of first bits of the w segments. Built level by level
+ * on the device from the index's summaries (deterministic: the same tree on every run); the
+ * series of each side keep their order, bit 0 first, so the leaves tile the "leaf order" of the
+ * series depth first, starting from the index order. Needs 5 x 4 B per series of scratch during
+ * the build and keeps 8 B per series plus 32 B per node. Rebuilding replaces the tree.
+ * PARIS_SEED_ADAPTIVE then seeds the best-so-far from the query's leaf of this tree: its root
+ * child is that of the query's first-bit word (an empty one is replaced by the next non-empty
+ * word, else the last one), then its bits choose the children; an empty leaf is replaced by the
+ * leaf holding the series at the empty leaf's start; a leaf with fewer than k series becomes the
+ * k series of the leaf order from its start (moved left to fit), and one with more than
+ * max(leaf capacity, k) series is cut to its first ones. With this seed, out_leaf of
+ * paris_approx_search_ex reports leaf-order positions. Answers never depend on the seed. */
+paris_status paris_build_adaptive_leaves(paris_index* idx, void* stream);
+/* Size of the adaptive-split tree (any pointer may be NULL); EINVAL when none was built. */
+paris_status paris_adaptive_leaves_info(const paris_index* idx, int64_t* n_nodes, int64_t* n_leaves,
+                                        int32_t* depth);
+/* Host copies of the tree: rows_host [n] (series row at each leaf-order position) and nodes_host
+ * [n_nodes][5] int64 (first leaf-order position, number of series, split segment or -1 for a
+ * leaf, index of the bit-0 child -- the bit-1 child follows it -- or -1, and the bits fixed per
+ * segment, 4 bits each, segment i at bits 4i..4i+3). Root children come first, in increasing
+ * first-bit word order. Either pointer may be NULL. */
+paris_status paris_adaptive_leaves_export(const paris_index* idx, uint32_t* rows_host, int64_t* nodes_host,
+                                          void* stream);
 
 /* Approximate search alone (Sec. 3.3): per query, the sorted-position range [lo, hi) of its
  * leaf (device or host [nq][2] int64) and the seed -- the k-th smallest fp32 squared distance

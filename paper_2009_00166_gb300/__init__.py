@@ -15,12 +15,16 @@ from .binding import (  # noqa: F401
     PARIS_REFINE_MIXED,
     PARIS_SEED_DESCENT,
     PARIS_SEED_LEARNED,
+    PARIS_SEED_ADAPTIVE,
     SeedModel,
     ParisError,
     ParisIndex,
     QueryStats,
     lib,
     paris_approx_search,
+    paris_adaptive_leaves_export,
+    paris_adaptive_leaves_info,
+    paris_build_adaptive_leaves,
     paris_attach_seed_model,
     paris_breakpoints,
     paris_build,

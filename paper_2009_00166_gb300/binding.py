@@ -14,6 +14,7 @@ PARIS_REFINE_FP32 = 0
 PARIS_REFINE_MIXED = 1
 PARIS_SEED_DESCENT = 0
 PARIS_SEED_LEARNED = 1
+PARIS_SEED_ADAPTIVE = 2
 SEED_MODEL_PARAMS = 1122816
 SEED_MODEL_SHAPES = [("W1", (256, 16)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (4096, 256)),
                      ("b3", (4096,))]
@@ -104,6 +105,9 @@ def lib():
             "paris_export_sax": ([VP, P, VP], I32),
             "paris_encode": ([P, I64, I32, I32, I32, P, P, P, VP], I32),
             "paris_export_order": ([VP, P, P, VP], I32),
+            "paris_build_adaptive_leaves": ([VP, VP], I32),
+            "paris_adaptive_leaves_info": ([VP, C.POINTER(I64), C.POINTER(I64), C.POINTER(I32)], I32),
+            "paris_adaptive_leaves_export": ([VP, P, P, VP], I32),
             "paris_approx_search": ([VP, P, I64, I32, P, P, VP], I32),
             "paris_lb_scan": ([VP, P, F32, P, P, I64, C.POINTER(I64), VP], I32),
             "paris_lb_scan_noalloc": ([VP, P, I64, P, P, P, I64, P, VP], I32),
@@ -371,6 +375,27 @@ def paris_export_order(index: ParisIndex):
     rows = np.empty(index.n, np.uint32)
     _check(lib().paris_export_order(index.handle, keys.ctypes.data, rows.ctypes.data, _stream(None)))
     return keys, rows.astype(np.int64)
+
+
+def paris_build_adaptive_leaves(index: ParisIndex, stream=None):
+    _check(lib().paris_build_adaptive_leaves(index.handle, _stream(stream)))
+
+
+def paris_adaptive_leaves_info(index: ParisIndex) -> dict:
+    nn, nl, d = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().paris_adaptive_leaves_info(index.handle, C.byref(nn), C.byref(nl), C.byref(d)))
+    return {"nodes": nn.value, "leaves": nl.value, "depth": d.value}
+
+
+def paris_adaptive_leaves_export(index: ParisIndex):
+    """(rows uint32 [n]: series row per leaf-order position, nodes int64 [n_nodes][5]:
+    start, count, split segment or -1, bit-0 child or -1, bits per segment packed 4 bits each)."""
+    import numpy as np
+    info = paris_adaptive_leaves_info(index)
+    rows = np.empty(index.n, np.uint32)
+    nodes = np.empty((info["nodes"], 5), np.int64)
+    _check(lib().paris_adaptive_leaves_export(index.handle, rows.ctypes.data, nodes.ctypes.data, _stream(None)))
+    return rows, nodes
 
 
 def paris_encode(series, w: int = 16, card: int = 256, want_paa: bool = False, stream=None):

@@ -166,6 +166,7 @@ void release_index(paris_index* idx) {
   dev_free(idx->beta_keys, (size_t)(idx->card - 1) * 8, st);
   dev_free(idx->beta_ext, (size_t)(idx->card + 1) * 8, st);
   release_shadow(idx);
+  release_adaptive(idx);
   delete idx;
 }
 
@@ -683,7 +684,10 @@ static paris_status check_query_opts(const paris_index* idx, const paris_query_o
   if (o.reserved[0]) return fail(PARIS_EINVAL, "paris_query_opts.reserved must be zero");
   if (o.private_bsf != 0 && o.private_bsf != 1) return fail(PARIS_EINVAL, "private_bsf must be 0 or 1");
   if (o.no_leaf_pruning != 0 && o.no_leaf_pruning != 1) return fail(PARIS_EINVAL, "no_leaf_pruning must be 0 or 1");
-  if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
+  if (o.seed != PARIS_SEED_DESCENT && o.seed != PARIS_SEED_LEARNED && o.seed != PARIS_SEED_ADAPTIVE)
+    return fail(PARIS_EINVAL, "unknown seed mode");
+  if (o.seed == PARIS_SEED_ADAPTIVE && !idx->ad_nodes)
+    return fail(PARIS_EINVAL, "PARIS_SEED_ADAPTIVE needs paris_build_adaptive_leaves first");
   if (o.seed == PARIS_SEED_LEARNED && !idx->seed_model)
     return fail(PARIS_EINVAL, "PARIS_SEED_LEARNED needs a model attached with paris_attach_seed_model");
   if (o.precision != PARIS_REFINE_FP32 && o.precision != PARIS_REFINE_MIXED)
@@ -845,7 +849,7 @@ struct KnnJob {
     timer.begin(1);
     if (o.seed == PARIS_SEED_LEARNED)
       PARIS_TRY(learned_keys(idx, idx->seed_model, idx->seed_r, qs, lkeys.as<uint64_t>(), st));
-    PARIS_TRY(launch_descent(idx, qs, st));
+    PARIS_TRY(launch_descent(idx, qs, st, o.seed == PARIS_SEED_ADAPTIVE));
     timer.end(1);
     return PARIS_OK;
   }
@@ -1422,8 +1426,10 @@ paris_status paris_approx_search_ex(const paris_index* idx, const float* queries
                                     int32_t seed_mode, int64_t* out_leaf, float* out_seed_sq, void* stream) {
   clear_error();
   PARIS_TRY(check_query_args(idx, queries, nq, k));
-  if (seed_mode != PARIS_SEED_DESCENT && seed_mode != PARIS_SEED_LEARNED) return fail(PARIS_EINVAL, "unknown seed mode");
+  if (seed_mode != PARIS_SEED_DESCENT && seed_mode != PARIS_SEED_LEARNED && seed_mode != PARIS_SEED_ADAPTIVE)
+    return fail(PARIS_EINVAL, "unknown seed mode");
   if (seed_mode == PARIS_SEED_LEARNED && !idx->seed_model) return fail(PARIS_EINVAL, "no seed model attached");
+  if (seed_mode == PARIS_SEED_ADAPTIVE && !idx->ad_nodes) return fail(PARIS_EINVAL, "no adaptive-split leaves built");
   if (nq == 0) return PARIS_OK;
   if (!out_leaf) return fail(PARIS_EINVAL, "out_leaf is NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1442,12 +1448,36 @@ paris_status paris_approx_search_ex(const paris_index* idx, const float* queries
     qs.keys = lkeys.as<uint64_t>();
     qs.nk = idx->seed_r + 1;
   }
-  PARIS_TRY(launch_descent(idx, qs, st));
+  PARIS_TRY(launch_descent(idx, qs, st, seed_mode == PARIS_SEED_ADAPTIVE));
   PARIS_CUDA(cudaMemcpyAsync(sl.dev, qs.leaf, (size_t)nq * 16, cudaMemcpyDeviceToDevice, st));
   if (out_seed_sq) PARIS_CUDA(cudaMemcpyAsync(ss.dev, qs.seed, (size_t)nq * 4, cudaMemcpyDeviceToDevice, st));
   PARIS_TRY(sl.finish(st));
   PARIS_TRY(ss.finish(st));
   return check_status_word(qs.status, st, "paris_approx_search");
+}
+
+paris_status paris_build_adaptive_leaves(paris_index* idx, void* stream) {
+  clear_error();
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  return build_adaptive(idx, (cudaStream_t)stream);
+}
+
+paris_status paris_adaptive_leaves_info(const paris_index* idx, int64_t* n_nodes, int64_t* n_leaves, int32_t* depth) {
+  clear_error();
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  if (!idx->ad_nodes) return fail(PARIS_EINVAL, "no adaptive-split leaves built");
+  if (n_nodes) *n_nodes = idx->ad_nnodes;
+  if (n_leaves) *n_leaves = idx->ad_leaves;
+  if (depth) *depth = idx->ad_depth;
+  return PARIS_OK;
+}
+
+paris_status paris_adaptive_leaves_export(const paris_index* idx, uint32_t* rows_host, int64_t* nodes_host,
+                                          void* stream) {
+  clear_error();
+  if (!idx) return fail(PARIS_EINVAL, "index is NULL");
+  if (!idx->ad_nodes) return fail(PARIS_EINVAL, "no adaptive-split leaves built");
+  return export_adaptive(idx, rows_host, nodes_host, (cudaStream_t)stream);
 }
 
 paris_status paris_leaf_scan(const paris_index* idx, const float* query, float threshold_sq, uint32_t* out_bits,

@@ -34,6 +34,14 @@ struct paris_index {
   float2* xnorm = nullptr;      // device [n rounded up to 64]: (|x|^2, |x|) in fp32, zero past n
   void* xtile = nullptr;        // device float4 per 64-row tile: (min |x|^2, max |x|^2, max |x|, 0)
   void* shadow_map = nullptr;   // host copy of the TMA descriptor of the shadow (CUtensorMap)
+  // adaptive-split leaves (paris_build_adaptive_leaves): tree nodes, root-child table, and per
+  // leaf-order position the series row and the leaf holding it
+  void* ad_nodes = nullptr;         // device AdNode [ad_cap]
+  int64_t ad_nnodes = 0, ad_cap = 0, ad_leaves = 0;
+  int32_t ad_depth = 0;
+  int32_t* ad_root = nullptr;       // device [2^w]: node of each first-bit word (nearest non-empty)
+  uint32_t* ad_rows = nullptr;      // device [n]
+  int32_t* ad_leaf_of = nullptr;    // device [n]
   // learned approximate-search proposal (borrowed; see paris_attach_seed_model)
   const paris_seed_model* seed_model = nullptr;
   int seed_r = 0;
@@ -100,6 +108,10 @@ paris_status launch_encode(const float* series, int64_t n, const RowShape& sh, i
 paris_status launch_unrotate_sax(const uint8_t* sax_rot, int64_t n, int w, uint8_t* out,
                                  cudaStream_t st);
 paris_status radix_sort_index(uint64_t* keys, uint32_t* rows, int64_t n, cudaStream_t st);
+// In-place exclusive prefix sum of m 32-bit counts (sums must fit in 32 bits).
+paris_status exclusive_scan(uint32_t* a, int64_t m, cudaStream_t st);
+// Frees the adaptive-split leaves of an index (NULL-safe fields).
+void release_adaptive(paris_index* idx);
 
 // Bound of the device-side waits of the pipelined kernels (paris_set_wait_limit), in ns.
 uint64_t wait_limit_ns();

@@ -205,14 +205,15 @@ __device__ __forceinline__ int smem_upper_bound(const uint64_t* a, int m, uint64
 // One CTA per query: for each of the query's nk keys (its own key first, then any learned
 // bucket keys), find the leaf of the fixed-order trie that holds that key's position (Sec. 3.3
 // approximate search); compute the distance to every series of the distinct leaves and seed the
-// best-so-far with the k-th smallest. The leaf range reported is the own key's.
+// best-so-far with the k-th smallest. The leaf range reported is the own key's. With leaf_in
+// (adaptive-split leaves, nk = 1) the leaf's range is given, in the order of rows_sorted.
 template <int ITERS>
 __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
     const float* __restrict__ series, int64_t n, int len, int vec, const uint64_t* __restrict__ keys,
     const uint32_t* __restrict__ rows_sorted, int leaf_cap, int k, const float* __restrict__ queries,
     const uint64_t* __restrict__ qkeys, int nk, int64_t* __restrict__ leaf_out, float* __restrict__ seed_out,
     uint32_t* __restrict__ thr, unsigned long long* __restrict__ bsf, float cg,
-    unsigned long long* __restrict__ counters) {
+    unsigned long long* __restrict__ counters, const int64_t* __restrict__ leaf_in) {
   extern __shared__ __align__(16) uint64_t s_mem[];
   const int Lp = max(leaf_cap, k);
   uint64_t* s_win = s_mem;               // [2 Lp + 1] keys of the window around a position
@@ -229,6 +230,11 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
   if (vec) qv.load(qp, len, lane);
   int filled = 0;
   for (int j = 0; j < nk; ++j) {
+    int64_t lo, hi;
+    if (leaf_in) {
+      lo = leaf_in[2 * q];
+      hi = leaf_in[2 * q + 1];
+    } else {
     const uint64_t x = qkeys[q * nk + j];
     int64_t pos0 = cta_lower_bound(keys, n, x, s_bounds);
     const bool clamped = pos0 >= n;
@@ -250,7 +256,6 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
     }
     __syncthreads();
     const int best = s_best;
-    int64_t lo, hi;
     if (best <= 64) {
       lo = s_lo[best];
       hi = s_hi[best];
@@ -263,6 +268,7 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
       int64_t start = clamped ? cta_lower_bound(keys, n, anchor, s_bounds) : pos;
       lo = start;
       hi = start + Lp;
+    }
     }
     if (t == 0) {
       int dup = 0;
@@ -922,8 +928,17 @@ static bool vec_ok(const paris_index* idx, const float* q) {
          ((uintptr_t)q % 16u) == 0u;
 }
 
-paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st) {
+paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st, bool adaptive) {
   if (qs.nq <= 0) return PARIS_OK;
+  const int64_t* leaf_in = nullptr;
+  const uint32_t* rows = idx->rows_sorted;
+  if (adaptive) {
+    if (!idx->ad_nodes) return fail(PARIS_EINVAL, "the index has no adaptive-split leaves");
+    if (qs.keys) return fail(PARIS_EINVAL, "adaptive-split leaves take the query's own key only");
+    PARIS_TRY(launch_adaptive_leaf(idx, qs, st));
+    leaf_in = qs.leaf;
+    rows = idx->ad_rows;
+  }
   const int Lp = max(idx->leaf_cap, qs.k);
   const int nk = qs.keys ? qs.nk : 1;
   int P2 = 1;
@@ -938,8 +953,8 @@ paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaSt
     PARIS_CUDA(cudaFuncSetAttribute(descent_kernel<IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)smem));                                                 \
     descent_kernel<IT><<<(unsigned)qs.nq, kDescentThreads, smem, st>>>(                          \
-        idx->series, idx->n, idx->len, vec, idx->keys_sorted, idx->rows_sorted, idx->leaf_cap, qs.k, \
-        qs.queries, qk, nk, qs.leaf, qs.seed, qs.thr, qs.bsf, qs.cg, qs.counters);               \
+        idx->series, idx->n, idx->len, vec, idx->keys_sorted, rows, idx->leaf_cap, qs.k,          \
+        qs.queries, qk, nk, qs.leaf, qs.seed, qs.thr, qs.bsf, qs.cg, qs.counters, leaf_in);      \
   } while (0)
   switch (it) {
     case 1: DESC(1); break;

@@ -69,7 +69,16 @@ struct ChunkState {
 };
 
 paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cudaStream_t st);
-paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st);
+// adaptive: the leaves of the adaptive-split tree (paris_build_adaptive_leaves) in place of the
+// fixed-order trie's.
+paris_status launch_descent(const paris_index* idx, const QueryState& qs, cudaStream_t st, bool adaptive = false);
+// Per query, the leaf-order range [lo, hi) of its adaptive-split leaf, into qs.leaf.
+paris_status launch_adaptive_leaf(const paris_index* idx, const QueryState& qs, cudaStream_t st);
+// Builds the adaptive-split tree of an index from its index-order summaries.
+paris_status build_adaptive(paris_index* idx, cudaStream_t st);
+// Host copies of the tree: series row per leaf-order position, and per node (start, count,
+// split segment or -1, bit-0 child or -1, bits per segment packed 4 bits each).
+paris_status export_adaptive(const paris_index* idx, uint32_t* rows_host, int64_t* nodes_host, cudaStream_t st);
 paris_status launch_lbscan(const paris_index* idx, const QueryState& qs, int64_t q, uint32_t* count,
                            uint32_t* rows, float* lb, int64_t cap, uint32_t* status, int stop_on_overflow,
                            cudaStream_t st);

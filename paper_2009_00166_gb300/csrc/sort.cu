@@ -187,6 +187,9 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(
   }
 }
 
+
+}  // namespace
+
 paris_status exclusive_scan(uint32_t* a, int64_t m, cudaStream_t st) {
   int64_t tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
   DevBuf sums;
@@ -198,8 +201,6 @@ paris_status exclusive_scan(uint32_t* a, int64_t m, cudaStream_t st) {
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;
 }
-
-}  // namespace
 
 paris_status radix_sort_index(uint64_t* keys, uint32_t* rows, int64_t n, cudaStream_t st) {
   if (n <= 1) {
