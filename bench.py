@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--clocks-csv", default="", help="keep the raw nvidia-smi clock samples of the timed region here")
     p.add_argument("--leaf-capacity", type=int, default=0, help="rows per approximate-search leaf (0: 2048)")
+    p.add_argument("--no-adaptive", action="store_true",
+                   help="skip the adaptive-split leaves comparison (seed from ADS+ adaptive leaves vs the fixed trie)")
     p.add_argument("--batch-n", type=int, default=50_000_000,
                    help="rows of the 4096-query batch workload reported beside (0: skip it)")
     p.add_argument("--multi-scale", type=float, default=1.0,
@@ -699,6 +701,39 @@ def main():
                                   "identical_answers": bool(torch.equal(gi, ref_i))}
         plan.free()
         idx.free()
+
+    # ---- beside it: the approximate search on adaptive-split ADS+ leaves (a leaf over capacity
+    # splits on its most balanced segment) against the fixed-order trie, on an index built once:
+    # tree build time and size, seed quality per sigma (seed distance over the true k-th
+    # distance), candidates, and queries/s of the headline form with either seed
+    if not args.no_adaptive:
+        aidx = P.paris_build_ex(X, 16, 256, bf16_shadow=precision == P.PARIS_REFINE_MIXED)
+        P.paris_build_adaptive_leaves(aidx)                           # warm-up build
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        P.paris_build_adaptive_leaves(aidx)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        arec = {"form": "ADS+ adaptive-split leaves vs the fixed-order trie (index built once; queries only)",
+                "tree_build_ms": a0.elapsed_time(a1), "tree": P.paris_adaptive_leaves_info(aidx)}
+        answers = {}
+        for name, sd in (("descent", P.PARIS_SEED_DESCENT), ("adaptive", P.PARIS_SEED_ADAPTIVE)):
+            _, seed_sq = P.paris_approx_search(aidx, Q, k, seed_mode=sd)
+            P.paris_exact_knn_ex(aidx, Q, k, mode=mode, precision=precision, seed=sd)
+            ms_, (ai_, ad_, ast_) = timed(lambda: P.paris_exact_knn_ex(aidx, Q, k, mode=mode, precision=precision,
+                                                                        seed=sd, want_stats=True), stream, 2)
+            answers[name] = ai_
+            ratio = (seed_sq.sqrt() / ad_[:, -1].clamp_min(1e-30)).cpu()
+            arec[name] = {"value": nq / (ms_ * 1e-3), "unit": "queries/s", "candidates_per_query":
+                          ast_["candidates"] / nq, "leaf_rows_per_query": ast_["leaf_rows"] / nq,
+                          "dense_queries": ast_["dense_queries"],
+                          "seed_over_true_by_sigma": [
+                              {"sigma": s_, "mean": float(ratio[i * args.per_sigma:(i + 1) * args.per_sigma].mean()),
+                               "median": float(ratio[i * args.per_sigma:(i + 1) * args.per_sigma].median())}
+                              for i, s_ in enumerate(SIGMAS)]}
+        arec["identical_answers"] = bool(torch.equal(answers["descent"], answers["adaptive"]))
+        beside["adaptive_leaves"] = arec
+        aidx.free()
 
     # ---- beside it: the 4096-query batch workload and the three-collection call
     batch_wl = multi_wl = None
