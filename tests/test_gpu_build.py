@@ -19,6 +19,16 @@ def encode_gpu(x, w, card):
     return sax.cpu().numpy(), key.cpu().numpy().view(np.uint64), paa.cpu().numpy()
 
 
+def encode_gpu_symbols(x, w, card):
+    """paris_encode without the PAA output: the symbols may then be decided from an fp32 sum
+    with a proven error bound (the exact sum only near a breakpoint), as in the index build."""
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    sax, key = P.paris_encode(torch.from_numpy(np.ascontiguousarray(x)).to(dev), w, card)
+    torch.cuda.synchronize()
+    return sax.cpu().numpy(), key.cpu().numpy().view(np.uint64)
+
+
 def check_encode(x, w, card):
     sax, key, paa = encode_gpu(x, w, card)
     want_paa = isax.paa(x, w)
@@ -26,6 +36,9 @@ def check_encode(x, w, card):
     want_sax = isax.symbols(want_paa, card)
     assert np.array_equal(sax, want_sax)
     assert np.array_equal(key, isax.key64(want_sax, card))
+    sax2, key2 = encode_gpu_symbols(x, w, card)
+    assert np.array_equal(sax2, want_sax)
+    assert np.array_equal(key2, key)
 
 
 def test_encode_random_walk_100k():
@@ -53,7 +66,7 @@ def test_encode_tiny_and_exact_values():
     check_encode(x, 16, 256)
 
 
-@pytest.mark.parametrize("length", [512, 1024, 2048, 4096])
+@pytest.mark.parametrize("length", [256, 512, 1024, 2048, 4096])
 def test_encode_planted_exactness(length):
     """Segments built to break a summation that drops low bits (w = 16, so s = len / 16 values
     per segment): the wide-span pattern 1.9999999 / 2^-15+2^-18-2^-38 in four orders and signs,
@@ -86,8 +99,29 @@ def test_encode_planted_exactness(length):
     assert r <= x.shape[0]
     check_encode(x, 16, 256)
     sax, _, _ = encode_gpu(x, 16, 256)
+    sax2, _ = encode_gpu_symbols(x, 16, 256)
     for row, seg, sym in near:
-        assert sax[row, seg] == sym
+        assert sax[row, seg] == sym and sax2[row, seg] == sym
+
+
+@pytest.mark.parametrize("length", [64, 128, 256])
+def test_encode_symbols_at_breakpoints(length):
+    """Segments whose every value is the fp32 value nearest to a breakpoint, or the fp32 value
+    just above or just below it (the mean is then that value exactly): the segment mean lies
+    within one fp32 step of the breakpoint, inside any error interval of an fp32 sum, so the
+    symbol must come from the exact comparison (upper region on a tie)."""
+    s = length // 16
+    beta = isax.breakpoints(256)
+    x = rw(3 * 255 // 16 + 3, length, 70 + length)
+    f32 = np.float32
+    k = 0
+    for j in range(255):
+        c = f32(beta[j])
+        for v in (c, np.nextafter(c, f32(np.inf), dtype=f32), np.nextafter(c, f32(-np.inf), dtype=f32)):
+            r, seg = divmod(k, 16)
+            x[r, seg * s:(seg + 1) * s] = v
+            k += 1
+    check_encode(x, 16, 256)
 
 
 def test_encode_rejects_nonfinite():
