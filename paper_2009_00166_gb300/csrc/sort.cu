@@ -8,7 +8,7 @@ namespace paris {
 namespace {
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_IPT = 16;
+constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int SCAN_THREADS = 1024;
@@ -112,12 +112,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_add(uint32_t* __restrict__ 
 struct ScatterSmem {
   uint64_t key[RS_TILE];
   uint32_t row[RS_TILE];
-  uint32_t warp_cnt[RS_WARPS][256];
-  uint32_t run[256];
+  uint32_t wcnt[RS_WARPS][256];  // per-warp digit counts, then each warp's offset within its digit
   uint32_t start[256];
   uint32_t s_warp[32];
 };
 
+// One stable pass: each warp ranks a contiguous run of RS_IPT x 32 keys of the block's tile by
+// digit (match_any groups the lanes of equal digit, a warp-private running count orders the
+// rounds), one block-wide scan turns the per-warp counts into offsets, the tile is reordered by
+// digit in shared memory and written out in runs of equal digit.
 __global__ void __launch_bounds__(RS_THREADS) radix_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ rin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ rout, int64_t n, int shift, const uint32_t* __restrict__ offs, int nblocks) {
@@ -125,68 +128,63 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(
   ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t wbase = base + (int64_t)warp * (RS_IPT * 32);
   const uint32_t lt_mask = (1u << lane) - 1u;
-  S.run[t] = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) S.wcnt[warp][lane * 8 + q] = 0u;
   uint64_t key[RS_IPT];
   uint32_t row[RS_IPT];
   uint32_t rank[RS_IPT];
 #pragma unroll
   for (int j = 0; j < RS_IPT; ++j) {
-    int64_t i = base + j * RS_THREADS + t;
-    bool valid = i < n;
+    const int64_t i = wbase + j * 32 + lane;
+    const bool valid = i < n;
     key[j] = valid ? kin[i] : 0ull;
     row[j] = valid ? (rin ? rin[i] : (uint32_t)i) : 0u;
   }
-  __syncthreads();
-#pragma unroll 1
+  __syncwarp();
+#pragma unroll
   for (int j = 0; j < RS_IPT; ++j) {
-    int64_t i = base + j * RS_THREADS + t;
-    uint32_t d = i < n ? ((uint32_t)(key[j] >> shift) & 255u) : 256u;
-    uint32_t peers = __match_any_sync(PARIS_FULL_MASK, d);
-    uint32_t wrank = __popc(peers & lt_mask);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) S.warp_cnt[warp][lane * 8 + q] = 0u;
+    const int64_t i = wbase + j * 32 + lane;
+    const uint32_t d = i < n ? ((uint32_t)(key[j] >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(PARIS_FULL_MASK, d);
+    const uint32_t before = d < 256u ? S.wcnt[warp][d] : 0u;
+    rank[j] = before + __popc(peers & lt_mask);
     __syncwarp();
-    if (d < 256u && lane == __ffs(peers) - 1) S.warp_cnt[warp][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t off = S.run[t];
+    if (d < 256u && lane == __ffs(peers) - 1) S.wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  uint32_t tot = 0;
 #pragma unroll
-      for (int w2 = 0; w2 < RS_WARPS; ++w2) {
-        uint32_t c = S.warp_cnt[w2][t];
-        S.warp_cnt[w2][t] = off;
-        off += c;
-      }
-      S.run[t] = off;
-    }
-    __syncthreads();
-    rank[j] = d < 256u ? S.warp_cnt[warp][d] + wrank : 0u;
-    __syncthreads();
+  for (int w2 = 0; w2 < RS_WARPS; ++w2) {
+    const uint32_t c = S.wcnt[w2][t];
+    S.wcnt[w2][t] = tot;
+    tot += c;
   }
   uint32_t excl;
-  uint32_t total = block_exclusive_scan(S.run[t], excl, S.s_warp);
+  const uint32_t total = block_exclusive_scan(tot, excl, S.s_warp);
   S.start[t] = excl;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < RS_IPT; ++j) {
-    int64_t i = base + j * RS_THREADS + t;
+    const int64_t i = wbase + j * 32 + lane;
     if (i < n) {
-      uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
-      uint32_t p = S.start[d] + rank[j];
+      const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
+      const uint32_t p = S.start[d] + S.wcnt[warp][d] + rank[j];
       S.key[p] = key[j];
       S.row[p] = row[j];
     }
   }
   __syncthreads();
   for (uint32_t p = t; p < total; p += RS_THREADS) {
-    uint64_t k = S.key[p];
-    uint32_t d = (uint32_t)(k >> shift) & 255u;
-    uint32_t o = offs[(int64_t)d * nblocks + blockIdx.x] + (p - S.start[d]);
+    const uint64_t k = S.key[p];
+    const uint32_t d = (uint32_t)(k >> shift) & 255u;
+    const uint32_t o = offs[(int64_t)d * nblocks + blockIdx.x] + (p - S.start[d]);
     kout[o] = k;
     rout[o] = S.row[p];
   }
 }
-
 
 }  // namespace
 
