@@ -79,6 +79,28 @@ __device__ __forceinline__ float warp_sq_dist_vec(const float* __restrict__ x, c
   return tot > abandon ? CUDART_INF_F : tot;
 }
 
+// fp32 squared distances of R rows to the warp's query (no abandoning): all R rows' loads are
+// issued before the first sum, so a warp keeps R rows in flight.
+template <int ITERS, int R>
+__device__ __forceinline__ void warp_sq_dist_rows(const float* const (&x)[R], const QVec<ITERS>& q, int len,
+                                                  int lane, float (&out)[R]) {
+  float4 xv[R][ITERS];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t) {
+      const int i4 = lane + 32 * t;
+      xv[r][t] = (4 * i4 < len) ? __ldcs(reinterpret_cast<const float4*>(x[r]) + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < ITERS; ++t) acc = sq4(xv[r][t], q.v[t], acc);
+    out[r] = warp_sum(acc);
+  }
+}
+
 __device__ __forceinline__ float warp_sq_dist_scalar(const float* __restrict__ x, const float* __restrict__ q,
                                                      int len, int lane, float abandon) {
   float acc = 0.f;
@@ -286,12 +308,32 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(
     __syncthreads();
     if (!s_dup) {
       const int m = (int)(hi - lo);
-      for (int i = warp; i < m; i += blockDim.x >> 5) {
-        uint32_t row = rows_sorted[lo + i];
-        const float* xr = series + (int64_t)row * len;
-        float F = vec ? warp_sq_dist_vec<ITERS>(xr, qv, len, lane, CUDART_INF_F)
-                      : warp_sq_dist_scalar(xr, qp, len, lane, CUDART_INF_F);
-        if (lane == 0) s_buf[filled + i] = ((unsigned long long)__float_as_uint(F) << 32) | row;
+      const int nw = blockDim.x >> 5;
+      if (vec) {
+        // RR rows per warp and round, their loads in flight together
+        constexpr int RR = ITERS >= 8 ? 1 : 8 / ITERS;
+        for (int i0 = warp * RR; i0 < m; i0 += nw * RR) {
+          uint32_t rw[RR];
+          const float* xr[RR];
+#pragma unroll
+          for (int r = 0; r < RR; ++r) {
+            rw[r] = rows_sorted[lo + min(i0 + r, m - 1)];
+            xr[r] = series + (int64_t)rw[r] * len;
+          }
+          float F[RR];
+          warp_sq_dist_rows<ITERS, RR>(xr, qv, len, lane, F);
+          if (lane == 0)
+#pragma unroll
+            for (int r = 0; r < RR; ++r)
+              if (i0 + r < m) s_buf[filled + i0 + r] = ((unsigned long long)__float_as_uint(F[r]) << 32) | rw[r];
+        }
+      } else {
+        for (int i = warp; i < m; i += nw) {
+          uint32_t row = rows_sorted[lo + i];
+          const float* xr = series + (int64_t)row * len;
+          float F = warp_sq_dist_scalar(xr, qp, len, lane, CUDART_INF_F);
+          if (lane == 0) s_buf[filled + i] = ((unsigned long long)__float_as_uint(F) << 32) | row;
+        }
       }
       filled += m;
     }
