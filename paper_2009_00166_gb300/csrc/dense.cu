@@ -444,6 +444,13 @@ __device__ __forceinline__ float next_up(float r) {
 // the row's 64-row norm range only, so each warp writes its 64 values per tile to shared memory
 // and every lane reads them back (one address per warp). A pair that passes gets the row's own
 // interval and is emitted when d~ - M <= thr.
+//
+// PASS 1 (k = 1 only) is the threshold pass in the same shape, over every SAMPLE-th row tile: a
+// lane's 32 dots of a chunk go through a butterfly of shuffles that leaves lane l with the
+// largest dot of query column l over the warp's 32 rows; the upper end
+// ru(ru(xn_max - 2 dot) + ru(|q|^2 + M_max)) falls as the dot grows, so that dot gives the smallest
+// upper end of the 32 rows, and the lane keeps its query's smallest over the visited tiles.
+template <int PASS>
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
     emit_kernel(const __grid_constant__ CUtensorMap tmX, DenseParams P) {
   extern __shared__ uint8_t dsm_raw[];
@@ -514,7 +521,8 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
   const uint32_t tmem_base = *tmem_holder;
   const int64_t ntiles = (P.n + BN - 1) / BN;
   const int64_t nranges = (P.n + RT - 1) / RT;
-  const int64_t tfirst = rank, tstride = cpg;
+  const int64_t tstep = PASS == 1 ? SAMPLE : 1;
+  const int64_t tfirst = rank * tstep, tstride = (int64_t)cpg * tstep;
   const uint64_t deadline = globaltimer() + P.wait_ns;
   const int nkb = P.nkb;
 
@@ -575,6 +583,61 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
                                     deadline + kDrainNs))
         *abort_flag = 1;
     }
+  } else if (PASS == 1) {  // ---- threshold epilogue (k = 1)
+    const int qd = warp & 3;
+    const int cq = (warp - 2) >> 2;
+    const bool on = cq * 64 < ncols;
+    float ubest[2] = {CUDART_INF_F, CUDART_INF_F};  // this lane's two query columns
+    int j = 0;
+    for (int64_t t = tfirst; t < ntiles; t += tstride, ++j) {
+      const int64_t r = 2 * t + (qd >> 1);
+      const float4 rng = r < nranges ? P.xtile[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool row_ok = t * BN + qd * 32 + lane < P.n;
+      const int ab = j & 1;
+      const uint32_t aph = (uint32_t)((j >> 1) & 1);
+      if (!mbar_wait(b_accf + 8 * ab, aph, abort_flag, deadline)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (on) {
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          const int col0 = cq * 64 + ch * 32;
+          if (col0 >= ncols) break;
+          uint32_t v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * QG + col0), v);
+          float a[32];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) a[c] = row_ok ? __uint_as_float(v[c]) : -CUDART_INF_F;
+          // butterfly: after the step of width o, a[0 .. o) hold columns (lane's bits above o) + c
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int c = 0; c < o; ++c) {
+              const float send = up ? a[c] : a[c + o];
+              const float keep = up ? a[c + o] : a[c];
+              a[c] = fmaxf(keep, __shfl_xor_sync(PARIS_FULL_MASK, send, o));
+            }
+          }
+          const float4 qc = smC[col0 + lane];  // lane l now holds column col0 + l
+          const float Mmax = __fmaf_ru(qc.y, rng.z, __fmul_ru(P.c2, __fadd_ru(qc.x, rng.y)));
+          const float U = __fadd_ru(__fmaf_ru(-2.0f, a[0], rng.y), __fadd_ru(qc.x, Mmax));
+          if (a[0] > -CUDART_INF_F) ubest[ch] = fminf(ubest[ch], U);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce + 8 * ab);
+    }
+    if (on)
+#pragma unroll
+      for (int ch = 0; ch < 2; ++ch) {
+        const int q = cq * 64 + ch * 32 + lane;
+        if (q < nq && ubest[ch] < CUDART_INF_F)
+          atomicMin(P.thr + P.q0 + P.qslot[gq0 + q], __float_as_uint(__fmul_ru(ubest[ch], P.cg)));
+      }
   } else {  // ---- epilogue: warps 2..17; TMEM lane quadrant warp % 4, query quarter (warp - 2) / 4
     const int qd = warp & 3;
     const int we = warp - 2;
@@ -939,7 +1002,8 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   PARIS_CUDA(cudaGetLastError());
   // set on every launch: the attribute is per device, and a cached flag would not be thread-safe
   PARIS_CUDA(cudaFuncSetAttribute(bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM));
-  PARIS_CUDA(cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMIT_SMEM));
+  PARIS_CUDA(cudaFuncSetAttribute(emit_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMIT_SMEM));
+  PARIS_CUDA(cudaFuncSetAttribute(emit_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMIT_SMEM));
   DenseParams P;
   P.wait_ns = wait_limit_ns();
   P.n = idx->n;
@@ -970,10 +1034,12 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   for (int phase = 1; phase <= 2; ++phase) {
     for (int g0 = 0; g0 < groups; g0 += GROUPS) {
       P.group0 = g0;
-      if (phase == 1)
+      if (phase == 1 && qs.k == 1)
+        emit_kernel<1><<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);
+      else if (phase == 1)
         bound_kernel<<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
       else
-        emit_kernel<<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);
+        emit_kernel<2><<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);
       note_launches(1);
       PARIS_CUDA(cudaGetLastError());
     }
