@@ -402,4 +402,43 @@ __device__ __forceinline__ uint64_t warp_pair_key64(int sym, int lane, int w, in
   return hi;
 }
 
+// Exclusive prefix over m values in one block (blockDim.x a multiple of 32, at most 1024): value(j)
+// gives the j-th value, write(j, excl, v) receives its exclusive prefix; returns the total. Every
+// thread of the block must call it.
+template <typename Value, typename Write>
+__device__ uint64_t block_prefix(int m, Value value, Write write) {
+  __shared__ uint64_t s_w[32];
+  __shared__ uint64_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < m; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    const uint64_t v = j < m ? (uint64_t)value(j) : 0ull;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(PARIS_FULL_MASK, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t y = lane < nw ? s_w[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t z = __shfl_up_sync(PARIS_FULL_MASK, y, o);
+        if (lane >= o) y += z;
+      }
+      if (lane < nw) s_w[lane] = y;
+    }
+    __syncthreads();
+    if (j < m) write(j, s_carry + (warp ? s_w[warp - 1] : 0ull) + x - v, v);
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += s_w[nw - 1];
+    __syncthreads();
+  }
+  return s_carry;
+}
+
 }  // namespace paris

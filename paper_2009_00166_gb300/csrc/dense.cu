@@ -771,13 +771,15 @@ __global__ void shadow_kernel(const float* __restrict__ x, int64_t n, int len, _
   }
 }
 
-__global__ void dense_select_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap, int* __restrict__ slots,
-                                    int* __restrict__ nd) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int m = 0;
-  for (int j = 0; j < qc; ++j)
-    if ((int64_t)count[j] > cap) slots[m++] = j;
-  *nd = m;
+// The slots whose candidate list overflowed (or was routed here), in slot order.
+__global__ void __launch_bounds__(1024) dense_select_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap,
+                                                            int* __restrict__ slots, int* __restrict__ nd) {
+  const uint64_t total = block_prefix(
+      qc, [&](int j) { return (int64_t)count[j] > cap ? 1ull : 0ull; },
+      [&](int j, uint64_t excl, uint64_t v) {
+        if (v) slots[excl] = j;
+      });
+  if (threadIdx.x == 0) *nd = (int)total;
 }
 
 __global__ void dense_reset_kernel(uint32_t* __restrict__ count, const int* __restrict__ slots, const int* nd) {
@@ -979,7 +981,7 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   if (nd_out) *nd_out = 0;
   int* slots = cs.dslots;
   int* ndev = cs.dnd;
-  dense_select_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, slots, ndev);
+  dense_select_kernel<<<1, 1024, 0, st>>>(cs.count, cs.qc, cs.cap, slots, ndev);
   note_launches(1);
   int nd = -1;
   int64_t tiles = ((int64_t)cs.qc + BM - 1) / BM;

@@ -201,16 +201,16 @@ __global__ void super_env_kernel(const uint4* __restrict__ env, int64_t npages, 
 // Work items of the list scan: per chunk query, ceil(min(kept, list_cap) / kItemPages) items
 // when its kept pages fit its list (the others go through the tile scan); prefix[qc] = total.
 constexpr int kItemPages = 64;
-__global__ void item_prefix_kernel(const uint32_t* __restrict__ list_count, int qc, int64_t list_cap,
-                                   uint32_t* __restrict__ prefix) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint32_t acc = 0;
-  for (int j = 0; j < qc; ++j) {
-    prefix[j] = acc;
-    const uint32_t c = list_count[j];
-    if ((int64_t)c <= list_cap) acc += (c + kItemPages - 1) / kItemPages;
-  }
-  prefix[qc] = acc;
+__global__ void __launch_bounds__(1024) item_prefix_kernel(const uint32_t* __restrict__ list_count, int qc,
+                                                            int64_t list_cap, uint32_t* __restrict__ prefix) {
+  const uint64_t total = block_prefix(
+      qc,
+      [&](int j) {
+        const uint32_t c = list_count[j];
+        return (int64_t)c <= list_cap ? (uint64_t)((c + kItemPages - 1) / kItemPages) : 0ull;
+      },
+      [&](int j, uint64_t excl, uint64_t) { prefix[j] = (uint32_t)excl; });
+  if (threadIdx.x == 0) prefix[qc] = (uint32_t)total;
 }
 
 constexpr int kListThreads = 512;
@@ -399,7 +399,7 @@ paris_status launch_lbscan_lists(const paris_index* idx, const QueryState& qs, c
                                  int stop_on_overflow, uint32_t* status, cudaStream_t st) {
   if (cs.qc <= 0) return PARIS_OK;
   const int64_t list_cap = page_list_cap(idx->n);
-  item_prefix_kernel<<<1, 32, 0, st>>>(cs.page_count, cs.qc, list_cap, cs.item_prefix);
+  item_prefix_kernel<<<1, 1024, 0, st>>>(cs.page_count, cs.qc, list_cap, cs.item_prefix);
   const size_t smem = (size_t)idx->card * 64 * sizeof(float);
   PARIS_CUDA(cudaFuncSetAttribute(lbscan_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = sm_count_leaf() * 2;

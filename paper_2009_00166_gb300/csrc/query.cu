@@ -151,23 +151,36 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
   }
 }
 
-// The lower-bound table, one entry per thread: T[c][i] for query blockIdx.y.
-__global__ void __launch_bounds__(256) qtable_kernel(const double* __restrict__ qpaa, int card, int w, double scale,
+// The lower-bound table, one entry per thread: T[c][i] for query blockIdx.y; a block covers 16
+// symbols of all 16 segments. Every FP64 value is held between its fp32 roundings down and up
+// (the query's PAA per segment, the block's 17 region ends), and the distance from the PAA to
+// region c is bounded from below in fp32 with rounding toward -inf: d = rd(lo- - P+) below the
+// region, rd(P- - hi+) above it, 0 otherwise; T = rd(rd(d * d) * s) <= s * (exact distance)^2.
+__global__ void __launch_bounds__(256) qtable_kernel(const double* __restrict__ qpaa, int card, int w, float scale,
                                                      const double* __restrict__ beta_ext, float* __restrict__ qtable) {
+  __shared__ float2 s_p[16];     // PAA of each segment: (round down, round up)
+  __shared__ float2 s_b[17];     // region ends c0 .. c0 + 16: (round down, round up)
   const int64_t q = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c0 = blockIdx.x * 16;
+  if (threadIdx.x < 16) {
+    const double P = qpaa[q * 16 + threadIdx.x];
+    s_p[threadIdx.x] = make_float2(__double2float_rd(P), __double2float_ru(P));
+  } else if (threadIdx.x < 33 && c0 + (int)threadIdx.x - 16 <= card) {
+    const double b = beta_ext[c0 + threadIdx.x - 16];
+    s_b[threadIdx.x - 16] = make_float2(__double2float_rd(b), __double2float_ru(b));
+  }
+  __syncthreads();
+  const int e = c0 * 16 + threadIdx.x;
   if (e >= card * 16) return;
-  const int c = e >> 4, seg = e & 15;
+  const int cl = threadIdx.x >> 4, seg = threadIdx.x & 15;
   float val = 0.f;
   if (seg < w) {
-    const double P = qpaa[q * 16 + seg];
-    const double lo = beta_ext[c], hi = beta_ext[c + 1];
-    double d = 0.0;
-    if (P < lo) d = lo - P;
-    else if (P > hi) d = P - hi;
-    const double mag = fabs(P) + (isinf(lo) ? 0.0 : fabs(lo)) + (isinf(hi) ? 0.0 : fabs(hi)) + 1.0;
-    d = fmax(0.0, d - mag * 0x1p-50);
-    val = __double2float_rd(scale * d * d);
+    const float2 p = s_p[seg];
+    const float lo = s_b[cl].x, hi = s_b[cl + 1].y;
+    float d = 0.f;
+    if (p.y < lo) d = __fsub_rd(lo, p.y);
+    else if (p.x > hi) d = __fsub_rd(p.x, hi);
+    val = __fmul_rd(__fmul_rd(d, d), scale);
   }
   qtable[q * (int64_t)card * 16 + e] = val;
 }
@@ -486,20 +499,22 @@ __global__ void __launch_bounds__(kLbThreads, 2) lbscan_kernel(
 // --------------------------------------------------------------------- refinement (Alg. 9)
 // Per-query candidate segments are padded to multiples of 32 in the flat work space so that a
 // 32-candidate step of a warp never spans two queries.
-__global__ void chunk_prefix_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap,
-                                    uint32_t* __restrict__ prefix, unsigned long long* __restrict__ counters) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    uint64_t acc = 0, raw = 0;
-    for (int j = 0; j < qc; ++j) {
-      prefix[j] = (uint32_t)acc;
-      uint64_t c = count[j];
-      raw += c;
-      uint64_t m = c < (uint64_t)cap ? c : (uint64_t)cap;
-      acc += (m + 31) & ~(uint64_t)31;
-    }
-    prefix[qc] = (uint32_t)acc;
-    atomicAdd(&counters[0], (unsigned long long)raw);
-  }
+__global__ void __launch_bounds__(1024) chunk_prefix_kernel(const uint32_t* __restrict__ count, int qc, int64_t cap,
+                                                             uint32_t* __restrict__ prefix,
+                                                             unsigned long long* __restrict__ counters) {
+  uint64_t raw = 0;
+  const uint64_t total = block_prefix(
+      qc,
+      [&](int j) {
+        const uint64_t c = count[j];
+        raw += c;
+        const uint64_t m = c < (uint64_t)cap ? c : (uint64_t)cap;
+        return (m + 31) & ~(uint64_t)31;
+      },
+      [&](int j, uint64_t excl, uint64_t) { prefix[j] = (uint32_t)excl; });
+  if (threadIdx.x == 0) prefix[qc] = (uint32_t)total;
+  for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(PARIS_FULL_MASK, raw, o);
+  if ((threadIdx.x & 31) == 0 && raw) atomicAdd(&counters[0], (unsigned long long)raw);
 }
 
 // Each warp step takes 32 candidates of one query (one per lane), re-tests their lower bounds
@@ -958,7 +973,7 @@ paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cud
   }
 #undef PREP
   dim3 tg((unsigned)((idx->card * 16 + 255) / 256), (unsigned)qs.nq);
-  qtable_kernel<<<tg, 256, 0, st>>>(qs.qpaa, idx->card, idx->w, (double)(idx->len / idx->w), idx->beta_ext,
+  qtable_kernel<<<tg, 256, 0, st>>>(qs.qpaa, idx->card, idx->w, (float)(idx->len / idx->w), idx->beta_ext,
                                     qs.qtable);
   note_launches(2);
   PARIS_CUDA(cudaGetLastError());
@@ -1063,7 +1078,7 @@ paris_status launch_lbscan_threshold(const paris_index* idx, const float* table,
 
 paris_status launch_refine(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                            cudaStream_t st) {
-  chunk_prefix_kernel<<<1, 32, 0, st>>>(cs.count, cs.qc, cs.cap, cs.prefix, qs.counters);
+  chunk_prefix_kernel<<<1, 1024, 0, st>>>(cs.count, cs.qc, cs.cap, cs.prefix, qs.counters);
   PARIS_CUDA(cudaMemsetAsync(cs.bucket, 0, (size_t)cs.qc * kBuckets * sizeof(uint32_t), st));
   {
     int64_t blocks_x = std::min<int64_t>((cs.cap + 255) / 256, 128);
