@@ -825,12 +825,15 @@ def main():
     wl = {"n": n, "len": length, "queries": nq}    # committed DRAM counters hold only at their own sizes
     if dominant == "dense":
         # algorithmic work of the BF16 screening: 2*len flops per (query, row) pair in the
-        # emission pass over every row tile, plus the threshold pass over one row tile in 16
+        # emission pass over every row tile, plus the threshold pass over one row tile in 16; the
+        # time is the screening phase's (both passes and their small selection kernels)
         flops = 2.0 * length * n * dense_q * (1.0 + 1.0 / 16.0)
         tf = flops / (ph["dense"] * 1e-3) / 1e12
         peak_tf = bf16_peak_sustained()
-        roof = {"kernel": "dense_kernel", "bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": tf / peak_tf, "traffic": traffic_for("dense_kernel", 0, wl)}
+        roof = {"kernel": "emit_kernel", "bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": tf / peak_tf, "traffic": traffic_for("emit_kernel", 0, wl),
+                "note": "time of the screening phase: threshold pass (emit_kernel<1>) + emission pass "
+                        "(emit_kernel<2>) + selection; traffic is the emission pass's DRAM bytes per launch"}
     elif dominant == "refine":
         roof = {"kernel": "refine_kernel", "bound": "hbm", "achieved": refine_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": refine_gbs / hbm_peak, "traffic": traffic_for("refine_kernel", 0, wl)}
@@ -838,19 +841,24 @@ def main():
         # the batched scan is bound by shared-memory table lookups: one 32-bit lookup per lane,
         # slot and query pair, counted by the library (early-abandoned slots are not looked up);
         # peak = 32 banks x 152 SMs x the median SM clock under load
-        lookups = float(sum(s["lb_lookups"] for r in recs for s in r["stats"]))
+        # (the work-list scan of the queries that keep few pages: 16 lookups per row it tests)
+        tile_lookups = float(sum(s["lb_lookups"] for r in recs for s in r["stats"]))
+        list_lookups = 16.0 * float(sum(s["list_rows"] for r in recs for s in r["stats"]))
+        lookups = tile_lookups + list_lookups
         qt_used = recs[0]["stats"][0]["query_tile"]
         ach = lookups / (ph["lbscan"] * 1e-3) / 1e9
         clk_mhz = clk.get("sm_mhz") or 2070.0
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_l = 32.0 * sms * clk_mhz * 1e6 / 1e9
-        roof = {"kernel": "lbscan_batched_kernel", "bound": "alu", "achieved": ach, "peak": peak_l,
+        kname = "lbscan_batched_kernel" if tile_lookups >= list_lookups else "lbscan_list_kernel"
+        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak_l,
                 "unit": "G shared-memory lookups/s", "frac": ach / peak_l,
-                "traffic": traffic_for("lbscan_batched_kernel", qt_used, wl),
-                "lookups_per_step": lookups / steps,
+                "traffic": traffic_for(kname, qt_used if kname == "lbscan_batched_kernel" else 0, wl),
+                "lookups_per_step": lookups / steps, "list_lookups_per_step": list_lookups / steps,
                 "query_tile": qt_used,
                 "summaries_read_per_step_gb_at_most": 16.0 * n * (-(-nq // max(1, qt_used))) / 1e9,
-                "note": "time includes the pilot pass and the query ordering; lookups counted on the device"}
+                "note": "time of the whole lower-bound phase (page pass, pilot, ordering, tile and list scans); "
+                        "lookups counted on the device"}
     else:
         roof = {"kernel": "lbscan_kernel", "bound": "hbm", "achieved": lb_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (lb_gbs or 0.0) / hbm_peak, "traffic": traffic_for("lbscan_kernel", 0, wl)}
