@@ -97,6 +97,8 @@ __global__ void page_env_kernel(const uint4* __restrict__ sax_sorted, int64_t n,
 // per half-warp, so the 32 lookups of a step fall in 32 different banks).
 // Writes bit p of bits[q][words] for each kept page (the caller zeroes bits), counts the kept
 // pages of each query in list_count[q] and lists the first list_cap of them in lists[q][].
+constexpr int kPageAhead = 4;  // words of pages whose envelopes a warp loads together
+
 __device__ __forceinline__ float box_lb(uint4 lo, uint4 hi, const uint4& sq, const uint32_t (&offp)[8], uint32_t tab) {
   const uint32_t wv[4] = {__vmaxu4(__vminu4(sq.x, hi.x), lo.x), __vmaxu4(__vminu4(sq.y, hi.y), lo.y),
                           __vmaxu4(__vminu4(sq.z, hi.z), lo.z), __vmaxu4(__vminu4(sq.w, hi.w), lo.w)};
@@ -157,25 +159,41 @@ __global__ void __launch_bounds__(kPageThreads) page_lb_kernel(
     // words of the 32 super pages: word 16 sw + j holds super pages 32 sw + 2j and 2j + 1
     uint32_t pw = (ks | (ks >> 1)) & 0x55555555u;
     while (pw) {
-      const int b = __ffs(pw) - 1;  // even: super page pair (b, b + 1)
-      pw &= pw - 1u;
-      const int64_t wd = sw * 16 + (b >> 1);
-      const int64_t pg = wd * 32 + lane;
-      const bool in_super = (ks >> (b + (lane >> 4))) & 1u;
-      const bool valid = in_super && pg < npages;
-      const uint4 lo = valid ? __ldg(env + 2 * pg) : make_uint4(0u, 0u, 0u, 0u);
-      const uint4 hi = valid ? __ldg(env + 2 * pg + 1) : make_uint4(0u, 0u, 0u, 0u);
-      const float lb = box_lb(lo, hi, sq, offp, tab);
-      const bool keep = valid && lb * kPageKeepScale <= t;
-      const uint32_t m = __ballot_sync(PARIS_FULL_MASK, keep);
-      if (!m) continue;
-      if (lane == 0 && bits) bits[q * words + wd] = m;
-      kept += __popc(m);
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(list_count + q, (uint32_t)__popc(m));
-      base = __shfl_sync(PARIS_FULL_MASK, base, 0);
-      const uint32_t at = base + __popc(m & ((1u << lane) - 1u));
-      if (lists && keep && (int64_t)at < list_cap) lists[q * list_cap + at] = (uint32_t)pg;
+      // up to kPageAhead words of pages per round, their envelope loads in flight together
+      int bs[kPageAhead];
+#pragma unroll
+      for (int a = 0; a < kPageAhead; ++a) {
+        bs[a] = pw ? __ffs(pw) - 1 : -1;  // even: super page pair (b, b + 1)
+        if (pw) pw &= pw - 1u;
+      }
+      uint4 lo[kPageAhead], hi[kPageAhead];
+      bool valid[kPageAhead];
+#pragma unroll
+      for (int a = 0; a < kPageAhead; ++a) {
+        const int b = bs[a];
+        const int64_t pg = (sw * 16 + (b >> 1)) * 32 + lane;
+        valid[a] = b >= 0 && ((ks >> (b + (lane >> 4))) & 1u) && pg < npages;
+        lo[a] = valid[a] ? __ldg(env + 2 * pg) : make_uint4(0u, 0u, 0u, 0u);
+        hi[a] = valid[a] ? __ldg(env + 2 * pg + 1) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int a = 0; a < kPageAhead; ++a) {
+        const int b = bs[a];
+        if (b < 0) break;  // warp-uniform
+        const int64_t wd = sw * 16 + (b >> 1);
+        const int64_t pg = wd * 32 + lane;
+        const float lb = box_lb(lo[a], hi[a], sq, offp, tab);
+        const bool keep = valid[a] && lb * kPageKeepScale <= t;
+        const uint32_t m = __ballot_sync(PARIS_FULL_MASK, keep);
+        if (!m) continue;
+        if (lane == 0 && bits) bits[q * words + wd] = m;
+        kept += __popc(m);
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(list_count + q, (uint32_t)__popc(m));
+        base = __shfl_sync(PARIS_FULL_MASK, base, 0);
+        const uint32_t at = base + __popc(m & ((1u << lane) - 1u));
+        if (lists && keep && (int64_t)at < list_cap) lists[q * list_cap + at] = (uint32_t)pg;
+      }
     }
   }
   if (lane == 0 && kept && pages_kept) atomicAdd(pages_kept, kept);
@@ -215,6 +233,7 @@ __global__ void __launch_bounds__(1024) item_prefix_kernel(const uint32_t* __res
 
 constexpr int kListThreads = 512;
 constexpr int kListStage = 64;
+constexpr int kListAhead = 4;  // groups of 32 summaries whose loads a warp issues together
 
 __device__ __forceinline__ void list_flush(uint32_t* s_row, float* s_lb, int nflush, int lane, uint32_t* count,
                                            uint32_t* out_rows, float* out_lb, int64_t cap, uint32_t* status) {
@@ -293,39 +312,53 @@ __global__ void __launch_bounds__(kListThreads, 2) lbscan_list_kernel(
     uint32_t* qrows = out_rows + (int64_t)q * cap;
     float* qlb = out_lb + (int64_t)q * cap;
     int fill = 0;
-    for (int64_t g = wib; g < groups; g += blockDim.x >> 5) {
-      const int64_t pos = ((int64_t)lst[p0 + g / kGpp] * kGpp + g % kGpp) * 32 + lane;
-      const uint4 word = pos < n ? __ldcs(sax + pos) : make_uint4(0u, 0u, 0u, 0u);
-      const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
-      float lb = 0.f;
+    const int nw = blockDim.x >> 5;
+    // kListAhead groups of 32 summaries per warp and round: their loads are in flight together
+    for (int64_t g0 = wib; g0 < groups; g0 += (int64_t)kListAhead * nw) {
+      int64_t pa[kListAhead];
+      uint4 wa[kListAhead];
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
-        const uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
-        float v;
-        asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-        lb += v;
+      for (int a = 0; a < kListAhead; ++a) {
+        const int64_t g = g0 + (int64_t)a * nw;
+        pa[a] = g < groups ? ((int64_t)lst[p0 + g / kGpp] * kGpp + g % kGpp) * 32 + lane : n;
       }
-      const bool keep = pos < n && lb * kPageKeepScale <= t;
-      tested += pos < n ? 1u : 0u;
-      const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
-      if (mk) {
-        if (keep) {
-          const int p = fill + __popc(mk & lt_mask);
-          st_row[p] = pos_row[pos];
-          st_lb[p] = lb;
+#pragma unroll
+      for (int a = 0; a < kListAhead; ++a) wa[a] = pa[a] < n ? __ldcs(sax + pa[a]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int a = 0; a < kListAhead; ++a) {
+        const int64_t pos = pa[a];
+        const uint4 word = wa[a];
+        const uint32_t wv[4] = {word.x, word.y, word.z, word.w};
+        float lb = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const uint32_t sel = (4u + 2u * (kk & 1)) | ((uint32_t)(kk & 3) << 4) | (5u << 8) | (5u << 12);
+          const uint32_t addr = tab + __byte_perm(wv[kk >> 2], offp[kk >> 1], sel);
+          float v;
+          asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+          lb += v;
         }
-        fill += __popc(mk);
-        __syncwarp();
-        if (fill >= 32) {
-          list_flush(st_row, st_lb, 32, lane, count + q, qrows, qlb, cap, status);
-          __syncwarp();
-          if (lane < fill - 32) {
-            st_row[lane] = st_row[32 + lane];
-            st_lb[lane] = st_lb[32 + lane];
+        const bool keep = pos < n && lb * kPageKeepScale <= t;
+        tested += pos < n ? 1u : 0u;
+        const uint32_t mk = __ballot_sync(PARIS_FULL_MASK, keep);
+        if (mk) {
+          if (keep) {
+            const int p = fill + __popc(mk & lt_mask);
+            st_row[p] = pos_row[pos];
+            st_lb[p] = lb;
           }
-          fill -= 32;
+          fill += __popc(mk);
           __syncwarp();
+          if (fill >= 32) {
+            list_flush(st_row, st_lb, 32, lane, count + q, qrows, qlb, cap, status);
+            __syncwarp();
+            if (lane < fill - 32) {
+              st_row[lane] = st_row[32 + lane];
+              st_lb[lane] = st_lb[32 + lane];
+            }
+            fill -= 32;
+            __syncwarp();
+          }
         }
       }
     }
