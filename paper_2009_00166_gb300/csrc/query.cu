@@ -58,7 +58,8 @@ __device__ __forceinline__ float sq4(float4 a, float4 b, float acc) {
 template <int ITERS>
 __device__ __forceinline__ float warp_sq_dist_vec(const float* __restrict__ x, const QVec<ITERS>& q,
                                                   int len, int lane, float abandon) {
-  constexpr int CH = ITERS >= 4 ? ITERS / 4 : 1;  // sweeps between abandon checks
+  // sweeps between abandon checks: rows of up to 256 values are loaded at once (one round trip)
+  constexpr int CH = ITERS >= 4 ? ITERS / 4 : ITERS;
   float acc = 0.f;
 #pragma unroll
   for (int t0 = 0; t0 < ITERS; t0 += CH) {
