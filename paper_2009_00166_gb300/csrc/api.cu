@@ -773,7 +773,7 @@ struct KnnJob {
                                (double)idx->card * 32.0));
       qc = std::max<int64_t>(1, std::min<int64_t>(qc, 4096));
     }
-    qc = std::min(qc, nq);
+    qc = std::min<int64_t>(std::min(qc, nq), 65535);  // per-query grids of a chunk use the y extent
     size_t off = 0;
     auto take = [&](size_t b) {
       size_t o2 = off;

@@ -152,38 +152,41 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ que
   }
 }
 
-// The lower-bound table, one entry per thread: T[c][i] for query blockIdx.y; a block covers 16
+// The lower-bound table, one entry per thread: T[c][i] for queries blockIdx.y + j * gridDim.y; a block covers 16
 // symbols of all 16 segments. Every FP64 value is held between its fp32 roundings down and up
 // (the query's PAA per segment, the block's 17 region ends), and the distance from the PAA to
 // region c is bounded from below in fp32 with rounding toward -inf: d = rd(lo- - P+) below the
 // region, rd(P- - hi+) above it, 0 otherwise; T = rd(rd(d * d) * s) <= s * (exact distance)^2.
-__global__ void __launch_bounds__(256) qtable_kernel(const double* __restrict__ qpaa, int card, int w, float scale,
-                                                     const double* __restrict__ beta_ext, float* __restrict__ qtable) {
-  __shared__ float2 s_p[16];     // PAA of each segment: (round down, round up)
-  __shared__ float2 s_b[17];     // region ends c0 .. c0 + 16: (round down, round up)
-  const int64_t q = blockIdx.y;
+__global__ void __launch_bounds__(256) qtable_kernel(const double* __restrict__ qpaa, int64_t nq, int card, int w,
+                                                     float scale, const double* __restrict__ beta_ext,
+                                                     float* __restrict__ qtable) {
+  __shared__ float2 s_p[16];  // PAA of each segment: (round down, round up)
+  __shared__ float2 s_b[17];  // region ends c0 .. c0 + 16: (round down, round up)
   const int c0 = blockIdx.x * 16;
-  if (threadIdx.x < 16) {
-    const double P = qpaa[q * 16 + threadIdx.x];
-    s_p[threadIdx.x] = make_float2(__double2float_rd(P), __double2float_ru(P));
-  } else if (threadIdx.x < 33 && c0 + (int)threadIdx.x - 16 <= card) {
-    const double b = beta_ext[c0 + threadIdx.x - 16];
-    s_b[threadIdx.x - 16] = make_float2(__double2float_rd(b), __double2float_ru(b));
-  }
-  __syncthreads();
   const int e = c0 * 16 + threadIdx.x;
-  if (e >= card * 16) return;
   const int cl = threadIdx.x >> 4, seg = threadIdx.x & 15;
-  float val = 0.f;
-  if (seg < w) {
-    const float2 p = s_p[seg];
-    const float lo = s_b[cl].x, hi = s_b[cl + 1].y;
-    float d = 0.f;
-    if (p.y < lo) d = __fsub_rd(lo, p.y);
-    else if (p.x > hi) d = __fsub_rd(p.x, hi);
-    val = __fmul_rd(__fmul_rd(d, d), scale);
+  for (int64_t q = blockIdx.y; q < nq; q += gridDim.y) {  // the grid's y extent is capped at 65535
+    __syncthreads();  // the previous query's values are no longer read
+    if (threadIdx.x < 16) {
+      const double P = qpaa[q * 16 + threadIdx.x];
+      s_p[threadIdx.x] = make_float2(__double2float_rd(P), __double2float_ru(P));
+    } else if (threadIdx.x < 33 && c0 + (int)threadIdx.x - 16 <= card) {
+      const double b = beta_ext[c0 + threadIdx.x - 16];
+      s_b[threadIdx.x - 16] = make_float2(__double2float_rd(b), __double2float_ru(b));
+    }
+    __syncthreads();
+    if (e >= card * 16) continue;
+    float val = 0.f;
+    if (seg < w) {
+      const float2 p = s_p[seg];
+      const float lo = s_b[cl].x, hi = s_b[cl + 1].y;
+      float d = 0.f;
+      if (p.y < lo) d = __fsub_rd(lo, p.y);
+      else if (p.x > hi) d = __fsub_rd(p.x, hi);
+      val = __fmul_rd(__fmul_rd(d, d), scale);
+    }
+    qtable[q * (int64_t)card * 16 + e] = val;
   }
-  qtable[q * (int64_t)card * 16 + e] = val;
 }
 
 // --------------------------------------------------------------------- approximate search
@@ -973,8 +976,8 @@ paris_status launch_query_prep(const paris_index* idx, const QueryState& qs, cud
     default: PREP(32); break;
   }
 #undef PREP
-  dim3 tg((unsigned)((idx->card * 16 + 255) / 256), (unsigned)qs.nq);
-  qtable_kernel<<<tg, 256, 0, st>>>(qs.qpaa, idx->card, idx->w, (float)(idx->len / idx->w), idx->beta_ext,
+  dim3 tg((unsigned)((idx->card * 16 + 255) / 256), (unsigned)std::min<int64_t>(qs.nq, 65535));
+  qtable_kernel<<<tg, 256, 0, st>>>(qs.qpaa, qs.nq, idx->card, idx->w, (float)(idx->len / idx->w), idx->beta_ext,
                                     qs.qtable);
   note_launches(2);
   PARIS_CUDA(cudaGetLastError());

@@ -226,3 +226,21 @@ def test_query_prep_planted_exactness(length):
     gi, gd = run_knn(idx, q, 3)
     assert_matches(x, q, 3, gi, gd)
     idx.free()
+
+
+def test_more_queries_than_a_grid_dimension():
+    """70,000 queries in one call (more than the 65,535 blocks of a grid's y extent): every step
+    that works per query must cover them all."""
+    import paper_2009_00166_gb300 as P
+    dev = require_gpu()
+    x = rw(3000, 64, 81)
+    q = rw(70_000, 64, 82)
+    idx = P.paris_build(torch.from_numpy(x).to(dev), 16, 256)
+    want_i, want_d = oknn.knn(x, q, 1)
+    for mode in (P.PARIS_MODE_BATCHED, P.PARIS_MODE_PLAIN):
+        gi, gd = run_knn(idx, q if mode == P.PARIS_MODE_BATCHED else q[-300:], 1, mode=mode)
+        wi = want_i if mode == P.PARIS_MODE_BATCHED else want_i[-300:]
+        assert np.array_equal(gi, wi)
+    leaf, seed = P.paris_approx_search(idx, torch.from_numpy(q).to(dev), 1)
+    assert np.all(seed.cpu().numpy() >= want_d[:, 0] ** 2 * (1 - 1e-5))
+    idx.free()
