@@ -61,10 +61,13 @@ constexpr size_t A_BYTES = (size_t)QTILES * MAX_KB * BM * 128;
 constexpr size_t DENSE_SMEM = 1024 + A_BYTES + STAGES * KBLK_BYTES + 256;
 static_assert(BM * 128 == KBLK_BYTES, "query and row tiles share the K-block shape");
 static_assert(DENSE_SMEM <= 232448, "dynamic shared memory of one CTA");
-// pass 2 (emit_kernel): a query group of QG queries is the MMA N side
-constexpr int QG = QTILES * BM;                          // queries per group
+// emit_kernel: a query group of up to QG queries is the MMA N side; its BF16 rows fill at most
+// Q_BYTES of shared memory, so a group holds qg = min(QG, 65536 / len) queries (rounded down to
+// a multiple of 32): 256 up to len 256, 128 at len 512, 64 at len 1024
+constexpr int QG = QTILES * BM;                          // largest group
+constexpr int E_MAX_LEN = 1024;                          // longest series the emit kernels take
 constexpr int E_STAGES = 5;                              // its ring depth
-constexpr size_t Q_BYTES = (size_t)MAX_KB * QG * 128;   // the group's K blocks
+constexpr size_t Q_BYTES = (size_t)MAX_KB * QG * 128;   // the group's K blocks (128 KB)
 constexpr size_t EMIT_SMEM = 1024 + Q_BYTES + E_STAGES * KBLK_BYTES + EPI_WARPS * 64 * 4 + QG * 16 + 256;
 static_assert(EMIT_SMEM <= 232448, "dynamic shared memory of one CTA");
 static_assert(2 * QG <= (int)TMEM_COLS, "two accumulators of QG columns");
@@ -75,6 +78,7 @@ struct DenseParams {
   int64_t n;
   int len, nkb;
   int group0, nd;        // first query group of the launch; nd < 0: read from nd_dev
+  int qg;                // queries per group of emit_kernel (a multiple of 32, at most QG)
   const int* nd_dev;
   const float2* xnorm;  // [n]: (|x|^2, |x|)
   const uint32_t* qbf;  // BF16 query rows, [rows][len] (pairs of elements per word)
@@ -455,17 +459,18 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     emit_kernel(const __grid_constant__ CUtensorMap tmX, DenseParams P) {
   extern __shared__ uint8_t dsm_raw[];
   const int nd = P.nd >= 0 ? P.nd : *P.nd_dev;
-  const int groups = (nd + QG - 1) / QG - P.group0;
+  const int qg = P.qg;
+  const int groups = (nd + qg - 1) / qg - P.group0;
   if (groups <= 0) return;
   const int G = groups < GROUPS ? groups : GROUPS;
   const int cpg = (int)gridDim.x / G;
   const int grp = (int)blockIdx.x % G, rank = (int)blockIdx.x / G;
   if (rank >= cpg) return;
-  const int gq0 = (P.group0 + grp) * QG;        // first screened query of the group
-  const int nq = min(QG, nd - gq0);              // its queries
+  const int gq0 = (P.group0 + grp) * qg;        // first screened query of the group
+  const int nq = min(qg, nd - gq0);              // its queries
   const int ncols = (nq + 31) & ~31;             // MMA N (a multiple of 16, at most 256)
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* smQ = base;                                   // [MAX_KB][QG rows] query K blocks
+  uint8_t* smQ = base;                                   // [nkb][qg rows] query K blocks
   uint8_t* smX = base + Q_BYTES;                         // [E_STAGES] row-tile K blocks (TMA)
   float* smL = (float*)(smX + E_STAGES * KBLK_BYTES);    // [EPI_WARPS][64] range thresholds L
   float4* smC = (float4*)(smL + EPI_WARPS * 64);         // [QG]: |q|^2, ru(c1 |q|), thr, slot
@@ -494,14 +499,14 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   // the group's queries, K block kb holding query r's 16-byte chunk j at
-  // kb * QG * 128 + r * 128 + 16 * (j ^ (r mod 8)) (the 128-byte swizzle of the descriptors)
+  // kb * qg * 128 + r * 128 + 16 * (j ^ (r mod 8)) (the 128-byte swizzle of the descriptors)
   {
     const int nkb = P.nkb;
-    for (int e = threadIdx.x; e < nkb * QG * 8; e += blockDim.x) {
-      const int j = e & 7, r = (e >> 3) & (QG - 1), kb = e >> 11;
+    for (int e = threadIdx.x; e < nkb * qg * 8; e += blockDim.x) {
+      const int j = e & 7, r = (e >> 3) % qg, kb = (e >> 3) / qg;
       if (r >= ncols) continue;
       const uint4 v = *reinterpret_cast<const uint4*>(P.qbf + (int64_t)(gq0 + r) * (P.len / 2) + kb * (BKE / 2) + j * 4);
-      *reinterpret_cast<uint4*>(smQ + (size_t)kb * QG * 128 + r * 128 + ((j ^ (r & 7)) << 4)) = v;
+      *reinterpret_cast<uint4*>(smQ + (size_t)kb * qg * 128 + r * 128 + ((j ^ (r & 7)) << 4)) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
     for (int q = threadIdx.x; q < QG; q += blockDim.x) {
@@ -568,7 +573,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smX + (size_t)s * KBLK_BYTES);
-          const uint32_t b0 = smem_u32(smQ + (size_t)kb * QG * 128);
+          const uint32_t b0 = smem_u32(smQ + (size_t)kb * qg * 128);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
             umma_bf16(d_tmem, smem_desc_sw128(a0 + 32 * ks), smem_desc_sw128(b0 + 32 * ks), idesc,
@@ -838,7 +843,7 @@ int sm_count_dense() {
 }  // namespace
 
 bool dense_supported(const paris_index* idx, int k) {
-  return k <= KMAX && idx->len % BKE == 0 && idx->len <= MAX_KB * BKE;
+  return k <= KMAX && idx->len % BKE == 0 && idx->len <= E_MAX_LEN;
 }
 
 void dense_margins(int len, float* c1, float* c2) {
@@ -889,7 +894,7 @@ __global__ void tile_range_kernel(const float2* __restrict__ nm, int64_t n, floa
 size_t norm_bytes(int64_t n) { return (size_t)((n + RT - 1) / RT * RT) * sizeof(float2); }
 size_t range_bytes(int64_t n) { return (size_t)((n + RT - 1) / RT) * sizeof(float4); }
 
-bool dense_shape_ok(int len) { return len % BKE == 0 && len <= MAX_KB * BKE; }
+bool dense_shape_ok(int len) { return len % BKE == 0 && len <= E_MAX_LEN; }
 
 paris_status alloc_shadow(const paris_index* idx, ShadowBufs* out, cudaStream_t st) {
   *out = ShadowBufs{};
@@ -1032,13 +1037,21 @@ paris_status launch_dense(paris_index* idx, const QueryState& qs, const ChunkSta
   const int64_t ntiles = (idx->n + BN - 1) / BN;
   const int grid = (int)std::max<int64_t>(std::min<int64_t>(ntiles, sm_count_dense()), GROUPS);
   const CUtensorMap* mapB = (const CUtensorMap*)idx->shadow_map;
-  const int groups = (int)((tiles + QTILES - 1) / QTILES);
+  P.qg = std::min(QG, (65536 / idx->len) & ~31);
+  const int64_t rows_max = tiles * BM;  // screened queries at most (nd, or the chunk when nd is on the device)
   for (int phase = 1; phase <= 2; ++phase) {
+    // the threshold pass: k = 1 in the rows-on-M shape; k > 1 with queries on M (two tiles of
+    // 128 queries of up to 256 values in shared memory); longer series with k > 1 skip it (it only
+    // tightens the thresholds: the emission pass is exact from any valid threshold)
+    const bool qm = phase == 1 && qs.k > 1;
+    if (qm && idx->len > MAX_KB * BKE) continue;
+    const int64_t gsize = qm ? (int64_t)QTILES * BM : P.qg;
+    const int groups = (int)((rows_max + gsize - 1) / gsize);
     for (int g0 = 0; g0 < groups; g0 += GROUPS) {
       P.group0 = g0;
-      if (phase == 1 && qs.k == 1)
+      if (phase == 1 && !qm)
         emit_kernel<1><<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);
-      else if (phase == 1)
+      else if (qm)
         bound_kernel<<<grid, DENSE_THREADS, DENSE_SMEM, st>>>(*mapB, P);
       else
         emit_kernel<2><<<grid, DENSE_THREADS, EMIT_SMEM, st>>>(*mapB, P);

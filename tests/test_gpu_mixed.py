@@ -38,8 +38,12 @@ def test_mixed_equals_oracle_hard_queries(k):
     idx.free()
 
 
-@pytest.mark.parametrize("n,length", [(30001, 256), (20000 + 63, 128), (9000, 64)])
+@pytest.mark.parametrize("n,length", [(30001, 256), (20000 + 63, 128), (9000, 64), (12001, 512), (20011, 320),
+                                      (16411, 1024)])
 def test_mixed_ragged_shapes(n, length):
+    """Longer series put fewer queries in a screening group (256 up to len 256, then
+    65536 / len rounded down to a multiple of 32: 192 at 320, 128 at 512, 64 at 1024), so 131
+    queries span one to three groups; k = 3 at len > 256 runs without the threshold pass."""
     import paper_2009_00166_gb300 as P
     import synth
     dev = require_gpu()
