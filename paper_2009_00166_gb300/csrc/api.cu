@@ -832,8 +832,10 @@ struct KnnJob {
   paris_status page_pass(int64_t c) {
     if (!prune || o.mode != PARIS_MODE_BATCHED || paged_chunk == c) return PARIS_OK;
     timer.begin(2);
+    // in MIXED refinement a query over its list is screened on the tensor cores: its page bits
+    // and exact page count are not needed (no tile scan runs then)
     PARIS_TRY(launch_page_lb(idx, qs, cs.q0, cs.qc, cs.pagebits, cs.page_list, cs.page_count,
-                             page_list_cap(idx->n), st));
+                             page_list_cap(idx->n), st, mixed && cs.cap < idx->n));
     timer.end(2);
     pages_examined += idx->npages * (int64_t)cs.qc;
     paged_chunk = c;

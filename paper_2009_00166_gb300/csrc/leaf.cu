@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kPageThreads) page_lb_kernel(
     const uint4* __restrict__ senv, int64_t nsuper, const uint4* __restrict__ env, int64_t npages, int64_t words,
     const float* __restrict__ qtable, const uint8_t* __restrict__ qsym, const uint32_t* __restrict__ thr, int card,
     uint32_t* __restrict__ bits, uint32_t* __restrict__ lists, uint32_t* __restrict__ list_count, int64_t list_cap,
-    unsigned long long* __restrict__ pages_kept) {
+    unsigned long long* __restrict__ pages_kept, int stop_over_cap) {
   extern __shared__ __align__(16) float s_tab[];
   const int64_t q = blockIdx.y;
   load_fp32_table(qtable + q * (int64_t)card * 16, card, s_tab);
@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(kPageThreads) page_lb_kernel(
   unsigned long long kept = 0;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t sw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; sw * 32 < nsuper; sw += nw) {
+    // a query whose kept pages already exceed its list goes to the tensor-core screening: when
+    // that is all the caller needs to know, its page pass ends here (one address per warp)
+    if (stop_over_cap && (int64_t)__ldcg(list_count + q) > list_cap) break;
     const int64_t sp = sw * 32 + lane;
     const bool sval = sp < nsuper;
     const uint4 slo = sval ? __ldg(senv + 2 * sp) : make_uint4(0u, 0u, 0u, 0u);
@@ -404,7 +407,8 @@ paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st) {
 }
 
 paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_t q0, int64_t nq, uint32_t* bits,
-                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st) {
+                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st,
+                            bool stop_over_cap) {
   if (nq <= 0) return PARIS_OK;
   if (!qs.qsym) return fail(PARIS_EINTERNAL, "query symbols were not prepared");
   const int64_t words = page_words(idx->n), npages = idx->npages, nsuper = (npages + 15) / 16;
@@ -422,7 +426,7 @@ paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_
   page_lb_kernel<<<grid, kPageThreads, smem, st>>>(env + 2 * npages, nsuper, env, npages, words,
                                                   qs.qtable + q0 * (int64_t)idx->card * 16, qs.qsym + q0 * 16,
                                                   qs.thr + q0, idx->card, bits, lists, list_count, list_cap,
-                                                  qs.counters + 5);
+                                                  qs.counters + 5, stop_over_cap ? 1 : 0);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
   return PARIS_OK;

@@ -92,9 +92,11 @@ int64_t page_list_cap(int64_t n);  // kept pages a BATCHED query may list (more:
 paris_status build_leaf_envelopes(paris_index* idx, cudaStream_t st);
 // Page bits of chunk queries [q0, q0 + nq) into bits ([nq][words], may be NULL), kept page counts into
 // list_count [nq] and the first list_cap kept pages of each into lists [nq][list_cap] (may be
-// NULL); bits and counts are zeroed first.
+// NULL); bits and counts are zeroed first. With stop_over_cap, a query's pass may end as soon as
+// its count passes list_cap (its bits and count are then partial; the count stays > list_cap).
 paris_status launch_page_lb(const paris_index* idx, const QueryState& qs, int64_t q0, int64_t nq, uint32_t* bits,
-                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st);
+                            uint32_t* lists, uint32_t* list_count, int64_t list_cap, cudaStream_t st,
+                            bool stop_over_cap = false);
 // The scan of the chunk's queries whose kept pages fit their lists (the others: tile scan).
 paris_status launch_lbscan_lists(const paris_index* idx, const QueryState& qs, const ChunkState& cs,
                                  int stop_on_overflow, uint32_t* status, cudaStream_t st);
