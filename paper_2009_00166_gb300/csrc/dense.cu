@@ -13,20 +13,26 @@
 //
 // Per pair the epilogue first applies a cheaper test with the row tile's norm range (smallest
 // and largest |x|^2, largest |x|): pass 2 drops a pair when rd(xn_min - 2 q~.x~) exceeds
-// ru(thr + M_max - |q|^2), which implies d~ - M > thr for the pair's own norms; only the pairs
-// that survive get the exact interval above. Pass 1 ranks the looser upper ends
-// ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max), which still bound the distance from above.
+// ru(thr + M_max - |q|^2) (applied as a per-query threshold on the dot product, see emit_kernel),
+// which implies d~ - M > thr for the pair's own norms; only the pairs that survive get the exact
+// interval above. Pass 1 ranks the looser upper ends ru(ru(xn_max - 2 q~.x~) + |q|^2 + M_max),
+// which still bound the distance from above.
 //
-// Kernel shape: one persistent CTA per SM holds two query tiles of 128 queries in shared memory
-// (BF16, K-major, 128-byte swizzle, written once per launch); warp 0 streams the row tiles of
-// the BF16 shadow of the series (128 rows x 64 K elements per stage) into a 6-stage ring with
-// TMA, warp 1 issues the tensor-core MMAs (one thread; 128 x 128 x 16 per instruction, both
-// operands from shared memory) of both query tiles against each row tile into double-buffered
-// TMEM accumulators (2 x 2 x 128 x 128 fp32, all 512 columns), and warps 2-17 read the
-// accumulators back (tcgen05.ld) and run the screening epilogue: one query per thread and 64
-// rows of the tile per warp, 32 at a time. The epilogue reads each 64-row norm range from global
-// memory two tiles ahead, and a row's own norms only for the rare pairs that pass the range
-// test. Each row tile read from HBM serves 256 queries.
+// Kernel shapes (one persistent CTA per SM; warp 0 streams the row tiles of the BF16 shadow of
+// the series, 128 rows x 64 K elements per stage, into a TMA ring; warp 1 issues the tensor-core
+// MMAs from one thread; warps 2-17 read the TMEM accumulators back with tcgen05.ld and run the
+// epilogue; every wait between roles is bounded):
+//   emit_kernel<2> (pass 2) and emit_kernel<1> (pass 1 for k = 1): rows on the MMA M side, a
+//     group of up to 256 queries (fewer for series longer than 256 values, so that the group
+//     fits 128 KB of shared memory) on N: one 128 x N x 16 MMA per K step, both operands in
+//     shared memory, double-buffered 128 x N fp32 accumulators; a thread of the epilogue owns a
+//     row and 64 of the group's queries. Up to 8 groups per launch split the CTAs and visit the
+//     row tiles in the same order, so each row tile read from HBM serves every group.
+//   bound_kernel (pass 1 for k > 1, series of at most 256 values): two tiles of 128 queries on M
+//     against each 128-row tile on N (128 x 128 x 16 MMAs), one query per epilogue thread, which
+//     keeps its k smallest upper ends in registers.
+// The epilogues read each 64-row norm range from global memory ahead of use, and a row's own
+// norms only for the pairs that pass the range test.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
