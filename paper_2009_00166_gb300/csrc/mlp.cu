@@ -1,7 +1,8 @@
 // Learned best-so-far proposal: a 16 -> 256 -> 256 -> 4096 MLP over the query PAA that ranks
 // 12-bit key-prefix buckets (first bit of segments 0..11). Training (softmax cross-entropy,
-// AdamW on FP32 master weights) and inference run in this file's kernels: BF16 tensor-core GEMMs
-// (mma.sync m16n8k16, FP32 accumulation) with fused bias + exact-erf GELU epilogues.
+// AdamW on FP32 master weights) and inference run in this file's kernels: BF16 GEMMs on the
+// 5th-generation tensor cores (tcgen05.mma, operands in shared memory, FP32 accumulation in
+// tensor memory) with fused bias + exact-erf GELU epilogues.
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
@@ -13,6 +14,7 @@
 #include <vector>
 
 #include "query.cuh"
+#include "tcgen05.cuh"
 
 struct paris_seed_model {
   static constexpr int IN = 16, HID = 256, OUT = 4096;
@@ -28,7 +30,6 @@ namespace paris {
 
 namespace {
 
-constexpr int G_BM = 64, G_BN = 64, G_BK = 32, G_THREADS = 128;
 constexpr int EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2;
 
 __device__ __forceinline__ float to_f(float x) { return x; }
@@ -39,86 +40,153 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+// GEMM tiles: 128 rows of C (the MMA M side, one TMEM lane each) x 128 columns (N), K in blocks
+// of 64 BF16 values (one 128-byte row of the swizzled layout).
+constexpr int T_BM = 128, T_BN = 128, T_BK = 64, T_THREADS = 128;
+constexpr size_t T_TILE = (size_t)T_BM * 128;  // one operand's K block: 128 rows x 128 bytes
+// 56 KB of shared memory per CTA: at most four CTAs per SM, whose 128 TMEM columns each fit the
+// SM's 512 (an allocation then never waits for another CTA)
+constexpr size_t T_SMEM = 56 * 1024;
+static_assert(1024 + 2 * T_TILE + 64 <= T_SMEM, "tiles and barrier fit");
+constexpr uint32_t T_TMEM_COLS = 128;
+
+__device__ uint32_t g_gemm_status;  // set when a GEMM's wait for its MMAs ran out
 
 // C[M][N] = sum_k A(m,k) B(k,n) with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn];
-// operands rounded to BF16 when staged in shared memory, FP32 accumulation. Epilogues: store,
-// + bias[n], or + bias[n] then GELU (C receives the pre-activation, H the activation).
+// operands rounded to BF16 when staged in shared memory, FP32 accumulation in tensor memory.
+// Per K block all threads stage both operands (16-byte chunks, 128-byte swizzle, K-major), one
+// thread issues four 128 x 128 x 16 MMAs and commits them to an mbarrier that every thread waits
+// on (bounded) before the next staging. Epilogues: store, + bias[n], or + bias[n] then GELU
+// (C receives the pre-activation, H the activation).
 template <typename TA, typename TB, int EPI>
-__global__ void __launch_bounds__(G_THREADS) gemm_bf16_kernel(int M, int N, int K, const TA* __restrict__ A,
-                                                              int64_t sam, int64_t sak, const TB* __restrict__ B,
-                                                              int64_t sbk, int64_t sbn, float* __restrict__ C,
-                                                              int64_t ldc, const float* __restrict__ bias,
-                                                              float* __restrict__ H) {
-  __shared__ __nv_bfloat16 As[G_BM][G_BK + 8];  // [m][k]
-  __shared__ __nv_bfloat16 Bs[G_BN][G_BK + 8];  // [n][k]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.y * G_BM, n0 = blockIdx.x * G_BN;
-  float acc[8][4];
+__global__ void __launch_bounds__(T_THREADS) gemm_tc_kernel(int M, int N, int K, const TA* __restrict__ A,
+                                                            int64_t sam, int64_t sak, const TB* __restrict__ B,
+                                                            int64_t sbk, int64_t sbn, float* __restrict__ C,
+                                                            int64_t ldc, const float* __restrict__ bias,
+                                                            float* __restrict__ H, uint64_t wait_ns) {
+  extern __shared__ uint8_t g_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)g_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + T_TILE;
+  uint64_t* bar = (uint64_t*)(sB + T_TILE);
+  uint32_t* holder = (uint32_t*)(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * T_BM, n0 = blockIdx.x * T_BN;
+  const uint32_t b_mma = tc::smem_u32(bar);
+  if (tid == 0) tc::mbar_init(b_mma, 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(holder), T_TMEM_COLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *holder;
+  const uint64_t deadline = tc::globaltimer() + wait_ns;
+  constexpr uint32_t idesc = tc::idesc_bf16(T_BM, T_BN);
+  bool ok = true;
+  uint32_t phase = 0;
+  const int nkb = (K + T_BK - 1) / T_BK;
+  for (int kb = 0; kb < nkb && ok; ++kb) {
+    const int k0 = kb * T_BK;
+    // row r's 16-byte chunk j (elements k0 + 8j .. k0 + 8j + 7) at r * 128 + 16 * (j ^ (r mod 8))
+    for (int e = tid; e < T_BM * 8; e += T_THREADS) {
+      const int r = e >> 3, j = e & 7;
+      float va[8], vb[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += G_BK) {
-    for (int e = tid; e < G_BM * G_BK; e += G_THREADS) {
-      const int mm = e / G_BK, kk = e % G_BK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      const float v = (gm < M && gk < K) ? to_f(A[(int64_t)gm * sam + (int64_t)gk * sak]) : 0.f;
-      As[mm][kk] = __float2bfloat16_rn(v);
-    }
-    for (int e = tid; e < G_BN * G_BK; e += G_THREADS) {
-      const int nn = e / G_BK, kk = e % G_BK;
-      const int gn = n0 + nn, gk = k0 + kk;
-      const float v = (gn < N && gk < K) ? to_f(B[(int64_t)gk * sbk + (int64_t)gn * sbn]) : 0.f;
-      Bs[nn][kk] = __float2bfloat16_rn(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < G_BK; ks += 16) {
-      const int r = warp * 16 + g;
-      uint32_t a[4];
-      a[0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * t]);
-      a[1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * t]);
-      a[2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * t + 8]);
-      a[3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * t + 8]);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][ks + 2 * t]);
-        b[1] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][ks + 2 * t + 8]);
-        mma_bf16_16816(acc[j], a, b);
+      for (int i = 0; i < 8; ++i) {
+        const int k = k0 + 8 * j + i;
+        va[i] = (m0 + r < M && k < K) ? to_f(A[(int64_t)(m0 + r) * sam + (int64_t)k * sak]) : 0.f;
+        vb[i] = (n0 + r < N && k < K) ? to_f(B[(int64_t)k * sbk + (int64_t)(n0 + r) * sbn]) : 0.f;
       }
+      uint4 pa, pb;
+      __nv_bfloat162 t;
+#define PACK(dst, src)                                   \
+  t = __floats2bfloat162_rn(src[0], src[1]);             \
+  dst.x = *reinterpret_cast<uint32_t*>(&t);              \
+  t = __floats2bfloat162_rn(src[2], src[3]);             \
+  dst.y = *reinterpret_cast<uint32_t*>(&t);              \
+  t = __floats2bfloat162_rn(src[4], src[5]);             \
+  dst.z = *reinterpret_cast<uint32_t*>(&t);              \
+  t = __floats2bfloat162_rn(src[6], src[7]);             \
+  dst.w = *reinterpret_cast<uint32_t*>(&t);
+      PACK(pa, va)
+      PACK(pb, vb)
+#undef PACK
+      const int off = r * 128 + ((j ^ (r & 7)) << 4);
+      *reinterpret_cast<uint4*>(sA + off) = pa;
+      *reinterpret_cast<uint4*>(sB + off) = pb;
     }
+    tc::fence_proxy_async();
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < T_BK / 16; ++ks)
+        tc::mma_bf16(tmem, tc::desc_sw128(tc::smem_u32(sA) + 32 * ks), tc::desc_sw128(tc::smem_u32(sB) + 32 * ks),
+                     idesc, (kb | ks) ? 1u : 0u);
+      tc::commit(b_mma);
+    }
+    // the MMAs read shared memory until they complete: every thread waits before restaging
+    ok = tc::mbar_wait_until(b_mma, phase, deadline);
+    phase ^= 1u;
+    tc::fence_after();
+    ok = __syncthreads_and(ok);
   }
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;  // TMEM lane = row of the tile
+#pragma unroll 1
+    for (int c0 = 0; c0 < T_BN; c0 += 32) {
+      if (n0 + c0 >= N) break;
+      uint32_t v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < M) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int row = m0 + warp * 16 + g + (c >= 2 ? 8 : 0);
-      const int col = n0 + j * 8 + 2 * t + (c & 1);
-      if (row < M && col < N) {
-        float val = acc[j][c];
-        if (EPI != EPI_STORE) val += bias[col];
-        C[(int64_t)row * ldc + col] = val;
-        if (EPI == EPI_BIAS_GELU) H[(int64_t)row * ldc + col] = gelu_f(val);
+        for (int jj = 0; jj < 32; ++jj) {
+          const int col = n0 + c0 + jj;
+          if (col < N) {
+            float val = __uint_as_float(v[jj]);
+            if (EPI != EPI_STORE) val += bias[col];
+            C[(int64_t)row * ldc + col] = val;
+            if (EPI == EPI_BIAS_GELU) H[(int64_t)row * ldc + col] = gelu_f(val);
+          }
+        }
       }
     }
+  } else {
+    // the MMAs were not seen to finish: wait (at most 0.1 s more) before the tensor memory they
+    // write is released, and report the timeout
+    if (tid == 0) atomicOr(&g_gemm_status, 1u);
+    tc::mbar_wait_until(b_mma, phase ^ 1u, tc::globaltimer() + 100000000ull);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_free(tmem, T_TMEM_COLS);
   }
 }
 
 template <typename TA, typename TB, int EPI>
 void gemm(int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn, float* C,
           int64_t ldc, const float* bias, float* H, cudaStream_t st) {
-  dim3 grid((N + G_BN - 1) / G_BN, (M + G_BM - 1) / G_BM);
-  gemm_bf16_kernel<TA, TB, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, H);
+  cudaFuncSetAttribute(gemm_tc_kernel<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T_SMEM);
+  dim3 grid((N + T_BN - 1) / T_BN, (M + T_BM - 1) / T_BM);
+  gemm_tc_kernel<TA, TB, EPI><<<grid, T_THREADS, T_SMEM, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, H,
+                                                               wait_limit_ns());
   note_launches(1);
+}
+
+// PARIS_ETIMEOUT when a GEMM since the last check gave up waiting for its MMAs (then cleared).
+paris_status check_gemm_status(cudaStream_t st) {
+  uint32_t s = 0;
+  PARIS_CUDA(cudaMemcpyFromSymbolAsync(&s, g_gemm_status, 4, 0, cudaMemcpyDeviceToHost, st));
+  PARIS_CUDA(cudaStreamSynchronize(st));
+  if (s) {
+    const uint32_t zero = 0;
+    PARIS_CUDA(cudaMemcpyToSymbolAsync(g_gemm_status, &zero, 4, 0, cudaMemcpyHostToDevice, st));
+    PARIS_CUDA(cudaStreamSynchronize(st));
+    return fail(PARIS_ETIMEOUT, "a seed-model GEMM's wait for its tensor-core operations expired");
+  }
+  return PARIS_OK;
 }
 
 // Mean softmax cross-entropy: per row, D <- (softmax(L) - onehot(y)) / B; loss += CE / B.
@@ -426,7 +494,7 @@ paris_status learned_keys(const paris_index* idx, const paris_seed_model* md, in
   bucket_keys_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(qs.qkey, bk.as<int>(), nq, r, keys);
   note_launches(1);
   PARIS_CUDA(cudaGetLastError());
-  return PARIS_OK;
+  return check_gemm_status(st);
 }
 
 }  // namespace paris
@@ -545,6 +613,7 @@ paris_status paris_seed_model_forward(const paris_seed_model* md, const double* 
   }
   PARIS_CUDA(cudaGetLastError());
   PARIS_CUDA(cudaStreamSynchronize(st));
+  PARIS_TRY(check_gemm_status(st));
   return PARIS_OK;
 }
 
@@ -573,6 +642,7 @@ paris_status paris_seed_model_topr(const paris_seed_model* md, const double* paa
   }
   PARIS_CUDA(cudaGetLastError());
   PARIS_CUDA(cudaStreamSynchronize(st));
+  PARIS_TRY(check_gemm_status(st));
   return PARIS_OK;
 }
 
@@ -596,6 +666,7 @@ paris_status paris_seed_model_gradients(const paris_seed_model* md, const double
   float l = 0.f;
   PARIS_CUDA(cudaMemcpyAsync(&l, ws.loss, 4, cudaMemcpyDeviceToHost, st));
   PARIS_CUDA(cudaStreamSynchronize(st));
+  PARIS_TRY(check_gemm_status(st));
   if (loss_host) *loss_host = l;
   return PARIS_OK;
 }
@@ -644,6 +715,7 @@ paris_status paris_seed_model_train(paris_seed_model* md, const double* paa, con
   }
   PARIS_CUDA(cudaGetLastError());
   PARIS_CUDA(cudaStreamSynchronize(st));
+  PARIS_TRY(check_gemm_status(st));
   return PARIS_OK;
 }
 
