@@ -64,8 +64,9 @@ typedef struct paris_build_opts {
   int32_t leaf_capacity; /* L: rows per approximate-search leaf; 0 = 2048; max 4096 */
   int32_t bf16_shadow;   /* 1: the encode pass also writes the BF16 copy of the series and the
                             row norms that PARIS_REFINE_MIXED screens with (otherwise they are
-                            built by the first MIXED query); no effect for shapes the screening
-                            does not support (len not a multiple of 64 or above 256) */
+                            built by the first MIXED query); written by the encode pass only when
+                            len is a multiple of 64, len <= 1024 and len / w <= 16 (otherwise
+                            the first MIXED query builds it) */
   int32_t series_on_host; /* 1 (host series only): keep the series in host memory instead of copying
                              it to the device -- the collection may exceed HBM. The build streams
                              it through two 512 MB device staging buffers (a copy of one chunk
@@ -112,7 +113,9 @@ enum {
   PARIS_REFINE_MIXED = 1, /* queries whose lower bounds keep many rows are screened by BF16
                              tensor-core |q|^2+|x|^2-2q.x tiles (FP32 accumulation); only rows
                              within the proven BF16 error margin of the best-so-far are
-                             re-checked in fp32. Same exact answers. k <= 16. */
+                             re-checked in fp32. Same exact answers. k <= 16; the screening
+                             needs len a multiple of 64 and at most 1024 (other shapes refine
+                             every kept candidate as PARIS_REFINE_FP32 does). */
 };
 
 enum {
